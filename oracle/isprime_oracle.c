@@ -1,0 +1,428 @@
+/*
+ * isprime_oracle.c -- plain, slow, obviously-correct CPU primality oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link,
+ * load or call this file; only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * What it computes (paper: "Improving MATLAB's isprime performance without
+ * arbitrary-precision arithmetic", Sec. 1): out[i] = 1 iff in[i] is prime,
+ * elementwise, same length as the input.  The paper's deterministic
+ * Miller-Rabin (Sec. 2, Eqs. 1-4) reaches exactly that result for every
+ * n < 2^64, so the oracle is the plain definition:
+ *
+ *   n < 2            -> 0                       (Sec. 1 example: isprime(1) = 0)
+ *   n < 2^24         -> trial division by 2 and every odd d with d*d <= n
+ *   n >= 2^24        -> trial division by the primes <= 97, then the strong
+ *                       probable-prime test (Sec. 2.1, read as the textbook
+ *                       condition) to each of the seven bases of Eq. 4,
+ *                       with a*b mod n taken in unsigned __int128 and a^e mod n
+ *                       by left-to-right square-and-multiply (ModExp, Sec. 2.4).
+ *
+ * Readings of the paper taken here:
+ *   - Eq. 1 prints a^(n-1) = +-1 (mod n) and Sec. 2.1 says every term of the
+ *     squaring sequence is +-1.  Fermat gives a^(n-1) = 1, and the property that
+ *     holds for primes is the strong condition: a^d = 1, or a^(2^r d) = n-1
+ *     for some 0 <= r < s, where n-1 = 2^s d with d odd.  That is what is
+ *     implemented.
+ *   - A base a with a mod n == 0 is skipped (the usual convention for the
+ *     seven-base set of Eq. 4; it cannot happen for n > 1795265022).
+ *
+ * Also here, for pinning the oracle against the paper and for cross-checks:
+ *   - ModAdd (Sec. 2.2, "Property 1") and the double-and-add modular multiply
+ *     of Sec. 2.3 with both overflow fixes applied, an __int128-free mulmod
+ *     that tests compare against the __int128 one;
+ *   - a plain sieve of Eratosthenes (Sec. 1 / Sec. 6 description of isprime);
+ *   - the 2/3/5/7 wheel of Sec. 3 (Eqs. 5-6) and wheel trial division;
+ *   - a counter of the modular squarings and multiplications the method's
+ *     schedule performs per element (measurement of algorithmic work);
+ *   - a multi-threaded driver (static 64 Ki-element chunks) used for large
+ *     pins and the CPU baseline.
+ *
+ * Parity unpinned: that the seven bases of Eq. 4 decide every n < 2^64 rests
+ * on the cited result (Sinclair 2011); the pseudoprime tables that prove it
+ * are not reproduced here.  Everything else is pinned by the tests.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#include <pthread.h>
+
+typedef unsigned __int128 u128;
+
+/* Eq. 4: the seven Miller-Rabin bases that are exact for all n < 2^64. */
+static const uint64_t kBases[7] = {2ULL, 325ULL, 9375ULL, 28178ULL,
+                                   450775ULL, 9780504ULL, 1795265022ULL};
+
+/* Primes <= 97, used only to cut work before Miller-Rabin. */
+static const uint64_t kSmallPrimes[25] = {2,  3,  5,  7,  11, 13, 17, 19, 23,
+                                          29, 31, 37, 41, 43, 47, 53, 59, 61,
+                                          67, 71, 73, 79, 83, 89, 97};
+
+#define TRIAL_ONLY_LIMIT (1ULL << 24)
+
+/* ------------------------------------------------------------------ */
+/* Modular arithmetic                                                  */
+/* ------------------------------------------------------------------ */
+
+/* a*b mod m by the exact 128-bit product. */
+uint64_t oracle_mulmod(uint64_t a, uint64_t b, uint64_t m) {
+  return (uint64_t)(((u128)a * (u128)b) % (u128)m);
+}
+
+/* ModAdd, Sec. 2.2: (a + b) mod m for a, b < m, no intermediate >= 2^64.
+ * If a + b >= m then a >= m - b and the sum reduces to a - (m - b)
+ * (Property 1); otherwise a + b < m is already reduced. */
+uint64_t oracle_modadd(uint64_t a, uint64_t b, uint64_t m) {
+  uint64_t gap = m - b; /* > 0 because b < m */
+  return (a >= gap) ? a - gap : a + b;
+}
+
+/* Sec. 2.3: double-and-add modular multiplication with the two overflow
+ * fixes the paper describes (the accumulate step and the doubling step both
+ * go through ModAdd).  No 128-bit arithmetic: an independent check of
+ * oracle_mulmod. */
+uint64_t oracle_mulmod_classic(uint64_t a, uint64_t b, uint64_t m) {
+  uint64_t c = 0;
+  a %= m;
+  while (b > 0) {
+    if (b & 1ULL) c = oracle_modadd(c, a, m);
+    a = oracle_modadd(a, a, m);
+    b >>= 1;
+  }
+  return c % m;
+}
+
+/* ModExp, Sec. 2.4: a^e mod m, left-to-right square-and-multiply.
+ * m >= 1.  Counts squarings / multiplications into *sq / *mu when non-null. */
+static uint64_t powmod_counted(uint64_t a, uint64_t e, uint64_t m,
+                               uint64_t *sq, uint64_t *mu) {
+  uint64_t r = 1 % m;
+  a %= m;
+  if (e == 0) return r;
+  int top = 63 - __builtin_clzll(e);
+  r = a; /* the leading 1 bit */
+  for (int b = top - 1; b >= 0; --b) {
+    r = oracle_mulmod(r, r, m);
+    if (sq) ++*sq;
+    if ((e >> b) & 1ULL) {
+      r = oracle_mulmod(r, a, m);
+      if (mu) ++*mu;
+    }
+  }
+  return r;
+}
+
+uint64_t oracle_powmod(uint64_t a, uint64_t e, uint64_t m) {
+  return powmod_counted(a, e, m, NULL, NULL);
+}
+
+/* Strong probable-prime test of odd n > 2 to base a (Sec. 2.1, textbook
+ * form).  Returns 1 if n passes.  sq/mu count the modular squarings and the
+ * multiplications by the base of the binary schedule. */
+static int sprp_counted(uint64_t n, uint64_t a, uint64_t *sq, uint64_t *mu) {
+  a %= n;
+  if (a == 0) return 1; /* base skipped */
+  uint64_t d = n - 1;
+  int s = __builtin_ctzll(d);
+  d >>= s;
+  uint64_t x = powmod_counted(a, d, n, sq, mu);
+  if (x == 1 || x == n - 1) return 1;
+  for (int r = 1; r < s; ++r) {
+    x = oracle_mulmod(x, x, n);
+    if (sq) ++*sq;
+    if (x == n - 1) return 1;
+    if (x == 1) return 0; /* a nontrivial square root of 1: composite */
+  }
+  return 0;
+}
+
+int oracle_sprp(uint64_t n, uint64_t a) {
+  if (n < 3 || (n & 1ULL) == 0) return 0;
+  return sprp_counted(n, a, NULL, NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* The classifier                                                       */
+/* ------------------------------------------------------------------ */
+
+int oracle_isprime1(uint64_t n) {
+  if (n < 2) return 0;
+  if (n < TRIAL_ONLY_LIMIT) {
+    if (n < 4) return 1;
+    if ((n & 1ULL) == 0) return 0;
+    for (uint64_t d = 3; d * d <= n; d += 2)
+      if (n % d == 0) return 0;
+    return 1;
+  }
+  for (int i = 0; i < 25; ++i)
+    if (n % kSmallPrimes[i] == 0) return 0; /* n > 97, so n is not that prime */
+  for (int i = 0; i < 7; ++i)
+    if (!sprp_counted(n, kBases[i], NULL, NULL)) return 0;
+  return 1;
+}
+
+void oracle_isprime_u64(const uint64_t *in, uint8_t *out, size_t n) {
+  for (size_t i = 0; i < n; ++i) out[i] = (uint8_t)oracle_isprime1(in[i]);
+}
+
+/* Double input (Sec. 8.1: doubles hold the values <= 2^53).  An element is
+ * valid when it is finite, >= 0, integral and <= 2^53; valid elements are
+ * classified as integers, invalid ones give 0.  Returns the invalid count. */
+uint64_t oracle_isprime_f64(const double *in, uint8_t *out, size_t n) {
+  uint64_t bad = 0;
+  const double lim = 9007199254740992.0; /* 2^53 */
+  for (size_t i = 0; i < n; ++i) {
+    double x = in[i];
+    if (!(x >= 0.0) || !(x <= lim) || floor(x) != x) {
+      out[i] = 0;
+      ++bad;
+      continue;
+    }
+    out[i] = (uint8_t)oracle_isprime1((uint64_t)x);
+  }
+  return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Multi-threaded driver: static 64 Ki-element chunks, chunk c goes to  */
+/* thread c mod T.                                                      */
+/* ------------------------------------------------------------------ */
+
+#define MT_CHUNK ((size_t)1 << 16)
+
+typedef struct {
+  const uint64_t *in;
+  uint8_t *out;
+  size_t n;
+  int tid, nthreads;
+} mt_job;
+
+static void *mt_worker(void *p) {
+  mt_job *j = (mt_job *)p;
+  for (size_t c = (size_t)j->tid * MT_CHUNK; c < j->n;
+       c += (size_t)j->nthreads * MT_CHUNK) {
+    size_t e = c + MT_CHUNK < j->n ? c + MT_CHUNK : j->n;
+    oracle_isprime_u64(j->in + c, j->out + c, e - c);
+  }
+  return NULL;
+}
+
+void oracle_isprime_u64_mt(const uint64_t *in, uint8_t *out, size_t n,
+                           int nthreads) {
+  if (nthreads <= 1 || n <= MT_CHUNK) {
+    oracle_isprime_u64(in, out, n);
+    return;
+  }
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  mt_job *jobs = (mt_job *)malloc(sizeof(mt_job) * (size_t)nthreads);
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].in = in;
+    jobs[t].out = out;
+    jobs[t].n = n;
+    jobs[t].tid = t;
+    jobs[t].nthreads = nthreads;
+    pthread_create(&th[t], NULL, mt_worker, &jobs[t]);
+  }
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+  free(th);
+  free(jobs);
+}
+
+/* pi(hi) - pi(lo): primes in [lo, hi) counted with the classifier,
+ * multi-threaded over consecutive integers (no input array). */
+typedef struct {
+  uint64_t lo, hi;
+  int tid, nthreads;
+  uint64_t count;
+} cnt_job;
+
+static void *cnt_worker(void *p) {
+  cnt_job *j = (cnt_job *)p;
+  const uint64_t chunk = 1ULL << 16;
+  uint64_t c0 = j->lo + (uint64_t)j->tid * chunk;
+  for (uint64_t c = c0; c < j->hi && c >= j->lo;
+       c += (uint64_t)j->nthreads * chunk) {
+    uint64_t e = (j->hi - c > chunk) ? c + chunk : j->hi;
+    for (uint64_t v = c; v < e; ++v) j->count += (uint64_t)oracle_isprime1(v);
+  }
+  return NULL;
+}
+
+uint64_t oracle_count_primes(uint64_t lo, uint64_t hi, int nthreads) {
+  if (hi <= lo) return 0;
+  if (nthreads < 1) nthreads = 1;
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  cnt_job *jobs = (cnt_job *)calloc((size_t)nthreads, sizeof(cnt_job));
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].lo = lo;
+    jobs[t].hi = hi;
+    jobs[t].tid = t;
+    jobs[t].nthreads = nthreads;
+    pthread_create(&th[t], NULL, cnt_worker, &jobs[t]);
+  }
+  uint64_t total = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    pthread_join(th[t], NULL);
+    total += jobs[t].count;
+  }
+  free(th);
+  free(jobs);
+  return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sieve of Eratosthenes (Sec. 1, Sec. 6): all primes <= N, ascending.   */
+/* Returns the number of primes; writes at most cap of them to out.      */
+/* ------------------------------------------------------------------ */
+
+size_t oracle_primes_upto(uint64_t N, uint64_t *out, size_t cap) {
+  if (N < 2) return 0;
+  uint8_t *composite = (uint8_t *)calloc((size_t)N + 1, 1);
+  if (!composite) return 0;
+  for (uint64_t p = 2; p * p <= N; ++p)
+    if (!composite[p])
+      for (uint64_t m = p * p; m <= N; m += p) composite[m] = 1;
+  size_t k = 0;
+  for (uint64_t v = 2; v <= N; ++v)
+    if (!composite[v]) {
+      if (k < cap) out[k] = v;
+      ++k;
+    }
+  free(composite);
+  return k;
+}
+
+/* Sec. 6, Table 1: number of divisions MATLAB's isprime performs on 1:N, i.e. the
+ * sum over n = 1..N of the count of sieved primes p <= floor(sqrt(N)) with
+ * p < n.  Computed exactly as that double sum would be, one n at a time
+ * against the sorted prime list. */
+uint64_t oracle_isprime_division_count(uint64_t N) {
+  uint64_t r = (uint64_t)sqrtl((long double)N);
+  while (r * r > N) --r;
+  while ((r + 1) * (r + 1) <= N) ++r;
+  size_t np = oracle_primes_upto(r, NULL, 0);
+  uint64_t *p = (uint64_t *)malloc(sizeof(uint64_t) * (np ? np : 1));
+  oracle_primes_upto(r, p, np);
+  uint64_t total = 0;
+  size_t below = 0; /* number of primes < n */
+  for (uint64_t n = 1; n <= N; ++n) {
+    while (below < np && p[below] < n) ++below;
+    total += below;
+  }
+  free(p);
+  return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* The 2/3/5/7 wheel (Sec. 3, Eqs. 5-6)                                  */
+/* ------------------------------------------------------------------ */
+
+static uint64_t gcd_u64(uint64_t a, uint64_t b) {
+  while (b) {
+    uint64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+/* Differences between consecutive integers coprime to the wheel modulus P
+ * (a product of the first primes: 6, 30, 210, ...), starting at 1 and
+ * running one full cycle up to P + 1.  Writes at most cap entries and
+ * returns the cycle length (the number of residues coprime to P). */
+int oracle_wheel_diffs_mod(uint64_t P, uint32_t *out, int cap) {
+  int k = 0;
+  uint64_t prev = 1;
+  for (uint64_t v = 2; v <= P + 1; ++v) {
+    if (gcd_u64(v, P) == 1) {
+      if (k < cap) out[k] = (uint32_t)(v - prev);
+      ++k;
+      prev = v;
+    }
+  }
+  return k;
+}
+
+/* The 2/3/5/7 wheel of Eq. 5: 48 entries. */
+int oracle_wheel_diffs(uint32_t *out) {
+  return oracle_wheel_diffs_mod(210, out, 48);
+}
+
+/* Sec. 3's medium-scalar method: divide by 2, 3, 5, 7, then by the wheel
+ * sequence 1 + cumsum(cycle repeated) while the divisor squared is <= n. */
+int oracle_isprime_wheel(uint64_t n) {
+  static const uint64_t first[4] = {2, 3, 5, 7};
+  if (n < 2) return 0;
+  for (int i = 0; i < 4; ++i)
+    if (n % first[i] == 0) return n == first[i];
+  uint32_t cyc[48];
+  oracle_wheel_diffs(cyc);
+  uint64_t d = 1;
+  for (uint64_t k = 0;; ++k) {
+    d += cyc[k % 48];
+    if ((u128)d * d > n) return 1;
+    if (n % d == 0) return 0;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithmic work counter                                             */
+/* ------------------------------------------------------------------ */
+/*
+ * Replays the array method's schedule for each element and counts its work:
+ *   odd n >= sieve_limit are trial-divided by the odd primes <= td_bound
+ *   (every such prime is tested: a data-parallel lane does not exit early);
+ *   survivors >= 2^32 go through the seven-base test in order until a base
+ *   fails; each base computes a^d by binary left-to-right square-and-multiply
+ *   and then squares while looking for n-1.
+ * counts[0] elements reaching the 64-bit test
+ * counts[1] modular squarings
+ * counts[2] multiplications by a base other than 2
+ * counts[3] multiplications by the base 2 (these are modular doublings)
+ * counts[4] base tests performed
+ * counts[5] trial-division divisibility tests
+ * counts[6] elements reaching the 32-bit test (sieve_limit <= n < 2^32)
+ * counts[7] primes found
+ */
+void oracle_work_counts(const uint64_t *in, size_t n, uint32_t td_bound,
+                        uint64_t sieve_limit, uint64_t *counts) {
+  static const uint64_t odd_primes[] = {
+      3,   5,   7,   11,  13,  17,  19,  23,  29,  31,  37,  41,  43,  47,
+      53,  59,  61,  67,  71,  73,  79,  83,  89,  97,  101, 103, 107, 109,
+      113, 127, 131, 137, 139, 149, 151, 157, 163, 167, 173, 179, 181, 191,
+      193, 197, 199, 211, 223, 227, 229, 233, 239, 241, 251};
+  const int nodd = (int)(sizeof(odd_primes) / sizeof(odd_primes[0]));
+  for (int k = 0; k < 8; ++k) counts[k] = 0;
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t v = in[i];
+    int prime = oracle_isprime1(v);
+    counts[7] += (uint64_t)prime;
+    if (v < 2 || (v & 1ULL) == 0 || v < sieve_limit) continue;
+    int divisible = 0;
+    for (int k = 0; k < nodd && odd_primes[k] <= td_bound; ++k) {
+      ++counts[5];
+      if (v % odd_primes[k] == 0) divisible = 1;
+    }
+    if (divisible) continue;
+    if (v < (1ULL << 32)) {
+      ++counts[6];
+      continue;
+    }
+    ++counts[0];
+    for (int b = 0; b < 7; ++b) {
+      uint64_t sq = 0, mu = 0;
+      int pass = sprp_counted(v, kBases[b], &sq, &mu);
+      ++counts[4];
+      counts[1] += sq;
+      if (kBases[b] == 2)
+        counts[3] += mu;
+      else
+        counts[2] += mu;
+      if (!pass) break;
+    }
+  }
+}
