@@ -1,0 +1,360 @@
+"""Benchmark: uint64 primality tests per second on GB300.
+
+Default workload (N=1): 2^24 uint64 values uniform in [2^49, 2^64) with the
+even indices forced odd ("plain_large"); one step classifies the whole array
+through the library (classify + sieve lookup + trial division + Miller-Rabin
+base 2 + the other six bases).  Inputs are resident in HBM before the timed
+region; the array (128 MiB) is larger than L2 and L2 is also flushed between
+steps.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                  [--workload plain_large|plain_small|plain_mixed]
+
+Under torchrun (N > 1) every rank classifies its own 2^24-element shard (weak
+scaling, no collective on the data path); rank 0 reports the max over ranks.
+`--impl reference` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import generators as wg  # noqa: E402
+
+METRIC = "uint64 primality tests/s & % int-pipe roofline vs plain; serve p50/p99 ms"
+UNIT = "tests/s"
+
+# Algorithmic work per element of plain_large (2^24 values, seed 1, trial
+# division by the 15 odd primes <= 53, sieve below 2^32), counted once over
+# the whole array by the CPU oracle's work counter (binary left-to-right
+# schedule of Sec. 2.4); tests/test_bench_constants.py re-derives them.
+WORK_PLAIN_LARGE = {
+    "trial_tests": 11.2492,       # divisibility tests (multiply-by-inverse)
+    "mr64_elements": 0.2041,      # survivors entering the base-2 test
+    "base2_squarings": 12.4367,
+    "base2_doublings": 6.2259,
+    "base2_passes": 0.0346,       # elements entering the six-base kernel
+    "rest_squarings": 12.5845,
+    "rest_multiplies": 6.3263,
+}
+# 32-bit multiply instructions per 64-bit Montgomery operation as written in
+# csrc/arith.cuh: a 64x64->128 product is 4 wide (32x32->64) partial
+# products, the 64x64->64 low product m = lo * n^-1 is 1 wide + 2 low, and
+# hi(m*n) needs all 4 wide products; a wide product counts as 2 issue slots
+# of the integer multiply pipe (measured mad.wide rate = 1/2 mad.lo rate).
+IMAD_SLOTS_PER_MULMOD = 2 * 4 + (2 + 2) + 2 * 4   # 20
+IMAD_SLOTS_PER_SQUARING = IMAD_SLOTS_PER_MULMOD    # squaring uses the same routine
+IMAD_SLOTS_PER_TRIAL_TEST = 4                      # 64-bit low product: 1 wide + 2 low
+IMAD_PER_SM_PER_CLK = 64                           # 32-bit IMAD issue rate per SM
+SM_COUNT_GB300 = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    p.add_argument("--workload", default="plain_large",
+                   choices=["plain_large", "plain_small", "plain_mixed"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _workload(name: str, rank: int) -> tuple[np.ndarray, str]:
+    if name == "plain_large":
+        n = 1 << 24
+        v = wg.uniform_range(1, n, 1 << 49, 1 << 64, offset=rank * n)
+        v[0::2] |= np.uint64(1)
+        return v, "2^24 uint64 uniform in [2^49, 2^64), even indices odd, seed 1"
+    if name == "plain_small":
+        n = 100_000
+        return wg.uniform_range(0, n, 0, 10**6, offset=rank * n), \
+            "100,000 uint64 uniform in [0, 10^6), seed 0"
+    n = 1 << 26
+    return wg.plain_mixed(n, seed=2, offset=rank * n), \
+        "2^26 uint64, bit length uniform in 2..64, seed 2"
+
+
+# ---------------------------------------------------------------- distributed
+
+def _dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if (args.impl == "mine" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [m for m in mhz if m > 0.5 * (max(mhz) if mhz else 1)]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def _oracle_rate(vals: np.ndarray, target_s: float = 10.0) -> dict:
+    """Times the CPU oracle (all host cores) on a bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.isprime_u64(vals[:4096], threads=cores)
+    t0 = time.perf_counter()
+    cal = vals[: 1 << 18]
+    oracle.isprime_u64(cal, threads=cores)
+    rate = cal.size / max(time.perf_counter() - t0, 1e-9)
+    n = int(min(vals.size, max(1 << 18, rate * target_s)))
+    sample = vals[:n]
+    t0 = time.perf_counter()
+    oracle.isprime_u64(sample, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} elements of the workload, one pass, {cores} threads",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    vals, desc = _workload(args.workload, 0)
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.isprime_u64(vals[: 1 << 16], threads=cores)
+    rate = (1 << 16) / max(time.perf_counter() - t0, 1e-9)
+    budget_s = 60.0
+    per_step = int(max(1 << 12, min(vals.size, rate * budget_s / max(args.steps + args.warmup, 1))))
+    for w in range(args.warmup):
+        oracle.isprime_u64(vals[:per_step], threads=cores)
+    total = 0.0
+    for k in range(args.steps):
+        off = (k * per_step) % max(vals.size - per_step, 1)
+        s = vals[off:off + per_step]
+        t0 = time.perf_counter()
+        oracle.isprime_u64(s, threads=cores)
+        total += time.perf_counter() - t0
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "elements_per_step": per_step,
+                       "description": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} consecutive elements of the workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_mine(args, world, rank, local):
+    import torch
+    import paper_2108_04791_gb300 as ipg
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    vals, desc = _workload(args.workload, rank)
+    n = vals.size
+    d_in = torch.from_numpy(vals.view(np.int64)).to(dev)
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    ctx = ipg.Context.default(local)              # builds the resident sieve (untimed)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
+
+    for _ in range(max(args.warmup, 3)):
+        ctx.isprime(d_in, out=out)
+    torch.cuda.synchronize(dev)
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.stats()["kernel_launches"]
+    ctx.timing_reset()
+    ctx.timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                    # evict the previous step's lines from L2
+        ev_s[k].record(stream)
+        ctx.isprime(d_in, out=out)
+        ev_e[k].record(stream)
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ctx.timing(False)
+    launches = ctx.stats()["kernel_launches"] - launches0
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+    total_s = sum(step_ms) / 1e3
+    total_s = _max_over_ranks(total_s, world, dev)
+    value = n * world * args.steps / total_s
+    ktimes = ctx.timing_read()
+
+    # ---- roofline of the dominant kernel
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms, dom_launches = ktimes[dom]
+    roof = None
+    imad_rate = None
+    try:
+        imad_rate = ipg.int_rates(local)
+    except Exception:  # noqa: BLE001
+        imad_rate = None
+    peak_ops = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6
+    if args.workload == "plain_large":
+        w = WORK_PLAIN_LARGE
+        slots = {
+            "classify_u64": w["trial_tests"] * IMAD_SLOTS_PER_TRIAL_TEST,
+            "mr64_base2": w["base2_squarings"] * IMAD_SLOTS_PER_SQUARING,
+            "mr64_rest": w["rest_squarings"] * IMAD_SLOTS_PER_SQUARING
+            + w["rest_multiplies"] * IMAD_SLOTS_PER_MULMOD,
+        }
+        if dom in slots:
+            per_launch = slots[dom] * n
+            achieved = per_launch / (dom_ms / dom_launches / 1e3)
+            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                    "unit": "T int-mul slots/s", "frac": achieved / peak_ops, "traffic": None,
+                    "kernel": dom, "kernel_ms_per_launch": dom_ms / dom_launches,
+                    "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived)",
+                    "algorithmic_slots_per_element": slots[dom]}
+    kernels = {k: {"ms_per_step": v[0] / max(args.steps, 1), "launches": v[1]}
+               for k, v in ktimes.items() if v[1]}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(vals.view(np.int64)).pin_memory()
+        h_out = torch.empty(n, dtype=torch.uint8).pin_memory()
+        hv = h_in.numpy().view(np.uint64)
+        ho = h_out.numpy()
+        ke = max(3, min(args.steps, 50))
+        for _ in range(2):
+            ipg._check(ipg.lib().isprime_u64_host(ctx.handle, hv.ctypes.data, ho.ctypes.data, n,
+                                                  ipg.ctypes.c_void_p(stream.cuda_stream)))
+        _barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ipg._check(ipg.lib().isprime_u64_host(ctx.handle, hv.ctypes.data, ho.ctypes.data, n,
+                                                  ipg.ctypes.c_void_p(stream.cuda_stream)))
+        dt = _max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": n * world * ke / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": n, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _oracle_rate(vals)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "elements": n, "description": desc,
+                       "l2": "input 128 MiB > L2, plus a 256 MiB L2 flush between steps",
+                       "parallelism": f"dp{world} (independent shards)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk, "kernels": kernels,
+            "wall_s_timed_region": wall, "int_rates": imad_rate,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _parse()
+    world, rank, local = _dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_mine(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * isprime.h -- C ABI of the GB300 elementwise primality library.
+ *
+ * The operation (paper: "Improving MATLAB's isprime performance without
+ * arbitrary-precision arithmetic", Sec. 1): given an array N, return an
+ * array of the same length whose element i is 1 if N[i] is prime and 0
+ * otherwise.  Values are unsigned 64-bit integers (uint64 path), or doubles
+ * that hold integers up to 2^53 (double path; Sec. 8.1 uses double up to
+ * 2^53 and uint64 above).  The result is exact for every value: small values
+ * are answered by a device-resident sieve (Sec. 6.1.3), the rest by trial
+ * division by small primes (Sec. 6.1.2) and deterministic Miller-Rabin with
+ * the seven bases of Eq. 4 (Sec. 2.1) in 64-bit Montgomery arithmetic, or the
+ * bases {2, 7, 61} below 2^32.
+ *
+ * Conventions for every entry point:
+ *   - Return value: ISPRIME_OK (0) or a negative isprime_status.  The text of
+ *     the most recent error on the calling thread is isprime_last_error().
+ *   - Pointers named d_* are device pointers (cudaMalloc'd or torch storage on
+ *     the context's device); h_* are host pointers.  The caller owns every
+ *     buffer it passes; the library owns its contexts (resident sieve, work
+ *     queues, staging buffers) and frees them in isprime_ctx_destroy.
+ *   - Device entry points are asynchronous on `stream` (a cudaStream_t; NULL
+ *     is the legacy default stream).  Outputs are valid once the stream has
+ *     synchronised.  Calls on one context from several streams are ordered
+ *     by the library (they share the context's work queues).
+ *   - n == 0 is a no-op returning ISPRIME_OK.  A NULL pointer with n > 0, an
+ *     input pointer that is not aligned to its element type, or an output
+ *     range that overlaps the input range gives ISPRIME_EINVAL and launches
+ *     nothing.
+ *   - Output bytes are exactly 0 or 1, in input order.
+ */
+#ifndef ISPRIME_H_
+#define ISPRIME_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ISPRIME_OK = 0,
+  ISPRIME_EINVAL = -1,    /* bad argument (NULL, misaligned, overlap, range) */
+  ISPRIME_ENOMEM = -2,    /* device or pinned-host allocation failed */
+  ISPRIME_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  ISPRIME_EDOMAIN = -4,   /* double input held values that are not integers in [0, 2^53] */
+  ISPRIME_ETIMEDOUT = -5, /* a bounded wait ran out */
+  ISPRIME_EBUSY = -6      /* request larger than the server's memory budget */
+} isprime_status;
+
+typedef struct isprime_ctx isprime_ctx;
+typedef struct CUstream_st *isprime_stream; /* same type as cudaStream_t */
+
+/* Launch and algorithm parameters of a context.  Results never depend on
+ * them; only speed does. */
+typedef struct {
+  uint32_t classify_block; /* threads per block of the classify kernel (64..1024, multiple of 32) */
+  uint32_t mr_block;       /* threads per block of the Miller-Rabin kernels (64..1024, multiple of 32) */
+  uint32_t blocks_per_sm;  /* grid = SMs x blocks_per_sm for grid-stride kernels (1..32) */
+  uint32_t td_primes;      /* odd primes 3, 5, 7, ... used for trial division (0..53) */
+  uint32_t chunk_log2;     /* elements per internal chunk = 2^chunk_log2 (16..28) */
+  uint32_t reserved[3];
+} isprime_tuning;
+
+/* Per-context counters since creation (or the last reset). */
+typedef struct {
+  uint64_t calls;          /* completed API calls that launched work */
+  uint64_t elements;       /* elements classified */
+  uint64_t kernel_launches;/* kernels launched by the library */
+  uint64_t sieve_limit;    /* S: values below S are answered by the sieve */
+  uint64_t scratch_bytes;  /* device memory held by the context */
+} isprime_stats;
+
+/* ---------------------------------------------------------------- contexts */
+
+/* Creates a context on `device`: builds the odd-only sieve bitmap for
+ * [0, sieve_limit) on the GPU (S/16 bytes; Sec. 6.1.3's "calculate all primes
+ * up to N" kept resident) and allocates the work queues.  sieve_limit must be
+ * 0 (no sieve) or a multiple of 2^20 no larger than 2^32; ISPRIME_SIEVE_DEFAULT
+ * selects 2^32.  Blocks until the sieve is built.  *out receives the
+ * context; the caller destroys it with isprime_ctx_destroy. */
+#define ISPRIME_SIEVE_DEFAULT ((uint64_t)-1)
+int isprime_ctx_create(int device, uint64_t sieve_limit, isprime_ctx **out);
+
+/* Synchronises the context's device work and frees everything it owns. */
+int isprime_ctx_destroy(isprime_ctx *ctx);
+
+/* The per-device default context used by the entry points without _ctx,
+ * created on first use (sieve limit 2^32) and kept until process exit. */
+int isprime_default_ctx(int device, isprime_ctx **out);
+
+int isprime_ctx_get_tuning(const isprime_ctx *ctx, isprime_tuning *out);
+/* Validates and installs new parameters (ISPRIME_EINVAL if out of range). */
+int isprime_ctx_set_tuning(isprime_ctx *ctx, const isprime_tuning *t);
+int isprime_ctx_stats(const isprime_ctx *ctx, isprime_stats *out);
+
+/* ------------------------------------------------------------- the hot path */
+
+/* out[i] = isprime(in[i]) for i < n (Sec. 1; Sec. 2 for 64-bit values).
+ * d_in: n uint64 values, 8-byte aligned.  d_out: n bytes.  Uses the default
+ * context of the current device. */
+int isprime_u64(const uint64_t *d_in, uint8_t *d_out, size_t n, isprime_stream stream);
+int isprime_u64_ctx(isprime_ctx *ctx, const uint64_t *d_in, uint8_t *d_out, size_t n,
+                    isprime_stream stream);
+
+/* Double path (Sec. 8.1): element i is valid when it is finite, >= 0,
+ * integral and <= 2^53; valid elements are classified as integers, invalid
+ * ones give 0.  If d_invalid is not NULL, the number of invalid elements is
+ * added to the device counter *d_invalid (the caller zeroes it and reads it
+ * after synchronising; a nonzero count is the ISPRIME_EDOMAIN condition). */
+int isprime_f64(const double *d_in, uint8_t *d_out, size_t n, unsigned long long *d_invalid,
+                isprime_stream stream);
+int isprime_f64_ctx(isprime_ctx *ctx, const double *d_in, uint8_t *d_out, size_t n,
+                    unsigned long long *d_invalid, isprime_stream stream);
+
+/* End-to-end form for host buffers: copies h_in to the device in chunks
+ * (through the context's pinned staging buffers), classifies, copies the
+ * bytes back into h_out and synchronises `stream` before returning.  h_in and
+ * h_out may be pageable or pinned. */
+int isprime_u64_host(isprime_ctx *ctx, const uint64_t *h_in, uint8_t *h_out, size_t n,
+                     isprime_stream stream);
+
+/* Number of primes below the context's sieve limit S, counted on the device
+ * from the resident bitmap (pi(S); 0 when S == 0).  Synchronous. */
+int isprime_sieve_count(isprime_ctx *ctx, uint64_t *out);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Kernel identifiers for the timing records. */
+enum {
+  ISPRIME_K_SIEVE_BASE = 0,
+  ISPRIME_K_SIEVE_SEGMENT = 1,
+  ISPRIME_K_CLASSIFY_U64 = 2,
+  ISPRIME_K_CLASSIFY_F64 = 3,
+  ISPRIME_K_MR64_BASE2 = 4,
+  ISPRIME_K_MR64_REST = 5,
+  ISPRIME_K_MR32 = 6,
+  ISPRIME_K_SIEVE_COUNT = 7,
+  ISPRIME_K_COUNT = 8
+};
+
+typedef struct {
+  double total_ms;   /* summed CUDA-event duration of the kernel's launches */
+  uint64_t launches; /* launches recorded */
+} isprime_kernel_time;
+
+/* While enabled, every kernel launch of the context is bracketed by CUDA
+ * events recorded on the launching stream.  isprime_timing_read synchronises
+ * the recorded events and returns per-kernel totals for the ISPRIME_K_COUNT
+ * kernels (array `out` of that length); reset clears them. */
+int isprime_timing_enable(isprime_ctx *ctx, int on);
+int isprime_timing_read(isprime_ctx *ctx, isprime_kernel_time *out, int count);
+int isprime_timing_reset(isprime_ctx *ctx);
+
+/* Integer-pipe throughput of this GPU, measured by kernels of independent
+ * dependency chains (8 per thread, all SMs, full occupancy).  Rates are lane
+ * operations per second; sm_clock_mhz is the SM clock seen during the
+ * measurement (clock64 cycles / event time).  Synchronous; used to state
+ * the integer-pipe roofline of the Miller-Rabin kernels. */
+typedef struct {
+  double mad_lo_u32;     /* mad.lo.u32 */
+  double mad_hi_u32;     /* mad.hi.u32 */
+  double mad_wide_u32;   /* mad.wide.u32 (32x32+64 -> 64) */
+  double mont_mul64;     /* complete 64-bit Montgomery multiplications */
+  double sm_clock_mhz;
+} isprime_int_rates;
+int isprime_measure_int_rates(int device, isprime_int_rates *out);
+
+/* ---------------------------------------------------------------- misc */
+
+const char *isprime_strerror(int status);
+const char *isprime_last_error(void);
+int isprime_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISPRIME_H_ */

@@ -167,14 +167,15 @@ def sprp(n, a) -> bool:
     return bool(lib().oracle_sprp(n, a))
 
 
-WORK_KEYS = ("mr64_elements", "squarings", "multiplies", "doublings",
-             "base_tests", "trial_tests", "mr32_elements", "primes")
+WORK_KEYS = ("mr64_elements", "base2_squarings", "base2_doublings", "base2_passes",
+             "rest_squarings", "rest_multiplies", "base_tests", "trial_tests",
+             "mr32_elements", "primes")
 
 
 def work_counts(values, td_bound: int = 53, sieve_limit: int = 1 << 32) -> dict:
     """Counts of the method's modular operations over the array."""
     a = np.ascontiguousarray(values, dtype=np.uint64)
-    c = np.zeros(8, dtype=np.uint64)
+    c = np.zeros(len(WORK_KEYS), dtype=np.uint64)
     lib().oracle_work_counts(a.ctypes.data, a.size, td_bound, sieve_limit,
                              c.ctypes.data)
     return {k: int(v) for k, v in zip(WORK_KEYS, c)}

@@ -380,13 +380,15 @@ int oracle_isprime_wheel(uint64_t n) {
  *   fails; each base computes a^d by binary left-to-right square-and-multiply
  *   and then squares while looking for n-1.
  * counts[0] elements reaching the 64-bit test
- * counts[1] modular squarings
- * counts[2] multiplications by a base other than 2
- * counts[3] multiplications by the base 2 (these are modular doublings)
- * counts[4] base tests performed
- * counts[5] trial-division divisibility tests
- * counts[6] elements reaching the 32-bit test (sieve_limit <= n < 2^32)
- * counts[7] primes found
+ * counts[1] modular squarings for base 2
+ * counts[2] multiplications by the base 2 (these are modular doublings)
+ * counts[3] elements passing base 2 (they go on to the other six bases)
+ * counts[4] modular squarings for the other six bases
+ * counts[5] multiplications by one of the other six bases
+ * counts[6] base tests performed
+ * counts[7] trial-division divisibility tests
+ * counts[8] elements reaching the 32-bit test (sieve_limit <= n < 2^32)
+ * counts[9] primes found
  */
 void oracle_work_counts(const uint64_t *in, size_t n, uint32_t td_bound,
                         uint64_t sieve_limit, uint64_t *counts) {
@@ -396,32 +398,35 @@ void oracle_work_counts(const uint64_t *in, size_t n, uint32_t td_bound,
       113, 127, 131, 137, 139, 149, 151, 157, 163, 167, 173, 179, 181, 191,
       193, 197, 199, 211, 223, 227, 229, 233, 239, 241, 251};
   const int nodd = (int)(sizeof(odd_primes) / sizeof(odd_primes[0]));
-  for (int k = 0; k < 8; ++k) counts[k] = 0;
+  for (int k = 0; k < 10; ++k) counts[k] = 0;
   for (size_t i = 0; i < n; ++i) {
     uint64_t v = in[i];
     int prime = oracle_isprime1(v);
-    counts[7] += (uint64_t)prime;
+    counts[9] += (uint64_t)prime;
     if (v < 2 || (v & 1ULL) == 0 || v < sieve_limit) continue;
     int divisible = 0;
     for (int k = 0; k < nodd && odd_primes[k] <= td_bound; ++k) {
-      ++counts[5];
+      ++counts[7];
       if (v % odd_primes[k] == 0) divisible = 1;
     }
     if (divisible) continue;
     if (v < (1ULL << 32)) {
-      ++counts[6];
+      ++counts[8];
       continue;
     }
     ++counts[0];
     for (int b = 0; b < 7; ++b) {
       uint64_t sq = 0, mu = 0;
       int pass = sprp_counted(v, kBases[b], &sq, &mu);
-      ++counts[4];
-      counts[1] += sq;
-      if (kBases[b] == 2)
-        counts[3] += mu;
-      else
+      ++counts[6];
+      if (b == 0) {
+        counts[1] += sq;
         counts[2] += mu;
+        counts[3] += (uint64_t)pass;
+      } else {
+        counts[4] += sq;
+        counts[5] += mu;
+      }
       if (!pass) break;
     }
   }

@@ -1,0 +1,279 @@
+"""GB300 elementwise primality (isprime) -- thin Python binding.
+
+Every step of the computation runs in the CUDA library
+(_lib/libisprime_gb300.so, C ABI in include/isprime.h); this module only
+marshals arguments: torch supplies device memory and the current stream.
+There is no CPU fallback: if the library is not built, every call raises.
+
+    import torch, paper_2108_04791_gb300 as ip
+    x = torch.tensor([1, 2, 3, 4, 5], dtype=torch.int64, device="cuda")
+    ip.isprime(x)            # tensor([0, 1, 1, 0, 1], dtype=torch.uint8)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["build", "lib", "isprime", "isprime_host", "Context", "Tuning", "IsPrimeError",
+           "int_rates", "KERNEL_NAMES"]
+
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ETIMEDOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6
+SIEVE_DEFAULT = (1 << 64) - 1
+KERNEL_NAMES = ["sieve_base", "sieve_segment", "classify_u64", "classify_f64",
+                "mr64_base2", "mr64_rest", "mr32", "sieve_count"]
+
+
+class IsPrimeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"isprime error {status}: {msg}")
+        self.status = status
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("classify_block", ctypes.c_uint32), ("mr_block", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("td_primes", ctypes.c_uint32),
+                ("chunk_log2", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_uint64), ("elements", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("sieve_limit", ctypes.c_uint64),
+                ("scratch_bytes", ctypes.c_uint64)]
+
+
+class _KTime(ctypes.Structure):
+    _fields_ = [("total_ms", ctypes.c_double), ("launches", ctypes.c_uint64)]
+
+
+class _IntRates(ctypes.Structure):
+    _fields_ = [("mad_lo_u32", ctypes.c_double), ("mad_hi_u32", ctypes.c_double),
+                ("mad_wide_u32", ctypes.c_double), ("mont_mul64", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double)]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles the CUDA library for sm_103a (in-tree)."""
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB_PATH
+            if not os.path.exists(path):
+                raise IsPrimeError(ECUDA, f"CUDA library not built ({path}); run "
+                                   "paper_2108_04791_gb300.build() on a machine with nvcc")
+            L = ctypes.CDLL(path)
+            vp, sz, u64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+            sigs = {
+                "isprime_ctx_create": ([i32, u64, ctypes.POINTER(vp)], i32),
+                "isprime_ctx_destroy": ([vp], i32),
+                "isprime_default_ctx": ([i32, ctypes.POINTER(vp)], i32),
+                "isprime_ctx_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
+                "isprime_ctx_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
+                "isprime_ctx_stats": ([vp, ctypes.POINTER(_Stats)], i32),
+                "isprime_u64": ([vp, vp, sz, vp], i32),
+                "isprime_u64_ctx": ([vp, vp, vp, sz, vp], i32),
+                "isprime_f64": ([vp, vp, sz, vp, vp], i32),
+                "isprime_f64_ctx": ([vp, vp, vp, sz, vp, vp], i32),
+                "isprime_u64_host": ([vp, vp, vp, sz, vp], i32),
+                "isprime_sieve_count": ([vp, ctypes.POINTER(u64)], i32),
+                "isprime_timing_enable": ([vp, i32], i32),
+                "isprime_timing_read": ([vp, ctypes.POINTER(_KTime), i32], i32),
+                "isprime_timing_reset": ([vp], i32),
+                "isprime_measure_int_rates": ([i32, ctypes.POINTER(_IntRates)], i32),
+                "isprime_strerror": ([i32], ctypes.c_char_p),
+                "isprime_last_error": ([], ctypes.c_char_p),
+                "isprime_version": ([], i32),
+            }
+            for name, (args, res) in sigs.items():
+                f = getattr(L, name)
+                f.argtypes, f.restype = args, res
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        L = lib()
+        raise IsPrimeError(status, f"{L.isprime_strerror(status).decode()}: "
+                                   f"{L.isprime_last_error().decode()}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(t, stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(t.device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _prep(t):
+    """Contiguous CUDA tensor of 8-byte elements and its kind ('u64'|'f64')."""
+    torch = _torch()
+    if not t.is_cuda:
+        raise ValueError("isprime expects a CUDA tensor (use isprime_host for host arrays)")
+    if t.dtype == torch.float64:
+        kind = "f64"
+    elif t.dtype in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        kind = "u64"
+    elif t.dtype in (torch.int32, torch.int16, torch.int8, torch.uint8, torch.bool):
+        if t.dtype != torch.bool and t.numel() and bool((t < 0).any()):
+            raise ValueError("negative integers are not valid isprime inputs")
+        t = t.to(torch.int64)
+        kind = "u64"
+    else:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return t.contiguous(), kind
+
+
+class Context:
+    """A library context on one device: resident sieve, queues, tuning."""
+
+    def __init__(self, device: int = 0, sieve_limit: int | None = None, _handle=None):
+        self._owned = _handle is None
+        if _handle is not None:
+            self._h = _handle
+        else:
+            h = ctypes.c_void_p()
+            _check(lib().isprime_ctx_create(device, SIEVE_DEFAULT if sieve_limit is None
+                                            else sieve_limit, ctypes.byref(h)))
+            self._h = h
+        self.device = device
+
+    @classmethod
+    def default(cls, device: int = 0) -> "Context":
+        h = ctypes.c_void_p()
+        _check(lib().isprime_default_ctx(device, ctypes.byref(h)))
+        return cls(device, _handle=h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._owned and self._h:
+            _check(lib().isprime_ctx_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- tuning / stats / timing
+    @property
+    def tuning(self) -> Tuning:
+        t = Tuning()
+        _check(lib().isprime_ctx_get_tuning(self._h, ctypes.byref(t)))
+        return t
+
+    def set_tuning(self, **kw):
+        t = self.tuning
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(lib().isprime_ctx_set_tuning(self._h, ctypes.byref(t)))
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(lib().isprime_ctx_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def timing(self, on: bool = True):
+        _check(lib().isprime_timing_enable(self._h, 1 if on else 0))
+
+    def timing_read(self) -> dict:
+        arr = (_KTime * len(KERNEL_NAMES))()
+        _check(lib().isprime_timing_read(self._h, arr, len(KERNEL_NAMES)))
+        return {name: (arr[i].total_ms, arr[i].launches) for i, name in enumerate(KERNEL_NAMES)}
+
+    def timing_reset(self):
+        _check(lib().isprime_timing_reset(self._h))
+
+    def sieve_count(self) -> int:
+        v = ctypes.c_uint64()
+        _check(lib().isprime_sieve_count(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    # -- the operation
+    def isprime(self, t, out=None, stream=None, invalid=None):
+        """Elementwise primality of a CUDA tensor; uint8 tensor of t's shape.
+
+        int64 / uint64 tensors are read as unsigned 64-bit values; float64
+        tensors take the double path (invalid elements give 0 and, if
+        `invalid` is a 1-element int64 CUDA tensor, are counted into it)."""
+        torch = _torch()
+        src, kind = _prep(t)
+        if out is None:
+            out = torch.empty(src.shape, dtype=torch.uint8, device=src.device)
+        elif out.dtype != torch.uint8 or out.shape != src.shape or not out.is_contiguous():
+            raise ValueError("out must be a contiguous uint8 tensor of the input's shape")
+        n = src.numel()
+        if n == 0:
+            return out
+        sh = _stream_handle(src, stream)
+        L = lib()
+        if kind == "u64":
+            _check(L.isprime_u64_ctx(self._h, src.data_ptr(), out.data_ptr(), n, sh))
+        else:
+            inv = None if invalid is None else ctypes.c_void_p(invalid.data_ptr())
+            _check(L.isprime_f64_ctx(self._h, src.data_ptr(), out.data_ptr(), n, inv, sh))
+        return out
+
+    def isprime_host(self, values, stream=None) -> np.ndarray:
+        """End-to-end call on a host array (copies in, classifies, copies out)."""
+        a = np.ascontiguousarray(values, dtype=np.uint64)
+        out = np.empty(a.shape, dtype=np.uint8)
+        if a.size:
+            sh = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
+            _check(lib().isprime_u64_host(self._h, a.ctypes.data, out.ctypes.data, a.size, sh))
+        return out
+
+
+_defaults: dict = {}
+
+
+def _default_ctx(device: int) -> Context:
+    c = _defaults.get(device)
+    if c is None:
+        c = _defaults[device] = Context.default(device)
+    return c
+
+
+def isprime(t, out=None, stream=None, invalid=None):
+    """Elementwise isprime of a CUDA tensor with the device's default context."""
+    return _default_ctx(t.device.index or 0).isprime(t, out=out, stream=stream, invalid=invalid)
+
+
+def isprime_host(values, device: int = 0) -> np.ndarray:
+    return _default_ctx(device).isprime_host(values)
+
+
+def int_rates(device: int = 0) -> dict:
+    r = _IntRates()
+    _check(lib().isprime_measure_int_rates(device, ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in r._fields_}

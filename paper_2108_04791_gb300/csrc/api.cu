@@ -1,0 +1,484 @@
+// api.cu -- contexts and the C ABI declared in include/isprime.h.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <memory>
+
+#include "internal.h"
+
+namespace ip {
+
+static thread_local std::string t_last_error;
+
+int set_error(int status, const std::string& msg) {
+  t_last_error = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return set_error(e == cudaErrorMemoryAllocation ? ISPRIME_ENOMEM : ISPRIME_ECUDA, buf);
+}
+
+static cudaEvent_t pool_get(isprime_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int launch_begin(isprime_ctx* ctx, int kid, cudaStream_t s, TimedLaunch* tl) {
+  tl->kid = kid;
+  tl->start = tl->stop = nullptr;
+  if (ctx->timing) {
+    tl->start = pool_get(ctx);
+    tl->stop = pool_get(ctx);
+    if (!tl->start || !tl->stop) return set_error(ISPRIME_ECUDA, "cudaEventCreate failed");
+    IP_CUDA(cudaEventRecord(tl->start, s));
+  }
+  return ISPRIME_OK;
+}
+
+int launch_end(isprime_ctx* ctx, cudaStream_t s, TimedLaunch* tl, const char* name) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  ctx->stats.kernel_launches++;
+  if (ctx->timing) {
+    IP_CUDA(cudaEventRecord(tl->stop, s));
+    ctx->pending.push_back(*tl);
+  }
+  return ISPRIME_OK;
+}
+
+static int collect_timing(isprime_ctx* ctx) {
+  for (auto& t : ctx->pending) {
+    IP_CUDA(cudaEventSynchronize(t.stop));
+    float ms = 0.f;
+    IP_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
+    ctx->kernel_ms[t.kid] += ms;
+    ctx->kernel_launches[t.kid] += 1;
+    ctx->event_pool.push_back(t.start);
+    ctx->event_pool.push_back(t.stop);
+  }
+  ctx->pending.clear();
+  return ISPRIME_OK;
+}
+
+static isprime_tuning default_tuning() {
+  isprime_tuning t{};
+  t.classify_block = 256;
+  t.mr_block = 128;
+  t.blocks_per_sm = 8;
+  t.td_primes = 15;  // 3..53
+  t.chunk_log2 = 24;
+  return t;
+}
+
+static int check_tuning(const isprime_tuning& t) {
+  auto bad_block = [](uint32_t b, uint32_t maxb) { return b < 32 || b > maxb || (b % 32) != 0; };
+  if (bad_block(t.classify_block, 1024)) return set_error(ISPRIME_EINVAL, "classify_block must be a multiple of 32 in [32, 1024]");
+  if (bad_block(t.mr_block, 256)) return set_error(ISPRIME_EINVAL, "mr_block must be a multiple of 32 in [32, 256]");
+  if (t.blocks_per_sm < 1 || t.blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "blocks_per_sm must be in [1, 32]");
+  if (t.td_primes > 53) return set_error(ISPRIME_EINVAL, "td_primes must be in [0, 53]");
+  if (t.chunk_log2 < 16 || t.chunk_log2 > 28) return set_error(ISPRIME_EINVAL, "chunk_log2 must be in [16, 28]");
+  return ISPRIME_OK;
+}
+
+static void free_queues(Queues& q) {
+  cudaFree(q.q64_n);
+  cudaFree(q.q64_idx);
+  cudaFree(q.q64b);
+  cudaFree(q.q32_n);
+  cudaFree(q.q32_idx);
+  cudaFree(q.counters);
+  q = Queues{};
+}
+
+static int ensure_queues(isprime_ctx* ctx, size_t cap) {
+  if (ctx->q.capacity >= cap) return ISPRIME_OK;
+  if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
+  free_queues(ctx->q);
+  Queues q;
+  IP_CUDA(cudaMalloc(&q.q64_n, cap * sizeof(uint64_t)));
+  IP_CUDA(cudaMalloc(&q.q64_idx, cap * sizeof(uint32_t)));
+  IP_CUDA(cudaMalloc(&q.q64b, cap * sizeof(uint32_t)));
+  IP_CUDA(cudaMalloc(&q.q32_n, cap * sizeof(uint32_t)));
+  IP_CUDA(cudaMalloc(&q.q32_idx, cap * sizeof(uint32_t)));
+  IP_CUDA(cudaMalloc(&q.counters, 4 * sizeof(uint32_t)));
+  q.capacity = cap;
+  ctx->q = q;
+  return ISPRIME_OK;
+}
+
+static size_t scratch_bytes(const isprime_ctx* ctx) {
+  return ctx->sieve_limit / 16 + ctx->q.capacity * 24 + ctx->stage_elems * 9;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+static int ctx_create(int device, uint64_t sieve_limit, isprime_ctx** out) {
+  if (!out) return set_error(ISPRIME_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (sieve_limit == ISPRIME_SIEVE_DEFAULT) sieve_limit = 1ull << 32;
+  if (sieve_limit > (1ull << 32) || (sieve_limit & ((1ull << 20) - 1)) != 0)
+    return set_error(ISPRIME_EINVAL, "sieve_limit must be 0 or a multiple of 2^20 no larger than 2^32");
+  int ndev = 0;
+  IP_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_error(ISPRIME_EINVAL, "device out of range");
+  DeviceGuard g(device);
+  std::unique_ptr<isprime_ctx> ctx(new isprime_ctx());
+  ctx->device = device;
+  IP_CUDA(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+  ctx->tune = default_tuning();
+  ctx->sieve_limit = sieve_limit;
+  IP_CUDA(cudaEventCreateWithFlags(&ctx->order_ev, cudaEventDisableTiming));
+  cudaStream_t s;
+  IP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  int st = ISPRIME_OK;
+  if (sieve_limit) {
+    cudaError_t e = cudaMalloc(&ctx->d_sieve, sieve_limit / 16);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(sieve)");
+    if (!st) st = sieve_build(ctx.get(), s);
+  }
+  if (!st) st = ensure_queues(ctx.get(), (size_t)1 << 20);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (st) {
+    isprime_ctx_destroy(ctx.release());
+    return st;
+  }
+  *out = ctx.release();
+  return ISPRIME_OK;
+}
+
+// Orders this call's use of the shared scratch after the previous call's,
+// whatever stream that was on.
+static int order_before(isprime_ctx* ctx, cudaStream_t s) {
+  if (ctx->order_ev_valid) IP_CUDA(cudaStreamWaitEvent(s, ctx->order_ev, 0));
+  return ISPRIME_OK;
+}
+static int order_after(isprime_ctx* ctx, cudaStream_t s) {
+  IP_CUDA(cudaEventRecord(ctx->order_ev, s));
+  ctx->order_ev_valid = true;
+  return ISPRIME_OK;
+}
+
+static bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t a0 = (uintptr_t)a, a1 = a0 + na, b0 = (uintptr_t)b, b1 = b0 + nb;
+  return a0 < b1 && b0 < a1;
+}
+
+// The array path: classify + Miller-Rabin per chunk, all asynchronous.
+// Argument checks shared by every array entry point (no CUDA calls).
+static int check_array_args(const void* d_in, const void* d_out, size_t n, size_t esz) {
+  if (n == 0) return ISPRIME_OK;
+  if (!d_in || !d_out) return set_error(ISPRIME_EINVAL, "NULL pointer with n > 0");
+  if ((uintptr_t)d_in % esz) return set_error(ISPRIME_EINVAL, "input not aligned to its element size");
+  if (n > (SIZE_MAX / esz)) return set_error(ISPRIME_EINVAL, "n too large");
+  if (ranges_overlap(d_in, n * esz, d_out, n)) return set_error(ISPRIME_EINVAL, "output overlaps input");
+  return ISPRIME_OK;
+}
+
+template <bool kF64>
+static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t n,
+                     unsigned long long* d_invalid, cudaStream_t s) {
+  const size_t esz = 8;
+  if (n == 0) return ISPRIME_OK;
+  int st0 = check_array_args(d_in, d_out, n, esz);
+  if (st0) return st0;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard g(ctx->device);
+  const size_t chunk = (size_t)1 << ctx->tune.chunk_log2;
+  int st = ensure_queues(ctx, std::min(chunk, std::max(n, (size_t)1 << 16)));
+  if (st) return st;
+  if ((st = order_before(ctx, s))) return st;
+  const size_t step = std::min(chunk, ctx->q.capacity);
+  for (size_t off = 0; off < n; off += step) {
+    const size_t len = std::min(step, n - off);
+    IP_CUDA(cudaMemsetAsync(ctx->q.counters, 0, 4 * sizeof(uint32_t), s));
+    ClassifyArgs a;
+    a.in = static_cast<const char*>(d_in) + off * esz;
+    a.out = d_out + off;
+    a.n = len;
+    a.sieve = ctx->d_sieve;
+    a.sieve_limit = ctx->sieve_limit;
+    a.ntd = ctx->tune.td_primes;
+    a.td_square = td_square_for(ctx->tune.td_primes);
+    a.q64_n = ctx->q.q64_n;
+    a.q64_idx = ctx->q.q64_idx;
+    a.q32_n = ctx->q.q32_n;
+    a.q32_idx = ctx->q.q32_idx;
+    a.counters = ctx->q.counters;
+    a.invalid = d_invalid;
+    a.head = ((uintptr_t)a.in % 16) ? 1u : 0u;
+    if (a.head > len) a.head = (uint32_t)len;
+    a.pair_store = (((uintptr_t)(a.out + a.head)) % 2 == 0) ? 1u : 0u;
+    st = kF64 ? launch_classify_f64(ctx, a, s) : launch_classify_u64(ctx, a, s);
+    if (st) return st;
+    if ((st = launch_mr(ctx, a.out, s))) return st;
+  }
+  if ((st = order_after(ctx, s))) return st;
+  ctx->stats.calls++;
+  ctx->stats.elements += n;
+  return ISPRIME_OK;
+}
+
+// ---------------------------------------------------------------- defaults
+
+static std::mutex g_default_mu;
+static isprime_ctx* g_default[64] = {};
+
+static int default_ctx(int device, isprime_ctx** out) {
+  if (device < 0 || device >= 64) return set_error(ISPRIME_EINVAL, "device out of range");
+  std::lock_guard<std::mutex> lock(g_default_mu);
+  if (!g_default[device]) {
+    int st = ctx_create(device, ISPRIME_SIEVE_DEFAULT, &g_default[device]);
+    if (st) return st;
+  }
+  *out = g_default[device];
+  return ISPRIME_OK;
+}
+
+static int current_default(isprime_ctx** out) {
+  int dev = 0;
+  IP_CUDA(cudaGetDevice(&dev));
+  return default_ctx(dev, out);
+}
+
+}  // namespace ip
+
+using namespace ip;
+
+extern "C" {
+
+int isprime_ctx_create(int device, uint64_t sieve_limit, isprime_ctx** out) {
+  return ctx_create(device, sieve_limit, out);
+}
+
+int isprime_ctx_destroy(isprime_ctx* ctx) {
+  if (!ctx) return ISPRIME_OK;
+  {
+    DeviceGuard g(ctx->device);
+    if (ctx->order_ev_valid) cudaEventSynchronize(ctx->order_ev);
+    collect_timing(ctx);
+    free_queues(ctx->q);
+    cudaFree(ctx->d_sieve);
+    cudaFree(ctx->d_base_primes);
+    cudaFree(ctx->d_stage_in);
+    cudaFree(ctx->d_stage_out);
+    if (ctx->h_pin_in) cudaFreeHost(ctx->h_pin_in);
+    if (ctx->h_pin_out) cudaFreeHost(ctx->h_pin_out);
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (auto e : ctx->stage_ev)
+      if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
+  }
+  for (int d = 0; d < 64; ++d) {
+    std::lock_guard<std::mutex> lock(g_default_mu);
+    if (g_default[d] == ctx) g_default[d] = nullptr;
+  }
+  delete ctx;
+  return ISPRIME_OK;
+}
+
+int isprime_default_ctx(int device, isprime_ctx** out) {
+  if (!out) return set_error(ISPRIME_EINVAL, "out is NULL");
+  return default_ctx(device, out);
+}
+
+int isprime_ctx_get_tuning(const isprime_ctx* ctx, isprime_tuning* out) {
+  if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
+  *out = ctx->tune;
+  return ISPRIME_OK;
+}
+
+int isprime_ctx_set_tuning(isprime_ctx* ctx, const isprime_tuning* t) {
+  if (!ctx || !t) return set_error(ISPRIME_EINVAL, "NULL argument");
+  int st = check_tuning(*t);
+  if (st) return st;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->tune = *t;
+  return ISPRIME_OK;
+}
+
+int isprime_ctx_stats(const isprime_ctx* ctx, isprime_stats* out) {
+  if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
+  *out = ctx->stats;
+  out->sieve_limit = ctx->sieve_limit;
+  out->scratch_bytes = scratch_bytes(ctx);
+  return ISPRIME_OK;
+}
+
+int isprime_u64_ctx(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
+                    isprime_stream stream) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  return run_array<false>(ctx, d_in, d_out, n, nullptr, (cudaStream_t)stream);
+}
+
+int isprime_u64(const uint64_t* d_in, uint8_t* d_out, size_t n, isprime_stream stream) {
+  if (n == 0) return ISPRIME_OK;
+  int st = check_array_args(d_in, d_out, n, 8);
+  if (st) return st;
+  isprime_ctx* ctx = nullptr;
+  st = current_default(&ctx);
+  if (st) return st;
+  return run_array<false>(ctx, d_in, d_out, n, nullptr, (cudaStream_t)stream);
+}
+
+int isprime_f64_ctx(isprime_ctx* ctx, const double* d_in, uint8_t* d_out, size_t n,
+                    unsigned long long* d_invalid, isprime_stream stream) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  return run_array<true>(ctx, d_in, d_out, n, d_invalid, (cudaStream_t)stream);
+}
+
+int isprime_f64(const double* d_in, uint8_t* d_out, size_t n, unsigned long long* d_invalid,
+                isprime_stream stream) {
+  if (n == 0) return ISPRIME_OK;
+  int st = check_array_args(d_in, d_out, n, 8);
+  if (st) return st;
+  isprime_ctx* ctx = nullptr;
+  st = current_default(&ctx);
+  if (st) return st;
+  return run_array<true>(ctx, d_in, d_out, n, d_invalid, (cudaStream_t)stream);
+}
+
+int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n,
+                     isprime_stream stream) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  if (n == 0) return ISPRIME_OK;
+  int st = check_array_args(h_in, h_out, n, 8);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> host_lock(ctx->host_mu);
+  DeviceGuard g(ctx->device);
+  const size_t chunk = (size_t)1 << ctx->tune.chunk_log2;
+  const size_t stage = std::min(chunk, std::max(n, (size_t)1 << 16));
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ctx->stage_elems < stage) {
+      if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
+      cudaFree(ctx->d_stage_in);
+      cudaFree(ctx->d_stage_out);
+      ctx->d_stage_in = nullptr;
+      ctx->d_stage_out = nullptr;
+      ctx->stage_elems = 0;
+      IP_CUDA(cudaMalloc(&ctx->d_stage_in, 2 * stage * sizeof(uint64_t)));
+      IP_CUDA(cudaMalloc(&ctx->d_stage_out, 2 * stage));
+      ctx->stage_elems = stage;
+    }
+  }
+  // Two staging slots: the copy-in of chunk k+1 overlaps the kernels of chunk
+  // k (stream order keeps each slot's reuse safe).
+  const size_t step = ctx->stage_elems;
+  st = ISPRIME_OK;
+  for (size_t off = 0, k = 0; off < n; off += step, ++k) {
+    const size_t len = std::min(step, n - off);
+    uint64_t* din = ctx->d_stage_in + (k & 1) * step;
+    uint8_t* dout = ctx->d_stage_out + (k & 1) * step;
+    IP_CUDA(cudaMemcpyAsync(din, h_in + off, len * 8, cudaMemcpyHostToDevice, s));
+    if ((st = run_array<false>(ctx, din, dout, len, nullptr, s))) return st;
+    IP_CUDA(cudaMemcpyAsync(h_out + off, dout, len, cudaMemcpyDeviceToHost, s));
+  }
+  IP_CUDA(cudaStreamSynchronize(s));
+  return ISPRIME_OK;
+}
+
+int isprime_sieve_count(isprime_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
+  *out = 0;
+  if (ctx->sieve_limit == 0) return ISPRIME_OK;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard g(ctx->device);
+  uint64_t* d = nullptr;
+  IP_CUDA(cudaMalloc(&d, sizeof(uint64_t)));
+  cudaStream_t s;
+  IP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  IP_CUDA(cudaMemsetAsync(d, 0, sizeof(uint64_t), s));
+  int st = sieve_count(ctx, s, d);
+  uint64_t h = 0;
+  if (!st) {
+    cudaError_t e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "sieve count readback");
+  }
+  cudaStreamDestroy(s);
+  cudaFree(d);
+  if (st) return st;
+  *out = h + (ctx->sieve_limit > 2 ? 1 : 0);  // the bitmap holds odd numbers; add the prime 2
+  return ISPRIME_OK;
+}
+
+int isprime_timing_enable(isprime_ctx* ctx, int on) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->timing = on != 0;
+  return ISPRIME_OK;
+}
+
+int isprime_timing_read(isprime_ctx* ctx, isprime_kernel_time* out, int count) {
+  if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard g(ctx->device);
+  int st = collect_timing(ctx);
+  if (st) return st;
+  for (int k = 0; k < count && k < ISPRIME_K_COUNT; ++k) {
+    out[k].total_ms = ctx->kernel_ms[k];
+    out[k].launches = ctx->kernel_launches[k];
+  }
+  return ISPRIME_OK;
+}
+
+int isprime_timing_reset(isprime_ctx* ctx) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard g(ctx->device);
+  int st = collect_timing(ctx);
+  for (int k = 0; k < ISPRIME_K_COUNT; ++k) {
+    ctx->kernel_ms[k] = 0;
+    ctx->kernel_launches[k] = 0;
+  }
+  return st;
+}
+
+int isprime_measure_int_rates(int device, isprime_int_rates* out) {
+  if (!out) return set_error(ISPRIME_EINVAL, "NULL argument");
+  return measure_int_rates(device, out);
+}
+
+const char* isprime_strerror(int status) {
+  switch (status) {
+    case ISPRIME_OK: return "ok";
+    case ISPRIME_EINVAL: return "invalid argument";
+    case ISPRIME_ENOMEM: return "out of memory";
+    case ISPRIME_ECUDA: return "CUDA error";
+    case ISPRIME_EDOMAIN: return "input outside the domain (not an integer in [0, 2^53])";
+    case ISPRIME_ETIMEDOUT: return "timed out";
+    case ISPRIME_EBUSY: return "request exceeds the memory budget";
+    default: return "unknown status";
+  }
+}
+
+const char* isprime_last_error(void) { return t_last_error.c_str(); }
+
+int isprime_version(void) { return 10000; }
+
+}  // extern "C"

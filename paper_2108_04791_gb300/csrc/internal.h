@@ -1,0 +1,112 @@
+// internal.h -- library-private declarations shared by the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/isprime.h"
+
+namespace ip {
+
+// Records the error text for isprime_last_error() and returns `status`.
+int set_error(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define IP_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::ip::cuda_fail(e_, #call); \
+  } while (0)
+
+// Queue layout (device, per context).  Capacities are the chunk length, so a
+// queue can hold every element of a chunk and never overflows.
+struct Queues {
+  uint64_t* q64_n = nullptr;    // values >= 2^32 that survived trial division
+  uint32_t* q64_idx = nullptr;  // their indices within the chunk
+  uint32_t* q64b = nullptr;     // positions in q64 that passed the base-2 test
+  uint32_t* q32_n = nullptr;    // values in [S, 2^32) that survived trial division
+  uint32_t* q32_idx = nullptr;
+  uint32_t* counters = nullptr; // [0] q64 size, [1] q32 size, [2] q64b size, [3] unused
+  size_t capacity = 0;
+};
+
+struct TimedLaunch {
+  int kid;
+  cudaEvent_t start, stop;
+};
+
+}  // namespace ip
+
+struct isprime_ctx {
+  int device = 0;
+  int sm_count = 0;
+  uint64_t sieve_limit = 0;
+  uint32_t* d_sieve = nullptr;       // odd-only bitmap: bit j <-> 2j+1
+  uint32_t* d_base_primes = nullptr; // odd primes < 2^16
+  uint32_t n_base_primes = 0;
+  ip::Queues q;
+  isprime_tuning tune{};
+  cudaEvent_t order_ev = nullptr;    // last use of the scratch queues
+  bool order_ev_valid = false;
+  std::mutex mu;
+  std::mutex host_mu;  // serialises isprime_u64_host (staging buffers)
+  // measurement
+  bool timing = false;
+  std::vector<ip::TimedLaunch> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double kernel_ms[ISPRIME_K_COUNT] = {};
+  uint64_t kernel_launches[ISPRIME_K_COUNT] = {};
+  isprime_stats stats{};
+  // end-to-end staging (host path)
+  void* h_pin_in = nullptr;
+  uint8_t* h_pin_out = nullptr;
+  uint64_t* d_stage_in = nullptr;
+  uint8_t* d_stage_out = nullptr;
+  size_t stage_elems = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_ev[4] = {};
+};
+
+namespace ip {
+
+// Launch bracket: timing events + launch counting + error check.
+int launch_begin(isprime_ctx* ctx, int kid, cudaStream_t s, TimedLaunch* tl);
+int launch_end(isprime_ctx* ctx, cudaStream_t s, TimedLaunch* tl, const char* name);
+
+// sieve.cu
+int sieve_build(isprime_ctx* ctx, cudaStream_t s);
+int sieve_count(isprime_ctx* ctx, cudaStream_t s, uint64_t* d_out);
+
+// classify.cu
+struct ClassifyArgs {
+  const void* in;
+  uint8_t* out;
+  uint64_t n;                 // elements in this chunk
+  const uint32_t* sieve;
+  uint64_t sieve_limit;
+  uint32_t ntd;
+  uint64_t td_square;         // survivors of trial division below this are prime
+  uint64_t* q64_n;
+  uint32_t* q64_idx;
+  uint32_t* q32_n;
+  uint32_t* q32_idx;
+  uint32_t* counters;
+  unsigned long long* invalid;
+  uint32_t head;              // leading elements handled singly (alignment)
+  uint32_t pair_store;        // 1 if out+head is 2-byte aligned (16-bit stores)
+};
+int launch_classify_u64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s);
+int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s);
+
+// mr.cu
+int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s);
+
+// probe.cu
+int measure_int_rates(int device, isprime_int_rates* out);
+
+uint64_t td_square_for(uint32_t ntd);
+
+}  // namespace ip

@@ -1,0 +1,136 @@
+// probe.cu -- integer-pipe throughput of this GPU (roofline denominators).
+//
+// Each kernel runs 8 independent dependency chains per thread over every SM
+// at full occupancy, so issue rate rather than latency bounds it.  The
+// operations are written as inline PTX so the compiler cannot fold them.
+#include "arith.cuh"
+#include "internal.h"
+
+namespace ip {
+
+constexpr int kChains = 8;
+constexpr int kIters = 1024;
+
+template <int kOp>
+__global__ void __launch_bounds__(256) int_rate_kernel(uint32_t* sink, uint32_t seed,
+                                                       unsigned long long* cycles) {
+  uint32_t a[kChains], b[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) {
+    a[k] = seed * (threadIdx.x + 1) + k;
+    b[k] = seed ^ (k * 0x9E3779B9u);
+  }
+  const uint32_t m = seed | 1u;
+  long long t0 = clock64();
+  for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+      if (kOp == 0) {
+        asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(m), "r"(b[k]));
+      } else if (kOp == 1) {
+        asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(m), "r"(b[k]));
+      } else {
+        // 32x32 + 64 -> 64: the 64-bit accumulator lives in (a, b)
+        asm volatile(
+            "{.reg .u64 t, c;\n\t"
+            "mov.b64 c, {%0, %1};\n\t"
+            "mad.wide.u32 t, %0, %2, c;\n\t"
+            "mov.b64 {%0, %1}, t;}"
+            : "+r"(a[k]), "+r"(b[k])
+            : "r"(m));
+      }
+    }
+  }
+  long long t1 = clock64();
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) acc ^= a[k] ^ b[k];
+  if (acc == 0x12345678u) sink[0] = acc;  // keeps the chains live
+  if (blockIdx.x == 0 && threadIdx.x == 0) *cycles = (unsigned long long)(t1 - t0);
+}
+
+__global__ void __launch_bounds__(256) mont_rate_kernel(uint64_t* sink, uint64_t seed) {
+  uint64_t x[kChains];
+  const uint64_t n = seed | (1ull << 63) | 1ull;
+  const uint64_t ninv = inv64(n);
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) x[k] = (seed * (threadIdx.x + 1) + k) % n;
+  for (int it = 0; it < kIters / 8; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) x[k] = mont_mul(x[k], x[(k + 1) & (kChains - 1)] | 1, n, ninv);
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) acc ^= x[k];
+  if (acc == 0x123456789ull) sink[0] = acc;
+}
+
+int measure_int_rates(int device, isprime_int_rates* out) {
+  int ndev = 0;
+  IP_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_error(ISPRIME_EINVAL, "device out of range");
+  int prev = 0;
+  IP_CUDA(cudaGetDevice(&prev));
+  IP_CUDA(cudaSetDevice(device));
+  int sms = 0, per_sm = 0;
+  IP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  IP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, int_rate_kernel<0>, 256, 0));
+  const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  uint32_t* sink = nullptr;
+  unsigned long long* d_cyc = nullptr;
+  IP_CUDA(cudaMalloc(&sink, 64));
+  IP_CUDA(cudaMalloc(&d_cyc, sizeof(unsigned long long)));
+  cudaEvent_t e0, e1;
+  IP_CUDA(cudaEventCreate(&e0));
+  IP_CUDA(cudaEventCreate(&e1));
+  const double lane_ops = (double)grid * 256 * kIters * kChains;
+  double rates[3] = {0, 0, 0};
+  double mhz = 0;
+  for (int op = 0; op < 3; ++op) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      IP_CUDA(cudaEventRecord(e0));
+      if (op == 0) int_rate_kernel<0><<<grid, 256>>>(sink, 12345u + rep, d_cyc);
+      if (op == 1) int_rate_kernel<1><<<grid, 256>>>(sink, 12345u + rep, d_cyc);
+      if (op == 2) int_rate_kernel<2><<<grid, 256>>>(sink, 12345u + rep, d_cyc);
+      IP_CUDA(cudaGetLastError());
+      IP_CUDA(cudaEventRecord(e1));
+      IP_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      IP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        if (op == 0) {
+          unsigned long long cyc = 0;
+          IP_CUDA(cudaMemcpy(&cyc, d_cyc, sizeof cyc, cudaMemcpyDeviceToHost));
+          mhz = (double)cyc / (ms * 1e3);  // cycles of one block over the kernel time
+        }
+      }
+    }
+    rates[op] = lane_ops / (best * 1e-3);
+  }
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    IP_CUDA(cudaEventRecord(e0));
+    mont_rate_kernel<<<grid, 256>>>(reinterpret_cast<uint64_t*>(sink), 0x9E3779B97F4A7C15ull + rep);
+    IP_CUDA(cudaGetLastError());
+    IP_CUDA(cudaEventRecord(e1));
+    IP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    IP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) best = ms;
+  }
+  out->mad_lo_u32 = rates[0];
+  out->mad_hi_u32 = rates[1];
+  out->mad_wide_u32 = rates[2];
+  out->mont_mul64 = (double)grid * 256 * (kIters / 8) * kChains / (best * 1e-3);
+  out->sm_clock_mhz = mhz;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  cudaFree(d_cyc);
+  cudaSetDevice(prev);
+  return ISPRIME_OK;
+}
+
+}  // namespace ip

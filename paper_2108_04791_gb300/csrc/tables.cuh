@@ -1,0 +1,74 @@
+// tables.cuh -- compile-time constants for the primality kernels.
+//
+// Trial division by small primes (the paper's "shrinking the input array",
+// Sec. 6.1.2, and division minimising, Sec. 6.1.3) is done without any
+// division: for odd p and any n < 2^64,
+//     p | n  <=>  n * p^-1 mod 2^64 <= floor((2^64 - 1) / p)
+// (Granlund and Montgomery, PLDI 1994, Sec. 9).  The inverses and limits are
+// generated at compile time by constexpr Newton iterations.
+#pragma once
+#include <stdint.h>
+
+namespace ip {
+
+// The Miller-Rabin bases of Eq. 4 (exact for all n < 2^64), and the three
+// bases that are exact below 4,759,123,141 > 2^32 (Jaeschke 1993).
+constexpr int kNumBases64 = 7;
+constexpr uint32_t kBases64[kNumBases64] = {2u,      325u,     9375u,      28178u,
+                                            450775u, 9780504u, 1795265022u};
+constexpr int kNumBases32 = 3;
+constexpr uint32_t kBases32[kNumBases32] = {2u, 7u, 61u};
+
+struct BaseTable {
+  uint32_t b64[kNumBases64];
+  uint32_t b32[kNumBases32];
+};
+
+constexpr BaseTable make_base_table() {
+  BaseTable t{};
+  for (int i = 0; i < kNumBases64; ++i) t.b64[i] = kBases64[i];
+  for (int i = 0; i < kNumBases32; ++i) t.b32[i] = kBases32[i];
+  return t;
+}
+
+// Odd primes 3..251 available for trial division.
+constexpr int kMaxTdPrimes = 53;
+constexpr uint32_t kTdPrimeList[kMaxTdPrimes] = {
+    3,   5,   7,   11,  13,  17,  19,  23,  29,  31,  37,  41,  43,  47,
+    53,  59,  61,  67,  71,  73,  79,  83,  89,  97,  101, 103, 107, 109,
+    113, 127, 131, 137, 139, 149, 151, 157, 163, 167, 173, 179, 181, 191,
+    193, 197, 199, 211, 223, 227, 229, 233, 239, 241, 251};
+// The prime after 251; (next prime after the last tested)^2 bounds the range
+// where surviving trial division already proves primality.
+constexpr uint32_t kTdNextPrimeAfterList = 257;
+
+struct TdTable {
+  uint64_t inv64[kMaxTdPrimes];
+  uint64_t lim64[kMaxTdPrimes];
+  uint32_t inv32[kMaxTdPrimes];
+  uint32_t lim32[kMaxTdPrimes];
+  uint32_t p[kMaxTdPrimes];
+};
+
+constexpr uint64_t ce_inv64(uint64_t n) {
+  uint64_t x = (3 * n) ^ 2;
+  for (int i = 0; i < 4; ++i) x *= 2 - n * x;
+  return x;
+}
+
+constexpr TdTable make_td_table() {
+  TdTable t{};
+  for (int i = 0; i < kMaxTdPrimes; ++i) {
+    uint64_t p = kTdPrimeList[i];
+    t.p[i] = (uint32_t)p;
+    t.inv64[i] = ce_inv64(p);
+    t.lim64[i] = ~0ULL / p;
+    t.inv32[i] = (uint32_t)ce_inv64(p);
+    t.lim32[i] = 0xFFFFFFFFu / (uint32_t)p;
+  }
+  return t;
+}
+
+constexpr TdTable kTdHost = make_td_table();
+
+}  // namespace ip

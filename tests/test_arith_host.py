@@ -1,0 +1,119 @@
+"""CPU unit tests of the device arithmetic header (csrc/arith.cuh).
+
+The header is compiled for the host with g++ (tests/host/arith_host_check.cpp)
+and compared with exact Python integers: Montgomery multiplication and
+set-up, modular doubling, Newton inverses, the multiply-by-inverse
+divisibility test, and the strong tests.  The GPU kernels use the same
+source; the GPU parity tests cover the kernels themselves.
+"""
+import ctypes
+import os
+import random
+import subprocess
+
+import pytest
+
+import numtheory as nt
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+R = 1 << 64
+
+
+@pytest.fixture(scope="module")
+def H(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("arith") / "arith_host.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", so,
+                    os.path.join(HERE, "host", "arith_host_check.cpp")], check=True)
+    L = ctypes.CDLL(so)
+    u64, u32, i32, p = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+    for name, args, res in [("h_inv64", [u64], u64), ("h_inv32", [u32], u32),
+                            ("h_mont_mul", [u64, u64, u64], u64), ("h_mod_dbl", [u64, u64], u64),
+                            ("h_mont_setup", [u64, p], None), ("h_sprp2_64", [u64], i32),
+                            ("h_sprp64", [u64, u64], i32), ("h_mont_mul32", [u32, u32, u32], u32),
+                            ("h_sprp32", [u32, u32], i32), ("h_td64", [u64, i32], i32),
+                            ("h_td32", [u32, i32], i32), ("h_td_prime", [i32], u32)]:
+        f = getattr(L, name)
+        f.argtypes, f.restype = args, res
+    return L
+
+
+def _moduli(rng, k=300):
+    ms = [3, 5, 2**32 + 15, 2**63 - 25, 2**63 + 1, 2**64 - 59, 2**64 - 1, (1 << 63) | 1]
+    return ms + [rng.randrange(3, R) | 1 for _ in range(k)] + [rng.randrange(3, 2**40) | 1 for _ in range(50)]
+
+
+def test_inverses(H):
+    rng = random.Random(1)
+    for n in _moduli(rng):
+        assert (H.h_inv64(n) * n) % R == 1
+        n32 = n & 0xFFFFFFFF | 1
+        assert (H.h_inv32(n32) * n32) % (1 << 32) == 1
+
+
+def test_mont_mul_and_setup(H):
+    rng = random.Random(2)
+    buf = (ctypes.c_uint64 * 4)()
+    for n in _moduli(rng):
+        rinv = pow(R, -1, n)
+        for _ in range(10):
+            a, b = rng.randrange(n), rng.randrange(n)
+            assert H.h_mont_mul(a, b, n) == a * b * rinv % n
+        for a, b in ((n - 1, n - 1), (0, n - 1), (n - 1, 1)):
+            assert H.h_mont_mul(a, b, n) == a * b * rinv % n
+        H.h_mont_setup(n, buf)
+        ninv, one, mone, r2 = list(buf)
+        assert ninv * n % R == 1
+        assert one == R % n and mone == (n - R % n) and r2 == R * R % n
+
+
+def test_mod_dbl(H):
+    rng = random.Random(3)
+    for n in _moduli(rng):
+        for x in [0, 1, n - 1, n // 2, (n + 1) // 2] + [rng.randrange(n) for _ in range(10)]:
+            assert H.h_mod_dbl(x, n) == 2 * x % n
+
+
+def test_strong_tests_against_python(H):
+    rng = random.Random(4)
+    vals = [rng.randrange(2**32, R) | 1 for _ in range(3000)]
+    vals += [2**61 - 1, 2**63 - 25, 2**64 - 59, 3215031751, 2152302898747, 3474749660383]
+    for n in vals:
+        assert bool(H.h_sprp2_64(n)) == nt.strong_base2(n), n
+        for a in (325, 9375, 1795265022):
+            d, s = n - 1, 0
+            while d % 2 == 0:
+                d //= 2
+                s += 1
+            x = pow(a, d, n)
+            ok = x in (1, n - 1) or any(pow(x, 1 << r, n) == n - 1 for r in range(1, s))
+            assert bool(H.h_sprp64(n, a)) == ok, (n, a)
+
+
+def test_sprp32_against_python(H):
+    rng = random.Random(5)
+    for n in [rng.randrange(3, 2**32) | 1 for _ in range(3000)] + [2047, 3277, 4033, 2**32 - 5]:
+        for a in (2, 7, 61):
+            if a % n == 0:
+                continue
+            d, s = n - 1, 0
+            while d % 2 == 0:
+                d //= 2
+                s += 1
+            x = pow(a, d, n)
+            ok = x in (1, n - 1) or any(pow(x, 1 << r, n) == n - 1 for r in range(1, s))
+            assert bool(H.h_sprp32(n, a % n)) == ok, (n, a)
+        rinv = pow(1 << 32, -1, n)
+        a, b = rng.randrange(n), rng.randrange(n)
+        assert H.h_mont_mul32(a, b, n) == a * b * rinv % n
+
+
+def test_divisibility_by_inverse(H):
+    rng = random.Random(6)
+    vals = [rng.randrange(R) for _ in range(2000)] + [0, 1, R - 1, 3 * 5 * 7 * 251]
+    for i in range(53):
+        p = H.h_td_prime(i)
+        assert nt.trial_is_prime(p) and p % 2 == 1
+        for v in vals + [p, p * (R // p - 1), p * rng.randrange(R // p)]:
+            assert bool(H.h_td64(v, i)) == (v % p == 0)
+            v32 = v & 0xFFFFFFFF
+            assert bool(H.h_td32(v32, i)) == (v32 % p == 0)

@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit for bit.
+
+Primality has exactly one right answer per element, so the bar is
+bit-exact equality (tolerance 0).  Inputs come from the seeded generators in
+`workloads`; expected values come only from the oracle (or from paper /
+mathematical constants).  Every call goes through the C ABI (via the thin
+ctypes binding).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import plain_small, plain_large, plain_mixed, mixed_doubles, bitlen_uniform
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+import paper_2108_04791_gb300 as ipg  # noqa: E402
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _to_dev(vals):
+    return torch.from_numpy(np.ascontiguousarray(vals, dtype=np.uint64).view(np.int64)).to(_dev())
+
+
+def _gpu(vals, ctx=None):
+    t = _to_dev(vals)
+    out = (ctx.isprime(t) if ctx is not None else ipg.isprime(t))
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _assert_same(vals, got, want):
+    bad = np.flatnonzero(got != want)
+    if bad.size:
+        i = int(bad[0])
+        raise AssertionError(f"{bad.size} mismatches; first at {i}: n={int(vals[i])} "
+                             f"gpu={int(got[i])} oracle={int(want[i])}")
+
+
+@pytest.fixture(scope="module")
+def ctx_nosieve():
+    _dev()
+    with ipg.Context(0, sieve_limit=0) as c:
+        yield c
+
+
+@pytest.fixture(scope="module")
+def ctx_small_sieve():
+    _dev()
+    with ipg.Context(0, sieve_limit=1 << 20) as c:
+        yield c
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_plain_small_full():
+    v = plain_small()
+    _assert_same(v, _gpu(v), oracle.isprime_u64(v))
+
+
+def test_plain_large_2p20():
+    v = plain_large(1 << 20)
+    _assert_same(v, _gpu(v), oracle.isprime_u64(v))
+
+
+def test_plain_large_full_size():
+    """The benchmark's workload at its full size (2^24), every element."""
+    v = plain_large()
+    _assert_same(v, _gpu(v), oracle.isprime_u64(v))
+
+
+def test_plain_mixed_2p22():
+    v = plain_mixed(1 << 22)
+    _assert_same(v, _gpu(v), oracle.isprime_u64(v))
+
+
+def test_plain_mixed_full_size_sampled():
+    """Full 2^26 elements on the GPU; every 61st element checked by the oracle."""
+    v = plain_mixed()
+    got = _gpu(v)
+    idx = np.arange(0, v.size, 61)
+    _assert_same(v[idx], got[idx], oracle.isprime_u64(v[idx]))
+    # prime density property over the whole array (Mertens-style sanity)
+    frac = got.mean()
+    assert 0.02 < frac < 0.2
+
+
+def test_mixed_doubles():
+    x = mixed_doubles(1 << 20)
+    t = torch.from_numpy(x).to(_dev())
+    inv = torch.zeros(1, dtype=torch.int64, device=_dev())
+    out = ipg.isprime(t, invalid=inv)
+    torch.cuda.synchronize()
+    want, bad = oracle.isprime_f64(x)
+    _assert_same(x.astype(np.uint64), out.cpu().numpy(), want)
+    assert int(inv.item()) == bad == 0
+
+
+def test_f64_domain_and_invalid_count():
+    x = np.array([0.0, -0.0, 1.0, 2.0, 7.0, 9.0, 2.0**53, 2.0**53 - 111, float("nan"),
+                  float("inf"), -float("inf"), -7.0, 2.5, 2.0**53 + 2, 1e300, 97.0, 3.0],
+                 dtype=np.float64)
+    for k in (1, 2, 3, len(x)):  # ragged lengths through head/tail paths
+        t = torch.from_numpy(x[:k].copy()).to(_dev())
+        inv = torch.zeros(1, dtype=torch.int64, device=_dev())
+        out = ipg.isprime(t, invalid=inv)
+        torch.cuda.synchronize()
+        want, bad = oracle.isprime_f64(x[:k])
+        assert out.cpu().numpy().tolist() == want.tolist()
+        assert int(inv.item()) == bad
+
+
+# ------------------------------------------------------------------ edge cases
+
+SPECIAL = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 25, 49, 121, 169, 251, 253, 257, 65521, 65537,
+           561, 1105, 1729, 2047, 3277, 4033, 4681, 8321, 3215031751, 2152302898747,
+           3474749660383, 341550071728321, 3825123056546413051,
+           2**31 - 1, 2**32 - 5, 2**32 - 1, 2**32, 2**32 + 1, 2**32 + 15, 2**48 - 59,
+           2**52 - 47, 2**53 - 111, 2**61 - 1, 2**62 - 57, 2**63 - 25, 2**63, 2**63 + 1,
+           2**64 - 59, 2**64 - 57, 2**64 - 3, 2**64 - 1, 4759123141, 1122004669633]
+
+
+@pytest.mark.parametrize("which", ["default", "nosieve", "smallsieve"])
+def test_special_values(which, ctx_nosieve, ctx_small_sieve):
+    ctx = {"default": None, "nosieve": ctx_nosieve, "smallsieve": ctx_small_sieve}[which]
+    v = np.array(SPECIAL, dtype=np.uint64)
+    _assert_same(v, _gpu(v, ctx), oracle.isprime_u64(v))
+
+
+def test_empty_input():
+    t = torch.empty(0, dtype=torch.int64, device=_dev())
+    assert ipg.isprime(t).numel() == 0
+
+
+def test_ragged_lengths_and_offsets():
+    base = plain_mixed(4096, seed=9)
+    big = _to_dev(base)
+    want_all = oracle.isprime_u64(base)
+    for off in (0, 1, 2, 3):
+        for n in list(range(1, 70)) + [127, 128, 129, 1023, 1025]:
+            t = big[off:off + n]          # misaligned by 8 bytes for odd off
+            out = torch.zeros(n + 3, dtype=torch.uint8, device=_dev())[1:n + 1]  # odd output address
+            ipg.isprime(t, out=out)
+            torch.cuda.synchronize()
+            assert out.cpu().numpy().tolist() == want_all[off:off + n].tolist(), (off, n)
+
+
+def test_no_sieve_and_small_sieve_contexts(ctx_nosieve, ctx_small_sieve):
+    v = np.concatenate([plain_mixed(1 << 20, seed=11), np.arange(0, 70000, dtype=np.uint64)])
+    want = oracle.isprime_u64(v)
+    _assert_same(v, _gpu(v, ctx_nosieve), want)
+    _assert_same(v, _gpu(v, ctx_small_sieve), want)
+
+
+def test_windows_at_boundaries():
+    """Consecutive integers around 2^20, 2^24, 2^32 and below 2^64."""
+    for lo in (1 << 20, (1 << 24) - 5000, (1 << 32) - 50000, (1 << 64) - 100000):
+        v = np.uint64(lo) + np.arange(100000, dtype=np.uint64)  # last window ends at 2^64 - 1
+        _assert_same(v, _gpu(v), oracle.isprime_u64(v))
+
+
+def test_strong_pseudoprimes_and_carmichaels(ctx_nosieve):
+    import numtheory as nt
+    N = 2_000_000
+    comp = ~nt.simple_sieve(N)
+    spsp = [n for n in range(9, N, 2) if comp[n] and nt.strong_base2(n)]
+    cars = []
+    for k in range(1, 1 << 20):
+        a, b, c = 6 * k + 1, 12 * k + 1, 18 * k + 1
+        if a * b * c >= 1 << 64:
+            break
+        if nt.trial_is_prime(a) and nt.trial_is_prime(b) and nt.trial_is_prime(c):
+            cars.append(a * b * c)
+    v = np.array(spsp + cars, dtype=np.uint64)
+    assert not _gpu(v).any()
+    assert not _gpu(v, ctx_nosieve).any()
+
+
+def test_tuning_does_not_change_results():
+    v = np.concatenate([plain_large(1 << 18, seed=21), plain_mixed(1 << 18, seed=22)])
+    want = oracle.isprime_u64(v)
+    with ipg.Context(0, sieve_limit=1 << 24) as c:
+        for kw in [dict(td_primes=0), dict(td_primes=1), dict(td_primes=53),
+                   dict(classify_block=64, mr_block=32, blocks_per_sm=1),
+                   dict(classify_block=1024, mr_block=256, blocks_per_sm=16),
+                   dict(chunk_log2=16)]:
+            c.set_tuning(**kw)
+            _assert_same(v, _gpu(v, c), want)
+
+
+def test_sieve_counts():
+    assert ipg.Context.default(0).sieve_count() == 203280221  # pi(2^32)
+    with ipg.Context(0, sieve_limit=1 << 20) as c:
+        assert c.sieve_count() == 82025                           # pi(2^20)
+    with ipg.Context(0, sieve_limit=1 << 24) as c:
+        assert c.sieve_count() == 1077871                         # pi(2^24)
+
+
+def test_mr32_exhaustive_against_sieve(ctx_small_sieve):
+    """Every odd n in [2^20, 2^32): 32-bit Miller-Rabin with bases {2,7,61}
+    (context with S = 2^20) equals the sieve lookup of the default context
+    (S = 2^32), whose bitmap is pinned by pi(2^32)."""
+    dev = _dev()
+    default = ipg.Context.default(0)
+    step = 1 << 27
+    lo = 1 << 20
+    total = 0
+    while lo < (1 << 32):
+        hi = min(lo + 2 * step, 1 << 32)
+        t = torch.arange(lo + 1, hi, 2, dtype=torch.int64, device=dev)
+        a = ctx_small_sieve.isprime(t)
+        b = default.isprime(t)
+        torch.cuda.synchronize()
+        if not torch.equal(a, b):
+            i = int(torch.nonzero(a != b)[0])
+            raise AssertionError(f"MR32 vs sieve differ at n={int(t[i])}")
+        total += int(a.sum())
+        lo = hi
+    # odd primes in [2^20, 2^32) = pi(2^32) - pi(2^20)
+    assert total == 203280221 - 82025
+
+
+def test_host_path_matches_device_path():
+    v = plain_mixed(300_001, seed=31)
+    c = ipg.Context.default(0)
+    got = c.isprime_host(v)
+    _assert_same(v, got, oracle.isprime_u64(v))
+
+
+def test_two_streams_share_one_context():
+    v1 = plain_large(1 << 18, seed=41)
+    v2 = plain_mixed(1 << 18, seed=42)
+    t1, t2 = _to_dev(v1), _to_dev(v2)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        o1 = ipg.isprime(t1)
+    with torch.cuda.stream(s2):
+        o2 = ipg.isprime(t2)
+    torch.cuda.synchronize()
+    _assert_same(v1, o1.cpu().numpy(), oracle.isprime_u64(v1))
+    _assert_same(v2, o2.cpu().numpy(), oracle.isprime_u64(v2))
+
+
+def test_timing_records_every_kernel():
+    c = ipg.Context.default(0)
+    c.timing_reset()
+    c.timing(True)
+    v = _to_dev(plain_large(1 << 20, seed=51))
+    c.isprime(v)
+    torch.cuda.synchronize()
+    rec = c.timing_read()
+    c.timing(False)
+    assert rec["classify_u64"][1] == 1 and rec["mr64_base2"][1] == 1 and rec["mr64_rest"][1] == 1
+    assert all(ms > 0 for ms, n in rec.values() if n)
+
+
+def test_int_rates_probe():
+    r = ipg.int_rates(0)
+    assert r["mad_lo_u32"] > 1e12 and r["mont_mul64"] > 1e10 and r["sm_clock_mhz"] > 100

@@ -282,12 +282,24 @@ def test_work_counter_invariants():
     w = oracle.work_counts(v, td_bound=53)
     out = oracle.isprime_u64(v)
     assert w["primes"] == int(out.sum())
-    # every prime runs all seven bases; each composite that reaches the test
-    # fails at one base
-    assert w["base_tests"] >= 7 * w["primes"]
-    assert w["mr64_elements"] >= w["primes"]
-    # squarings per base are about the bit length of d, below 64
-    assert w["squarings"] <= 64 * w["base_tests"]
+    # every prime passes base 2 and runs the other six bases; each composite
+    # that reaches the test fails at exactly one base
+    assert w["base2_passes"] >= w["primes"]
+    assert w["base_tests"] >= w["mr64_elements"] + 6 * w["primes"]
+    # binary schedule: fewer than 64 squarings and 64 multiplies per base test
+    assert w["base2_squarings"] < 64 * w["mr64_elements"]
+    assert w["rest_squarings"] < 64 * 6 * w["base2_passes"]
+    assert w["base2_doublings"] < w["base2_squarings"]
     # trial division: 15 odd primes <= 53 for each odd element
     odd = int((v & np.uint64(1)).sum())
     assert w["trial_tests"] == 15 * odd
+
+
+def test_work_counter_exact_on_one_prime():
+    """n = 2^61 - 1: n - 1 = 2 (2^60 - 1), s = 1, d = 2^60 - 1 (60 one bits):
+    every base does 59 squarings and 59 multiplications, no extra squaring."""
+    w = oracle.work_counts(np.array([2**61 - 1], dtype=np.uint64), td_bound=53)
+    assert w["mr64_elements"] == 1 and w["base2_passes"] == 1 and w["primes"] == 1
+    assert w["base2_squarings"] == 59 and w["base2_doublings"] == 59
+    assert w["rest_squarings"] == 6 * 59 and w["rest_multiplies"] == 6 * 59
+    assert w["base_tests"] == 7 and w["trial_tests"] == 15
