@@ -21,6 +21,8 @@ __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t* sink, uint32_t 
     b[k] = seed ^ (k * 0x9E3779B9u);
   }
   const uint32_t m = seed | 1u;
+  unsigned long long g0, g1;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g0));
   long long t0 = clock64();
   for (int it = 0; it < kIters; ++it) {
 #pragma unroll
@@ -42,11 +44,16 @@ __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t* sink, uint32_t 
     }
   }
   long long t1 = clock64();
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g1));
   uint32_t acc = 0;
 #pragma unroll
   for (int k = 0; k < kChains; ++k) acc ^= a[k] ^ b[k];
   if (acc == 0x12345678u) sink[0] = acc;  // keeps the chains live
-  if (blockIdx.x == 0 && threadIdx.x == 0) *cycles = (unsigned long long)(t1 - t0);
+  // SM clock of this block's SM while it ran: cycles over global nanoseconds
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cycles[0] = (unsigned long long)(t1 - t0);
+    cycles[1] = g1 - g0;
+  }
 }
 
 __global__ void __launch_bounds__(256) mont_rate_kernel(uint64_t* sink, uint64_t seed) {
@@ -79,7 +86,7 @@ int measure_int_rates(int device, isprime_int_rates* out) {
   uint32_t* sink = nullptr;
   unsigned long long* d_cyc = nullptr;
   IP_CUDA(cudaMalloc(&sink, 64));
-  IP_CUDA(cudaMalloc(&d_cyc, sizeof(unsigned long long)));
+  IP_CUDA(cudaMalloc(&d_cyc, 2 * sizeof(unsigned long long)));
   cudaEvent_t e0, e1;
   IP_CUDA(cudaEventCreate(&e0));
   IP_CUDA(cudaEventCreate(&e1));
@@ -101,9 +108,9 @@ int measure_int_rates(int device, isprime_int_rates* out) {
       if (ms < best) {
         best = ms;
         if (op == 0) {
-          unsigned long long cyc = 0;
-          IP_CUDA(cudaMemcpy(&cyc, d_cyc, sizeof cyc, cudaMemcpyDeviceToHost));
-          mhz = (double)cyc / (ms * 1e3);  // cycles of one block over the kernel time
+          unsigned long long cyc[2] = {0, 0};
+          IP_CUDA(cudaMemcpy(cyc, d_cyc, sizeof cyc, cudaMemcpyDeviceToHost));
+          mhz = cyc[1] ? 1e3 * (double)cyc[0] / (double)cyc[1] : 0.0;
         }
       }
     }
