@@ -121,6 +121,23 @@ int isprime_f64_ctx(isprime_ctx *ctx, const double *d_in, uint8_t *d_out, size_t
 int isprime_u64_host(isprime_ctx *ctx, const uint64_t *h_in, uint8_t *h_out, size_t n,
                      isprime_stream stream);
 
+/* Allocation-free variant of isprime_u64 (the paper has no counterpart;
+ * this exists for callers that cannot allocate device memory when they need
+ * the test -- e.g. code running under an allocator that owns all device
+ * memory, or a hook that must not take the driver's allocation lock).
+ * Same inputs, outputs and results as isprime_u64, but the work queues live
+ * in one fixed array of ISPRIME_NOALLOC_SCRATCH_BYTES of device memory that
+ * is part of the library image (every GPU that loads the library holds it
+ * until exit); no sieve is used.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.  n > ISPRIME_NOALLOC_MAX_ELEMS gives ISPRIME_EINVAL.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on a device share the array: calls whose GPU work
+ * overlaps race, so the caller must order them (one stream, or events). */
+#define ISPRIME_NOALLOC_MAX_ELEMS ((size_t)1 << 20)
+#define ISPRIME_NOALLOC_SCRATCH_BYTES ((size_t)24 * ((size_t)1 << 20) + 256)
+int isprime_u64_noalloc(const uint64_t *d_in, uint8_t *d_out, size_t n, isprime_stream stream);
+
 /* Number of primes below the context's sieve limit S, counted on the device
  * from the resident bitmap (pi(S); 0 when S == 0).  Synchronous. */
 int isprime_sieve_count(isprime_ctx *ctx, uint64_t *out);

@@ -205,6 +205,14 @@ int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s)
   return launch_classify<double>(ctx, a, s, ISPRIME_K_CLASSIFY_F64, "classify_kernel<f64>");
 }
 
+// Launch without a context (explicit grid and block); used by the
+// allocation-free entry point.
+int launch_classify_u64_raw(const ClassifyArgs& a, unsigned grid, unsigned block, cudaStream_t s) {
+  classify_kernel<uint64_t><<<grid, block, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "classify_kernel<u64>");
+}
+
 uint64_t td_square_for(uint32_t ntd) {
   const uint64_t next = ntd < (uint32_t)kMaxTdPrimes ? kTdPrimeList[ntd] : kTdNextPrimeAfterList;
   return next * next;

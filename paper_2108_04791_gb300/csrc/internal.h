@@ -104,6 +104,11 @@ int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s)
 // mr.cu
 int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s);
 
+// Context-free launchers (explicit launch shape), used by noalloc.cu.
+int launch_classify_u64_raw(const ClassifyArgs& a, unsigned grid, unsigned block, cudaStream_t s);
+int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, unsigned block,
+                  cudaStream_t s);
+
 // probe.cu
 int measure_int_rates(int device, isprime_int_rates* out);
 

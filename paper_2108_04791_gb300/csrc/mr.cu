@@ -161,4 +161,16 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
   return launch_end(ctx, s, &tl, "mr64_rest_kernel");
 }
 
+// Launch without a context (explicit grid and block and queue pointers);
+// used by the allocation-free entry point.
+int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, unsigned block,
+                  cudaStream_t s) {
+  if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
+  mr64_base2_kernel<<<grid, block, 0, s>>>(q.q64_n, q.counters, q.q64b);
+  const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
+  mr64_rest_kernel<<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
+}
+
 }  // namespace ip
