@@ -69,9 +69,11 @@ def _parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--workload", default="plain_large",
-                   choices=["plain_large", "plain_small", "plain_mixed"])
+                   choices=["plain_large", "plain_small", "plain_mixed", "batched"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-probe", action="store_true", help="skip the integer-rate probe")
+    p.add_argument("--tune", default="", help="tuning overrides, e.g. mont_impl=1,td_primes=24")
     return p.parse_args()
 
 
@@ -241,6 +243,8 @@ def run_mine(args, world, rank, local):
     d_in = torch.from_numpy(vals.view(np.int64)).to(dev)
     out = torch.empty(n, dtype=torch.uint8, device=dev)
     ctx = ipg.Context.default(local)              # builds the resident sieve (untimed)
+    if args.tune:
+        ctx.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
 
@@ -280,10 +284,8 @@ def run_mine(args, world, rank, local):
     dom_ms, dom_launches = ktimes[dom]
     roof = None
     imad_rate = None
-    try:
+    if not args.no_probe:
         imad_rate = ipg.int_rates(local)
-    except Exception:  # noqa: BLE001
-        imad_rate = None
     peak_ops = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6
     if args.workload == "plain_large":
         w = WORK_PLAIN_LARGE
@@ -339,7 +341,75 @@ def run_mine(args, world, rank, local):
                        "parallelism": f"dp{world} (independent shards)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "kernels": kernels,
+            "tuning": ctx.tuning.as_dict(),
             "wall_s_timed_region": wall, "int_rates": imad_rate,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_batched(args, world, rank, local):
+    """4096 ragged arrays (log-uniform sizes 1..2^20, 25% primes near 2^64,
+    10% semiprimes) classified by one batched launch per step, against the
+    same arrays through one plain call each."""
+    import torch
+    import paper_2108_04791_gb300 as ipg
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    from workloads import torch_gen
+    d_all, offs = torch_gen.batched_arrays(n_arrays=4096, max_size=1 << 20, seed=3 + 1000 * rank,
+                                           device=dev)
+    n = d_all.numel()
+    out_all = torch.empty(n, dtype=torch.uint8, device=dev)
+    ins = [d_all[offs[i]:offs[i + 1]] for i in range(len(offs) - 1)]
+    outs = [out_all[offs[i]:offs[i + 1]] for i in range(len(offs) - 1)]
+    ctx = ipg.Context.default(local)
+    if args.tune:
+        ctx.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
+    stream = torch.cuda.current_stream(dev)
+    steps, warm = max(args.steps, 1), max(args.warmup, 3)
+
+    def timed(fn, k):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        _barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return _max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+
+    launches0 = ctx.stats()["kernel_launches"]
+    ctx.timing_reset()
+    ctx.timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_batch = timed(lambda: ctx.isprime_batched(ins, outs), steps)
+    clk = clocks.stop()
+    ctx.timing(False)
+    launches = ctx.stats()["kernel_launches"] - launches0
+    kt = ctx.timing_read()
+    k_plain = max(1, min(steps, 3))
+    t_plain = timed(lambda: [ctx.isprime(x, out=o) for x, o in zip(ins, outs)], k_plain)
+    value = n * world * steps / t_batch
+    plain_value = n * world * k_plain / t_plain
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": 1e3 * t_batch / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched", "arrays": len(ins), "elements": int(n),
+                       "description": wg.WORKLOADS["batched"], "launch": "one CUDA-graph replay per step"},
+            "plain_per_call": {"value": plain_value, "unit": UNIT, "steps": k_plain,
+                               "calls_per_step": len(ins)},
+            "speedup_vs_plain_calls": value / plain_value,
+            "gpu_launches": launches, "clocks": clk,
+            "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]} for k, v in kt.items() if v[1]},
+            "tuning": ctx.tuning.as_dict(),
         }
         print(json.dumps(line), flush=True)
 
@@ -349,6 +419,8 @@ def main():
     world, rank, local = _dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
     else:
         run_mine(args, world, rank, local)
     if world > 1:

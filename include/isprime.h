@@ -60,6 +60,15 @@ typedef struct {
   uint32_t blocks_per_sm;  /* grid = SMs x blocks_per_sm for grid-stride kernels (1..32) */
   uint32_t td_primes;      /* odd primes 3, 5, 7, ... used for trial division (0..53) */
   uint32_t chunk_log2;     /* elements per internal chunk = 2^chunk_log2 (16..28) */
+  uint32_t mont_impl;      /* 64-bit Montgomery formulation of the six-base kernel: 0 128-bit
+                              product (squaring with one cross product), 1 word-level, 2 128-bit
+                              product with PTX word-level reduction, 3 fused product scanning,
+                              4 128-bit multiply with fused squaring, 5 128-bit product with
+                              squaring as a general multiply */
+  uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..5) */
+  uint32_t batch_block;    /* threads per block of the batched kernel (64..256, multiple of 32) */
+  uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */
+  uint32_t batch_blocks_per_sm; /* cap on resident batched blocks per SM (0 = occupancy limit) */
   uint32_t reserved[3];
 } isprime_tuning;
 
@@ -114,6 +123,39 @@ int isprime_f64(const double *d_in, uint8_t *d_out, size_t n, unsigned long long
 int isprime_f64_ctx(isprime_ctx *ctx, const double *d_in, uint8_t *d_out, size_t n,
                     unsigned long long *d_invalid, isprime_stream stream);
 
+/* One array of a batch: n values at d_in (8-byte aligned), n bytes at d_out. */
+typedef struct {
+  const uint64_t *d_in;
+  uint8_t *d_out;
+  uint64_t n;
+} isprime_array;
+
+/* Batched form: classifies every array of `arrays` (a host array of
+ * n_arrays descriptors) in one persistent kernel launch, replayed from a
+ * CUDA graph that the context records on first use.  Results are identical
+ * to calling isprime_u64_ctx on each array.  Arrays may have any lengths
+ * (including 0); no array's output may overlap any array's input or output.
+ * Asynchronous on `stream`; the descriptors are copied before return. */
+int isprime_u64_batched(isprime_ctx *ctx, const isprime_array *arrays, size_t n_arrays,
+                        isprime_stream stream);
+
+/* Autotuner: chooses the context's tuning (every field that affects only
+ * speed) by timing the caller's device sample d_sample (n values) on this
+ * GPU; d_scratch_out is n bytes of device memory for the outputs.  mode
+ * ISPRIME_TUNE_PLAIN tunes isprime_u64_ctx, ISPRIME_TUNE_BATCHED tunes
+ * isprime_u64_batched (the sample is cut into ragged arrays).  Coordinate
+ * descent over candidate values, best of three timed runs per candidate.
+ * If cache_path is not NULL and holds a result for this GPU, runtime
+ * version, sample size and mode, that result is installed without timing;
+ * otherwise the result is appended to the file.  *out (nullable) receives
+ * the installed tuning.  Synchronous. */
+#define ISPRIME_TUNE_PLAIN 0
+#define ISPRIME_TUNE_BATCHED 1
+int isprime_autotune(isprime_ctx *ctx, const uint64_t *d_sample, uint8_t *d_scratch_out, size_t n,
+                     int mode, const char *cache_path, isprime_tuning *out);
+/* Writes "field=value,..." for every tuning field into buf (cap bytes). */
+int isprime_tuning_format(const isprime_tuning *t, char *buf, size_t cap);
+
 /* End-to-end form for host buffers: copies h_in to the device in chunks
  * (through the context's pinned staging buffers), classifies, copies the
  * bytes back into h_out and synchronises `stream` before returning.  h_in and
@@ -154,7 +196,8 @@ enum {
   ISPRIME_K_MR64_REST = 5,
   ISPRIME_K_MR32 = 6,
   ISPRIME_K_SIEVE_COUNT = 7,
-  ISPRIME_K_COUNT = 8
+  ISPRIME_K_BATCHED = 8,
+  ISPRIME_K_COUNT = 9
 };
 
 typedef struct {
@@ -179,7 +222,16 @@ typedef struct {
   double mad_lo_u32;     /* mad.lo.u32 */
   double mad_hi_u32;     /* mad.hi.u32 */
   double mad_wide_u32;   /* mad.wide.u32 (32x32+64 -> 64) */
-  double mont_mul64;     /* complete 64-bit Montgomery multiplications */
+  /* 64-bit Montgomery operations per second, by formulation:
+   * [0] multiply, 128-bit product and hi(ab) - hi(mn) REDC
+   * [1] multiply, word-level REDC with wide multiply-adds
+   * [2] squaring, word-level
+   * [3] squaring, 128-bit form with one cross product
+   * [4] multiply, 128-bit product with a word-level REDC in PTX carry chains
+   * [5] squaring as a general multiply of [0]
+   * [6] multiply, fused product-scanning form (wide multiply-adds carry all carries)
+   * [7] squaring, fused form */
+  double mont_variant[8];
   double sm_clock_mhz;
 } isprime_int_rates;
 int isprime_measure_int_rates(int device, isprime_int_rates *out);

@@ -28,7 +28,7 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ETIMEDOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6
 SIEVE_DEFAULT = (1 << 64) - 1
 KERNEL_NAMES = ["sieve_base", "sieve_segment", "classify_u64", "classify_f64",
-                "mr64_base2", "mr64_rest", "mr32", "sieve_count"]
+                "mr64_base2", "mr64_rest", "mr32", "sieve_count", "batched"]
 
 
 class IsPrimeError(RuntimeError):
@@ -40,10 +40,17 @@ class IsPrimeError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("classify_block", ctypes.c_uint32), ("mr_block", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("td_primes", ctypes.c_uint32),
-                ("chunk_log2", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("chunk_log2", ctypes.c_uint32), ("mont_impl", ctypes.c_uint32),
+                ("mont_impl_base2", ctypes.c_uint32), ("batch_block", ctypes.c_uint32),
+                ("batch_tile_log2", ctypes.c_uint32), ("batch_blocks_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class ArrayDesc(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("n", ctypes.c_uint64)]
 
 
 class _Stats(ctypes.Structure):
@@ -58,7 +65,7 @@ class _KTime(ctypes.Structure):
 
 class _IntRates(ctypes.Structure):
     _fields_ = [("mad_lo_u32", ctypes.c_double), ("mad_hi_u32", ctypes.c_double),
-                ("mad_wide_u32", ctypes.c_double), ("mont_mul64", ctypes.c_double),
+                ("mad_wide_u32", ctypes.c_double), ("mont_variant", ctypes.c_double * 8),
                 ("sm_clock_mhz", ctypes.c_double)]
 
 
@@ -90,6 +97,9 @@ def lib():
                 "isprime_f64": ([vp, vp, sz, vp, vp], i32),
                 "isprime_f64_ctx": ([vp, vp, vp, sz, vp, vp], i32),
                 "isprime_u64_host": ([vp, vp, vp, sz, vp], i32),
+                "isprime_u64_batched": ([vp, ctypes.POINTER(ArrayDesc), sz, vp], i32),
+                "isprime_autotune": ([vp, vp, vp, sz, i32, ctypes.c_char_p, ctypes.POINTER(Tuning)], i32),
+                "isprime_tuning_format": ([ctypes.POINTER(Tuning), ctypes.c_char_p, sz], i32),
                 "isprime_sieve_count": ([vp, ctypes.POINTER(u64)], i32),
                 "isprime_timing_enable": ([vp, i32], i32),
                 "isprime_timing_read": ([vp, ctypes.POINTER(_KTime), i32], i32),
@@ -244,6 +254,41 @@ class Context:
             _check(L.isprime_f64_ctx(self._h, src.data_ptr(), out.data_ptr(), n, inv, sh))
         return out
 
+    def autotune(self, sample, mode: str = "plain", cache_path: str | None = None) -> dict:
+        """Times `sample` (a CUDA integer tensor) under candidate tunings and
+        installs the fastest (see isprime_autotune)."""
+        torch = _torch()
+        src, kind = _prep(sample)
+        out = torch.empty(src.numel(), dtype=torch.uint8, device=src.device)
+        t = Tuning()
+        m = {"plain": 0, "batched": 1}[mode]
+        _check(lib().isprime_autotune(self._h, src.data_ptr(), out.data_ptr(), src.numel(), m,
+                                      cache_path.encode() if cache_path else None, ctypes.byref(t)))
+        return t.as_dict()
+
+    def isprime_batched(self, tensors, outs=None, stream=None):
+        """Classifies a list of CUDA tensors (any lengths) in one batched
+        launch; returns the list of uint8 outputs."""
+        torch = _torch()
+        srcs = []
+        for t in tensors:
+            src, kind = _prep(t)
+            if kind != "u64":
+                raise TypeError("the batched form takes integer tensors")
+            srcs.append(src)
+        if outs is None:
+            outs = [torch.empty(s.shape, dtype=torch.uint8, device=s.device) for s in srcs]
+        descs = (ArrayDesc * max(len(srcs), 1))()
+        for i, (s_, o) in enumerate(zip(srcs, outs)):
+            descs[i].d_in = s_.data_ptr() if s_.numel() else None
+            descs[i].d_out = o.data_ptr() if o.numel() else None
+            descs[i].n = s_.numel()
+        if srcs:
+            sh = _stream_handle(srcs[0], stream)
+            _check(lib().isprime_u64_batched(self._h, descs, len(srcs), sh))
+        self._keep = srcs  # keep converted inputs alive until the stream runs them
+        return outs
+
     def isprime_host(self, values, stream=None) -> np.ndarray:
         """End-to-end call on a host array (copies in, classifies, copies out)."""
         a = np.ascontiguousarray(values, dtype=np.uint64)
@@ -276,4 +321,9 @@ def isprime_host(values, device: int = 0) -> np.ndarray:
 def int_rates(device: int = 0) -> dict:
     r = _IntRates()
     _check(lib().isprime_measure_int_rates(device, ctypes.byref(r)))
-    return {k: getattr(r, k) for k, _ in r._fields_}
+    out = {k: getattr(r, k) for k, _ in r._fields_ if k != "mont_variant"}
+    names = ["mul_128", "mul_word", "sqr_word", "sqr_128", "mul_128_ptxredc", "sqr_as_mul_128",
+             "mul_fused", "sqr_fused"]
+    for i, nm in enumerate(names):
+        out["mont_" + nm] = r.mont_variant[i]
+    return out

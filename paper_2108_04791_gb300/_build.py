@@ -23,7 +23,8 @@ OBJ_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-O2,-Wall", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["api.cu", "sieve.cu", "classify.cu", "mr.cu", "probe.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "sieve.cu", "classify.cu", "mr.cu", "probe.cu", "noalloc.cu", "batched.cu",
+           "autotune.cu"]
 
 
 def nvcc() -> str:

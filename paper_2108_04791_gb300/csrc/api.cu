@@ -75,9 +75,14 @@ static isprime_tuning default_tuning() {
   isprime_tuning t{};
   t.classify_block = 256;
   t.mr_block = 128;
-  t.blocks_per_sm = 8;
+  t.blocks_per_sm = 16;
   t.td_primes = 15;  // 3..53
   t.chunk_log2 = 24;
+  t.mont_impl = 0;
+  t.mont_impl_base2 = 5;
+  t.batch_block = 128;
+  t.batch_tile_log2 = 10;
+  t.batch_blocks_per_sm = 0;
   return t;
 }
 
@@ -88,6 +93,11 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.blocks_per_sm < 1 || t.blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "blocks_per_sm must be in [1, 32]");
   if (t.td_primes > 53) return set_error(ISPRIME_EINVAL, "td_primes must be in [0, 53]");
   if (t.chunk_log2 < 16 || t.chunk_log2 > 28) return set_error(ISPRIME_EINVAL, "chunk_log2 must be in [16, 28]");
+  if (t.mont_impl > 5) return set_error(ISPRIME_EINVAL, "mont_impl must be in [0, 5]");
+  if (t.mont_impl_base2 > 5) return set_error(ISPRIME_EINVAL, "mont_impl_base2 must be in [0, 5]");
+  if (bad_block(t.batch_block, 256)) return set_error(ISPRIME_EINVAL, "batch_block must be a multiple of 32 in [32, 256]");
+  if (t.batch_tile_log2 < 8 || t.batch_tile_log2 > 14) return set_error(ISPRIME_EINVAL, "batch_tile_log2 must be in [8, 14]");
+  if (t.batch_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "batch_blocks_per_sm must be in [0, 32]");
   return ISPRIME_OK;
 }
 
@@ -147,6 +157,7 @@ static int ctx_create(int device, uint64_t sieve_limit, isprime_ctx** out) {
   std::unique_ptr<isprime_ctx> ctx(new isprime_ctx());
   ctx->device = device;
   IP_CUDA(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+  IP_CUDA(cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   ctx->tune = default_tuning();
   ctx->sieve_limit = sieve_limit;
   IP_CUDA(cudaEventCreateWithFlags(&ctx->order_ev, cudaEventDisableTiming));
@@ -287,9 +298,16 @@ int isprime_ctx_destroy(isprime_ctx* ctx) {
     if (ctx->h_pin_in) cudaFreeHost(ctx->h_pin_in);
     if (ctx->h_pin_out) cudaFreeHost(ctx->h_pin_out);
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+    if (ctx->batch_ev) cudaEventDestroy(ctx->batch_ev);
+    cudaFree(ctx->d_batch);
+    if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
+    cudaFree(ctx->d_tile_counter);
     for (auto e : ctx->stage_ev)
       if (e) cudaEventDestroy(e);
-    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->host_last) cudaEventDestroy(ctx->host_last);
+    if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+    if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
   }
   for (int d = 0; d < 64; ++d) {
@@ -315,6 +333,11 @@ int isprime_ctx_set_tuning(isprime_ctx* ctx, const isprime_tuning* t) {
   if (!ctx || !t) return set_error(ISPRIME_EINVAL, "NULL argument");
   int st = check_tuning(*t);
   if (st) return st;
+  const size_t smem = batched_smem_bytes(t->batch_block, 1u << t->batch_tile_log2);
+  if (smem > (size_t)ctx->smem_optin)
+    return set_error(ISPRIME_EINVAL, "batch_block and batch_tile_log2 need " + std::to_string(smem) +
+                                         " bytes of shared memory per block; this GPU allows " +
+                                         std::to_string(ctx->smem_optin));
   std::lock_guard<std::mutex> lock(ctx->mu);
   ctx->tune = *t;
   return ISPRIME_OK;
@@ -361,6 +384,26 @@ int isprime_f64(const double* d_in, uint8_t* d_out, size_t n, unsigned long long
   return run_array<true>(ctx, d_in, d_out, n, d_invalid, (cudaStream_t)stream);
 }
 
+int isprime_u64_batched(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays,
+                        isprime_stream stream) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  if (n_arrays == 0) return ISPRIME_OK;
+  if (!arrays) return set_error(ISPRIME_EINVAL, "arrays is NULL");
+  for (size_t i = 0; i < n_arrays; ++i) {
+    int st = check_array_args(arrays[i].d_in, arrays[i].d_out, arrays[i].n, 8);
+    if (st) return set_error(st, "array " + std::to_string(i) + ": " + t_last_error);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard g(ctx->device);
+  int st = order_before(ctx, s);
+  if (st) return st;
+  if ((st = batched_run(ctx, arrays, n_arrays, s))) return st;
+  if ((st = order_after(ctx, s))) return st;
+  ctx->stats.calls++;
+  return ISPRIME_OK;
+}
+
 int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n,
                      isprime_stream stream) {
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
@@ -370,10 +413,19 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
   cudaStream_t s = (cudaStream_t)stream;
   std::lock_guard<std::mutex> host_lock(ctx->host_mu);
   DeviceGuard g(ctx->device);
-  const size_t chunk = (size_t)1 << ctx->tune.chunk_log2;
-  const size_t stage = std::min(chunk, std::max(n, (size_t)1 << 16));
+  // Pipeline: chunk k is copied in on copy_in, classified on `stream`, and
+  // copied out on copy_out, through staging slot k % 2, so the copy-in of
+  // chunk k+1 and the copy-out of chunk k-1 overlap the kernels of chunk k.
+  const size_t step_max = std::min((size_t)1 << ctx->tune.chunk_log2, (size_t)1 << 22);
+  const size_t stage = std::min(step_max, n);
   {
     std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!ctx->copy_in) {
+      IP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
+      IP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
+      for (auto& e : ctx->stage_ev) IP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      IP_CUDA(cudaEventCreateWithFlags(&ctx->host_last, cudaEventDisableTiming));
+    }
     if (ctx->stage_elems < stage) {
       if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
       cudaFree(ctx->d_stage_in);
@@ -386,18 +438,30 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
       ctx->stage_elems = stage;
     }
   }
-  // Two staging slots: the copy-in of chunk k+1 overlaps the kernels of chunk
-  // k (stream order keeps each slot's reuse safe).
-  const size_t step = ctx->stage_elems;
-  st = ISPRIME_OK;
+  const size_t step = std::min(ctx->stage_elems, step_max);
+  cudaEvent_t* in_ready = &ctx->stage_ev[0];   // [2] copy-in of a slot finished
+  cudaEvent_t* comp_done = &ctx->stage_ev[2];  // [2] kernels reading/writing a slot finished
+  cudaEvent_t* out_done = &ctx->stage_ev[4];   // [2] copy-out of a slot finished
+  // The slots may still be in use by a previous call's last chunks.
+  IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->host_last, 0));
   for (size_t off = 0, k = 0; off < n; off += step, ++k) {
     const size_t len = std::min(step, n - off);
-    uint64_t* din = ctx->d_stage_in + (k & 1) * step;
-    uint8_t* dout = ctx->d_stage_out + (k & 1) * step;
-    IP_CUDA(cudaMemcpyAsync(din, h_in + off, len * 8, cudaMemcpyHostToDevice, s));
+    const int slot = (int)(k & 1);
+    uint64_t* din = ctx->d_stage_in + slot * step;
+    uint8_t* dout = ctx->d_stage_out + slot * step;
+    if (k >= 2) IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, comp_done[slot], 0));
+    IP_CUDA(cudaMemcpyAsync(din, h_in + off, len * 8, cudaMemcpyHostToDevice, ctx->copy_in));
+    IP_CUDA(cudaEventRecord(in_ready[slot], ctx->copy_in));
+    IP_CUDA(cudaStreamWaitEvent(s, in_ready[slot], 0));
+    if (k >= 2) IP_CUDA(cudaStreamWaitEvent(s, out_done[slot], 0));
     if ((st = run_array<false>(ctx, din, dout, len, nullptr, s))) return st;
-    IP_CUDA(cudaMemcpyAsync(h_out + off, dout, len, cudaMemcpyDeviceToHost, s));
+    IP_CUDA(cudaEventRecord(comp_done[slot], s));
+    IP_CUDA(cudaStreamWaitEvent(ctx->copy_out, comp_done[slot], 0));
+    IP_CUDA(cudaMemcpyAsync(h_out + off, dout, len, cudaMemcpyDeviceToHost, ctx->copy_out));
+    IP_CUDA(cudaEventRecord(out_done[slot], ctx->copy_out));
   }
+  IP_CUDA(cudaEventRecord(ctx->host_last, ctx->copy_out));
+  IP_CUDA(cudaStreamSynchronize(ctx->copy_out));
   IP_CUDA(cudaStreamSynchronize(s));
   return ISPRIME_OK;
 }

@@ -93,7 +93,8 @@ IP_HD uint32_t inv32(uint32_t n) {
 // ---------------------------------------------------------------------------
 struct Mont64 {
   uint64_t n;     // modulus (odd)
-  uint64_t ninv;  // n^-1 mod 2^64
+  uint64_t ninv;  // n^-1 mod 2^64 (128-bit-product REDC)
+  uint32_t q;     // -n^-1 mod 2^32 (word-level REDC)
   uint64_t one;   // R mod n      (Montgomery form of 1)
   uint64_t mone;  // n - one      (Montgomery form of n-1)
 };
@@ -113,6 +114,175 @@ IP_HD uint64_t mont_sqr(uint64_t a, uint64_t n, uint64_t ninv) {
   return mont_mul(a, a, n, ninv);
 }
 
+// Squaring in the same 128-bit form with the cross product computed once:
+// a^2 = a0^2 + 2 a0 a1 2^32 + a1^2 2^64 (three wide products instead of
+// four); the REDC is the one of mont_mul.
+IP_HD uint64_t mont_sqr_h(uint64_t a, uint64_t n, uint64_t ninv) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+  const uint64_t L = (uint64_t)a0 * a0;
+  const uint64_t X = (uint64_t)a0 * a1;
+  const uint64_t Y = (uint64_t)a1 * a1;
+  const uint64_t lo = L + (X << 33);
+  const uint64_t hi = Y + (X >> 31) + (lo < L);
+  const uint64_t m = lo * ninv;
+  const uint64_t mh = mulhi64(m, n);
+  const uint64_t r = hi - mh;
+  return (hi < mh) ? r + n : r;
+}
+
+#if defined(__CUDACC__)
+// The 128-bit form with the REDC done word by word in PTX carry chains:
+// t = a*b from the compiler's 64-bit products, then two rounds of
+// m = t_i q mod 2^32, t += m n 2^(32 i) (q = -n^-1 mod 2^32).
+__device__ __forceinline__ uint64_t mont_mul_p(uint64_t a, uint64_t b, uint64_t n, uint32_t q) {
+  const uint64_t lo = a * b;
+  const uint64_t hi = __umul64hi(a, b);
+  uint32_t t0 = (uint32_t)lo, t1 = (uint32_t)(lo >> 32), t2 = (uint32_t)hi, t3 = (uint32_t)(hi >> 32);
+  uint32_t t4, m;
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  asm("mul.lo.u32      %5, %0, %8;\n\t"
+      "mad.lo.cc.u32   %0, %5, %6, %0;\n\t"
+      "madc.lo.cc.u32  %1, %5, %7, %1;\n\t"
+      "addc.cc.u32     %2, %2, 0;\n\t"
+      "addc.cc.u32     %3, %3, 0;\n\t"
+      "addc.u32        %4, 0, 0;\n\t"
+      "mad.hi.cc.u32   %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32  %2, %5, %7, %2;\n\t"
+      "addc.cc.u32     %3, %3, 0;\n\t"
+      "addc.u32        %4, %4, 0;\n\t"
+      "mul.lo.u32      %5, %1, %8;\n\t"
+      "mad.lo.cc.u32   %1, %5, %6, %1;\n\t"
+      "madc.lo.cc.u32  %2, %5, %7, %2;\n\t"
+      "addc.cc.u32     %3, %3, 0;\n\t"
+      "addc.u32        %4, %4, 0;\n\t"
+      "mad.hi.cc.u32   %2, %5, %6, %2;\n\t"
+      "madc.hi.cc.u32  %3, %5, %7, %3;\n\t"
+      "addc.u32        %4, %4, 0;"
+      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "=r"(t4), "=r"(m)
+      : "r"(n0), "r"(n1), "r"(q));
+  const uint64_t r = ((uint64_t)t3 << 32) | t2;
+  return (t4 != 0 || r >= n) ? r - n : r;
+}
+#endif
+
+// Word-level Montgomery multiplication (Montgomery 1985, two 32-bit words
+// of reduction per 64-bit product), written with 32x32+64 -> 64 wide
+// multiply-adds so that every partial product and its carry-in take one
+// IMAD.WIDE.  q = -n^-1 mod 2^32.  Inputs a, b < n; result in [0, n).
+//   product:   4 wide  (a0b0, a0b1, a1b0, a1b1)
+//   reduction: 2 x (m = t_i q mod 2^32, then m n0 and m n1 wide)
+// The running value after the product is t3:t2:t1:t0 < n^2; adding
+// m n + m' n 2^32 keeps it below 2n 2^64, so one extra bit (t4) suffices.
+IP_HD uint64_t mont_reduce_w(uint32_t t0, uint32_t t1, uint64_t H, uint64_t n, uint32_t q) {
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  // round 1: cancel t0
+  uint32_t m = t0 * q;
+  uint64_t acc = (uint64_t)m * n0 + t0;
+  acc = (uint64_t)m * n1 + t1 + (acc >> 32);
+  t1 = (uint32_t)acc;
+  const uint64_t c = acc >> 32;
+  H += c;
+  uint32_t t4 = H < c;
+  // round 2: cancel t1
+  m = t1 * q;
+  acc = (uint64_t)m * n0 + t1;
+  acc = (uint64_t)m * n1 + (uint32_t)H + (acc >> 32);
+  const uint64_t U = (H >> 32) + (acc >> 32) + ((uint64_t)t4 << 32);  // < 2^33
+  uint64_t r = (U << 32) | (uint32_t)acc;
+  return ((U >> 32) != 0 || r >= n) ? r - n : r;
+}
+
+IP_HD uint64_t mont_mul_w(uint64_t a, uint64_t b, uint64_t n, uint32_t q) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+  const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+  uint64_t acc = (uint64_t)a0 * b0;
+  const uint32_t t0 = (uint32_t)acc;
+  acc = (uint64_t)a0 * b1 + (acc >> 32);
+  const uint64_t c1 = acc >> 32;
+  acc = (uint64_t)a1 * b0 + (uint32_t)acc;
+  const uint32_t t1 = (uint32_t)acc;
+  const uint64_t H = (uint64_t)a1 * b1 + c1 + (acc >> 32);  // top 64 bits of a*b
+  return mont_reduce_w(t0, t1, H, n, q);
+}
+
+// a^2: a0^2 + 2 a0 a1 2^32 + a1^2 2^64 with three wide products.
+IP_HD uint64_t mont_sqr_w(uint64_t a, uint64_t n, uint32_t q) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+  const uint64_t L = (uint64_t)a0 * a0;
+  const uint64_t X = (uint64_t)a0 * a1;
+  const uint64_t D = X << 1;                   // low 64 bits of 2X
+  const uint64_t dt = X >> 63;                 // bit 64 of 2X
+  const uint64_t u = (L >> 32) + (uint32_t)D;  // < 2^33
+  const uint32_t t0 = (uint32_t)L, t1 = (uint32_t)u;
+  // top 64 bits of a^2 (cannot overflow: a^2 < 2^128)
+  const uint64_t H = (uint64_t)a1 * a1 + (D >> 32) + (u >> 32) + (dt << 32);
+  return mont_reduce_w(t0, t1, H, n, q);
+}
+
+// Fused product-scanning Montgomery multiplication (q = -n^-1 mod 2^32).
+// The product a*b and the two word-level reduction steps are interleaved so
+// that every carry enters as the 64-bit addend of a 32x32+64 -> 64 wide
+// multiply-add, which costs nothing extra:
+//   acc0 = m0 n0 + t0         (m0 = t0 q, so the low word of acc0 is 0)
+//   X = a0 b1 + hi(a0 b0),  Y = a1 b0 + lo(X),  Z = m0 n1 + lo(Y)
+//   w1 + k1 2^32 = lo(Z) + hi(acc0)                (word 1 of a b + m0 n)
+//   V = m1 n0 + w1            (m1 = w1 q, so the low word of V is 0)
+//   (a b + m0 n + m1 n 2^32) / 2^64
+//       = (a1 b1 + hi(X)) + (m1 n1 + hi(Y)) + hi(Z) + hi(V) + k1  < 2n.
+// Eight wide products and two 32-bit products; the result is reduced to
+// [0, n) by one conditional subtraction.
+IP_HD uint64_t mont_fused_tail(uint64_t U, uint64_t U2, uint32_t hz, uint32_t hv, uint32_t k1,
+                               uint64_t n) {
+  const uint64_t small = (uint64_t)hz + hv + k1;  // < 2^33
+  uint64_t r = U + U2;
+  uint32_t c = r < U;
+  r += small;
+  c += r < small;
+  return (c || r >= n) ? r - n : r;
+}
+
+IP_HD uint64_t mont_mul_f(uint64_t a, uint64_t b, uint64_t n, uint32_t q) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+  const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  const uint64_t P = (uint64_t)a0 * b0;
+  const uint32_t t0 = (uint32_t)P;
+  const uint32_t m0 = t0 * q;
+  const uint64_t acc0 = (uint64_t)m0 * n0 + t0;
+  const uint64_t X = (uint64_t)a0 * b1 + (P >> 32);
+  const uint64_t Y = (uint64_t)a1 * b0 + (uint32_t)X;
+  const uint64_t Z = (uint64_t)m0 * n1 + (uint32_t)Y;
+  const uint64_t W1 = (Z & 0xFFFFFFFFull) + (acc0 >> 32);  // < 2^33
+  const uint32_t w1 = (uint32_t)W1;
+  const uint32_t m1 = w1 * q;
+  const uint64_t V = (uint64_t)m1 * n0 + w1;
+  const uint64_t U = (uint64_t)a1 * b1 + (X >> 32);
+  const uint64_t U2 = (uint64_t)m1 * n1 + (Y >> 32);
+  return mont_fused_tail(U, U2, (uint32_t)(Z >> 32), (uint32_t)(V >> 32), (uint32_t)(W1 >> 32), n);
+}
+
+// Squaring in the fused form: the cross product a0 a1 is computed once and
+// used for both X and Y (one wide product fewer, two 64-bit adds more).
+IP_HD uint64_t mont_sqr_f(uint64_t a, uint64_t n, uint32_t q) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  const uint64_t P = (uint64_t)a0 * a0;
+  const uint32_t t0 = (uint32_t)P;
+  const uint32_t m0 = t0 * q;
+  const uint64_t acc0 = (uint64_t)m0 * n0 + t0;
+  const uint64_t C = (uint64_t)a0 * a1;
+  const uint64_t X = C + (P >> 32);          // cannot overflow: C <= (2^32-1)^2
+  const uint64_t Y = C + (uint32_t)X;
+  const uint64_t Z = (uint64_t)m0 * n1 + (uint32_t)Y;
+  const uint64_t W1 = (Z & 0xFFFFFFFFull) + (acc0 >> 32);
+  const uint32_t w1 = (uint32_t)W1;
+  const uint32_t m1 = w1 * q;
+  const uint64_t V = (uint64_t)m1 * n0 + w1;
+  const uint64_t U = (uint64_t)a1 * a1 + (X >> 32);
+  const uint64_t U2 = (uint64_t)m1 * n1 + (Y >> 32);
+  return mont_fused_tail(U, U2, (uint32_t)(Z >> 32), (uint32_t)(V >> 32), (uint32_t)(W1 >> 32), n);
+}
+
 // 2x mod n for x < n (ModAdd of x to itself, Sec. 2.2): if 2x overflows 64
 // bits it is certainly >= n, and the wrapped difference is exact.
 IP_HD uint64_t mod_dbl(uint64_t x, uint64_t n) {
@@ -123,40 +293,108 @@ IP_HD uint64_t mod_dbl(uint64_t x, uint64_t n) {
 IP_HD Mont64 mont64_setup(uint64_t n) {
   Mont64 m;
   m.n = n;
-  m.ninv = inv64(n);
+  const uint32_t i32 = inv32((uint32_t)n);
+  uint64_t i64 = i32;
+  i64 *= 2 - n * i64;  // one Newton step lifts the 32-bit inverse to 64 bits
+  m.ninv = i64;
+  m.q = 0u - i32;
   // 2^64 mod n: for n > 2^63 it is 2^64 - n, otherwise reduce (0 - n) mod n.
   m.one = ((int64_t)n < 0) ? (0 - n) : (0 - n) % n;
   m.mone = n - m.one;
   return m;
 }
 
+// The Montgomery multiplication and squaring used by the kernels, selected
+// at compile time (the tuning parameter mont_impl picks the instantiation):
+//   0: 128-bit product, REDC hi(ab) - hi(mn); squaring with one cross product
+//   1: word-level REDC with wide multiply-adds (mont_mul_w / mont_sqr_w)
+//   2: 128-bit product with a word-level REDC in PTX carry chains (device)
+//   3: fused product-scanning multiplication and squaring (mont_mul_f/_sqr_f)
+//   4: 128-bit multiplication with the fused squaring
+//   5: 128-bit multiplication, squaring as a general multiplication
+template <int kImpl>
+struct MontOps;
+
+template <>
+struct MontOps<0> {
+  static IP_HD uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) { return mont_mul(a, b, M.n, M.ninv); }
+  static IP_HD uint64_t sqr(uint64_t a, const Mont64& M) { return mont_sqr_h(a, M.n, M.ninv); }
+};
+
+template <>
+struct MontOps<1> {
+  static IP_HD uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) { return mont_mul_w(a, b, M.n, M.q); }
+  static IP_HD uint64_t sqr(uint64_t a, const Mont64& M) { return mont_sqr_w(a, M.n, M.q); }
+};
+
+template <>
+struct MontOps<3> {
+  static IP_HD uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) { return mont_mul_f(a, b, M.n, M.q); }
+  static IP_HD uint64_t sqr(uint64_t a, const Mont64& M) { return mont_sqr_f(a, M.n, M.q); }
+};
+
+// 4: the 128-bit-form multiplication with the fused squaring
+template <>
+struct MontOps<4> {
+  static IP_HD uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) { return mont_mul(a, b, M.n, M.ninv); }
+  static IP_HD uint64_t sqr(uint64_t a, const Mont64& M) { return mont_sqr_f(a, M.n, M.q); }
+};
+
+// 5: the 128-bit multiplication, squaring as a general multiplication
+template <>
+struct MontOps<5> {
+  static IP_HD uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) { return mont_mul(a, b, M.n, M.ninv); }
+  static IP_HD uint64_t sqr(uint64_t a, const Mont64& M) { return mont_mul(a, a, M.n, M.ninv); }
+};
+
+#if defined(__CUDACC__)
+template <>
+struct MontOps<2> {
+  static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
+    return mont_mul_p(a, b, M.n, M.q);
+  }
+  static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
+    return mont_mul_p(a, a, M.n, M.q);
+  }
+};
+#endif
+
 // R^2 mod n from R mod n: 8 doublings give R 2^8; each Montgomery squaring
 // maps R 2^k to R 2^(2k): 2^8 -> 2^16 -> 2^32 -> 2^64.
+template <int kImpl = 0>
 IP_HD uint64_t mont64_r2(const Mont64& M) {
   uint64_t x = M.one;
 #pragma unroll
   for (int i = 0; i < 8; ++i) x = mod_dbl(x, M.n);
-  x = mont_sqr(x, M.n, M.ninv);
-  x = mont_sqr(x, M.n, M.ninv);
-  x = mont_sqr(x, M.n, M.ninv);
+  x = MontOps<kImpl>::sqr(x, M);
+  x = MontOps<kImpl>::sqr(x, M);
+  x = MontOps<kImpl>::sqr(x, M);
   return x;
 }
 
 // Strong probable-prime test to base 2 (Sec. 2.1), n odd, n > 2.
 // 2^d by left-to-right binary exponentiation where "multiply by the base"
-// is a modular doubling.
+// is a modular doubling.  The exponent is processed from the top in whole
+// nibbles (leading zero bits square the Montgomery 1, which stays 1), with a
+// 4-way unrolled body and the exponent bit read from a shifting register.
+template <int kImpl = 0>
 IP_HD bool sprp2_64(const Mont64& M, uint64_t d, int s) {
-  const uint64_t n = M.n, ninv = M.ninv;
-  int top = 63 - clz64(d);
-  uint64_t x = mod_dbl(M.one, n);  // the leading 1 bit: 2 in Montgomery form
-  for (int b = top - 1; b >= 0; --b) {
-    x = mont_sqr(x, n, ninv);
-    uint64_t y = mod_dbl(x, n);
-    x = ((d >> b) & 1) ? y : x;
+  const uint64_t n = M.n;
+  const int nib = (64 - clz64(d) + 3) >> 2;  // nibbles in d (d >= 1)
+  uint64_t e = d << (64 - 4 * nib);          // exponent bits left-aligned
+  uint64_t x = M.one;
+  for (int k = 0; k < nib; ++k) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x = MontOps<kImpl>::sqr(x, M);
+      const uint64_t y = mod_dbl(x, n);
+      x = ((int64_t)e < 0) ? y : x;
+      e <<= 1;
+    }
   }
   if (x == M.one || x == M.mone) return true;
   for (int r = 1; r < s; ++r) {
-    x = mont_sqr(x, n, ninv);
+    x = MontOps<kImpl>::sqr(x, M);
     if (x == M.mone) return true;
     if (x == M.one) return false;
   }
@@ -164,10 +402,11 @@ IP_HD bool sprp2_64(const Mont64& M, uint64_t d, int s) {
 }
 
 // Finishes a strong test once x = a^d (Montgomery form) is known.
+template <int kImpl = 0>
 IP_HD bool sprp_tail64(const Mont64& M, uint64_t x, int s) {
   if (x == M.one || x == M.mone) return true;
   for (int r = 1; r < s; ++r) {
-    x = mont_sqr(x, M.n, M.ninv);
+    x = MontOps<kImpl>::sqr(x, M);
     if (x == M.mone) return true;
     if (x == M.one) return false;
   }
@@ -176,11 +415,12 @@ IP_HD bool sprp_tail64(const Mont64& M, uint64_t x, int s) {
 
 // a^d for a base a < n given in Montgomery form (aR), plain left-to-right
 // binary exponentiation (host reference for the windowed device kernels).
+template <int kImpl = 0>
 IP_HD uint64_t mont_pow_binary(const Mont64& M, uint64_t aR, uint64_t d) {
   uint64_t x = M.one;
   for (int b = 63 - clz64(d); b >= 0; --b) {
-    x = mont_sqr(x, M.n, M.ninv);
-    if ((d >> b) & 1) x = mont_mul(x, aR, M.n, M.ninv);
+    x = MontOps<kImpl>::sqr(x, M);
+    if ((d >> b) & 1) x = MontOps<kImpl>::mul(x, aR, M);
   }
   return x;
 }

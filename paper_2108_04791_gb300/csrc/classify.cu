@@ -10,71 +10,12 @@
 //   the prime); a survivor below p_{k+1}^2 is prime; other survivors go to
 //   the 32-bit (n < 2^32) or 64-bit Miller-Rabin queue, and their output byte
 //   is written 0 here and set to 1 later if they are prime.
-// Loads are 16-byte vector loads (two elements per thread, coalesced); queue
-// appends are warp-aggregated (one atomic per warp and queue).
-#include "arith.cuh"
+// Loads are 16-byte vector loads (coalesced, eight elements per thread per
+// tile); queue appends are block-aggregated (one atomic per queue and tile).
+#include "device_common.cuh"
 #include "internal.h"
-#include "tables.cuh"
 
 namespace ip {
-
-__constant__ TdTable c_td = make_td_table();
-
-enum : int { kComposite = 0, kPrime = 1, kMR64 = 2, kMR32 = 3 };
-
-__device__ __forceinline__ int classify_value(uint64_t n, const ClassifyArgs& a) {
-  if (n < 2) return kComposite;
-  if ((n & 1) == 0) return n == 2 ? kPrime : kComposite;
-  if (n < a.sieve_limit)
-    return (int)((__ldg(a.sieve + (n >> 6)) >> ((uint32_t)(n >> 1) & 31u)) & 1u);
-  bool hit = false, equal = false;
-  if (n < (1ull << 32)) {
-    const uint32_t v = (uint32_t)n;
-    for (uint32_t i = 0; i < a.ntd; ++i) {
-      hit |= v * c_td.inv32[i] <= c_td.lim32[i];
-      equal |= v == c_td.p[i];
-    }
-  } else {
-#pragma unroll 4
-    for (uint32_t i = 0; i < a.ntd; ++i) hit |= n * c_td.inv64[i] <= c_td.lim64[i];
-  }
-  if (equal) return kPrime;
-  if (hit) return kComposite;
-  if (n < a.td_square) return kPrime;
-  return n < (1ull << 32) ? kMR32 : kMR64;
-}
-
-__device__ __forceinline__ void warp_push64(bool want, uint64_t v, uint32_t idx, uint64_t* qn,
-                                            uint32_t* qi, uint32_t* counter) {
-  const unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
-  if (mask == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (want) {
-    const uint32_t pos = base + __popc(mask & ((1u << lane) - 1u));
-    qn[pos] = v;
-    qi[pos] = idx;
-  }
-}
-
-__device__ __forceinline__ void warp_push32(bool want, uint32_t v, uint32_t idx, uint32_t* qn,
-                                            uint32_t* qi, uint32_t* counter) {
-  const unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
-  if (mask == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (want) {
-    const uint32_t pos = base + __popc(mask & ((1u << lane) - 1u));
-    qn[pos] = v;
-    qi[pos] = idx;
-  }
-}
 
 // Double input: finite, >= 0, integral and <= 2^53 (Sec. 8.1) converts
 // exactly; anything else is invalid (output 0, counted).
@@ -122,7 +63,7 @@ template <typename T>
 __device__ void classify_single(const ClassifyArgs& a, uint64_t i) {
   bool ok;
   const uint64_t v = Loader<T>::one(a.in, i, &ok);
-  int d = ok ? classify_value(v, a) : kComposite;
+  int d = ok ? classify_value<-1>(v, a) : kComposite;
   if (!ok && a.invalid) atomicAdd(a.invalid, 1ull);
   a.out[i] = (uint8_t)(d == kPrime);
   if (d == kMR64) {
@@ -136,49 +77,133 @@ __device__ void classify_single(const ClassifyArgs& a, uint64_t i) {
   }
 }
 
-template <typename T>
+// Exclusive block-wide prefix sum of v; *total receives the block sum.
+// Every thread of the block must call it (two barriers).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp,
+                                                         uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < nwarps ? s_warp[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  *total = s_warp[32];
+  return s_warp[warp] + incl - v;
+}
+
+constexpr int kPairsPerThread = 4;  // 8 elements per thread per tile
+
+// One tile = blockDim * kPairsPerThread pairs.  Pair p covers the elements
+// head + 2p and head + 2p + 1.  Survivors of a tile are appended to the
+// queues with one atomic per queue for the whole block.
+template <typename T, int kNtd>
 __global__ void __launch_bounds__(1024) classify_kernel(ClassifyArgs a) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  __shared__ uint32_t s_scan[33];
+  __shared__ uint32_t s_base[2];
   const uint64_t head = a.head;
   const uint64_t npairs = (a.n - head) / 2;
-  // Vectorised body: pair p covers elements head + 2p and head + 2p + 1.
-  // The loop bound is per warp, so every lane takes part in the ballots.
-  for (uint64_t wbase = (gtid & ~31ull); wbase < npairs; wbase += nthreads) {
-    const uint64_t p = wbase + lane;
-    const bool valid = p < npairs;
-    uint64_t v0 = 0, v1 = 0;
-    bool ok0 = true, ok1 = true;
-    int d0 = kComposite, d1 = kComposite;
-    const uint64_t i0 = head + 2 * p;
-    if (valid) {
-      Loader<T>::pair(a.in, i0, &v0, &v1, &ok0, &ok1);
-      d0 = ok0 ? classify_value(v0, a) : kComposite;
-      d1 = ok1 ? classify_value(v1, a) : kComposite;
-      const uint8_t o0 = (uint8_t)(d0 == kPrime), o1 = (uint8_t)(d1 == kPrime);
-      if (a.pair_store)
-        *reinterpret_cast<uint16_t*>(a.out + i0) = (uint16_t)(o0 | (o1 << 8));
-      else {
-        a.out[i0] = o0;
-        a.out[i0 + 1] = o1;
+  const uint64_t tile_pairs = (uint64_t)blockDim.x * kPairsPerThread;
+  const uint64_t ntiles = (npairs + tile_pairs - 1) / tile_pairs;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    uint64_t v[2 * kPairsPerThread];
+    int d[2 * kPairsPerThread];
+    uint32_t n64 = 0, n32 = 0, nbad = 0;
+#pragma unroll
+    for (int k = 0; k < kPairsPerThread; ++k) {
+      const uint64_t p = tile * tile_pairs + (uint64_t)k * blockDim.x + threadIdx.x;
+      d[2 * k] = d[2 * k + 1] = kComposite;
+      v[2 * k] = v[2 * k + 1] = 0;
+      if (p < npairs) {
+        const uint64_t i0 = head + 2 * p;
+        bool ok0, ok1;
+        Loader<T>::pair(a.in, i0, &v[2 * k], &v[2 * k + 1], &ok0, &ok1);
+        d[2 * k] = ok0 ? classify_value<kNtd>(v[2 * k], a) : kComposite;
+        d[2 * k + 1] = ok1 ? classify_value<kNtd>(v[2 * k + 1], a) : kComposite;
+        nbad += (uint32_t)!ok0 + (uint32_t)!ok1;
+        const uint8_t o0 = (uint8_t)(d[2 * k] == kPrime), o1 = (uint8_t)(d[2 * k + 1] == kPrime);
+        if (a.pair_store)
+          *reinterpret_cast<uint16_t*>(a.out + i0) = (uint16_t)(o0 | (o1 << 8));
+        else {
+          a.out[i0] = o0;
+          a.out[i0 + 1] = o1;
+        }
       }
     }
-    if (a.invalid) {
-      const unsigned bad = __ballot_sync(0xFFFFFFFFu, valid && !ok0) ;
-      const unsigned bad1 = __ballot_sync(0xFFFFFFFFu, valid && !ok1);
-      if (lane == 0 && (bad | bad1))
-        atomicAdd(a.invalid, (unsigned long long)(__popc(bad) + __popc(bad1)));
+#pragma unroll
+    for (int j = 0; j < 2 * kPairsPerThread; ++j) {
+      n64 += (uint32_t)(d[j] == kMR64);
+      n32 += (uint32_t)(d[j] == kMR32);
     }
-    warp_push64(d0 == kMR64, v0, (uint32_t)i0, a.q64_n, a.q64_idx, &a.counters[0]);
-    warp_push64(d1 == kMR64, v1, (uint32_t)(i0 + 1), a.q64_n, a.q64_idx, &a.counters[0]);
-    warp_push32(d0 == kMR32, (uint32_t)v0, (uint32_t)i0, a.q32_n, a.q32_idx, &a.counters[1]);
-    warp_push32(d1 == kMR32, (uint32_t)v1, (uint32_t)(i0 + 1), a.q32_n, a.q32_idx, &a.counters[1]);
+    // counts fit in 16 bits each (<= 8 per thread, <= 8192 per block)
+    uint32_t total;
+    const uint32_t pre = block_exclusive_scan(n64 | (n32 << 16), s_scan, &total);
+    if (threadIdx.x == 0) {
+      s_base[0] = (total & 0xFFFFu) ? atomicAdd(&a.counters[0], total & 0xFFFFu) : 0u;
+      s_base[1] = (total >> 16) ? atomicAdd(&a.counters[1], total >> 16) : 0u;
+    }
+    if (a.invalid) {
+      const unsigned bad = __reduce_add_sync(0xFFFFFFFFu, nbad);
+      if ((threadIdx.x & 31) == 0 && bad) atomicAdd(a.invalid, (unsigned long long)bad);
+    }
+    __syncthreads();
+    uint32_t pos64 = s_base[0] + (pre & 0xFFFFu);
+    uint32_t pos32 = s_base[1] + (pre >> 16);
+#pragma unroll
+    for (int k = 0; k < kPairsPerThread; ++k) {
+      const uint64_t p = tile * tile_pairs + (uint64_t)k * blockDim.x + threadIdx.x;
+      const uint32_t i0 = (uint32_t)(head + 2 * p);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * k + h;
+        if (d[j] == kMR64) {
+          a.q64_n[pos64] = v[j];
+          a.q64_idx[pos64] = i0 + h;
+          ++pos64;
+        } else if (d[j] == kMR32) {
+          a.q32_n[pos32] = (uint32_t)v[j];
+          a.q32_idx[pos32] = i0 + h;
+          ++pos32;
+        }
+      }
+    }
+    __syncthreads();  // s_base / s_scan are reused by the next tile
   }
   // Alignment head (at most one element) and odd tail (at most one).
-  if (gtid == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (uint64_t i = 0; i < head; ++i) classify_single<T>(a, i);
     for (uint64_t i = head + 2 * npairs; i < a.n; ++i) classify_single<T>(a, i);
+  }
+}
+
+// Trial-division counts with a compiled specialisation; other counts use
+// the runtime-count kernel.
+template <typename T>
+static void launch_classify_kernel(const ClassifyArgs& a, unsigned grid, unsigned block,
+                                   cudaStream_t s) {
+  switch (a.ntd) {
+    case 0: classify_kernel<T, 0><<<grid, block, 0, s>>>(a); break;
+    case 7: classify_kernel<T, 7><<<grid, block, 0, s>>>(a); break;
+    case 11: classify_kernel<T, 11><<<grid, block, 0, s>>>(a); break;
+    case 15: classify_kernel<T, 15><<<grid, block, 0, s>>>(a); break;
+    case 23: classify_kernel<T, 23><<<grid, block, 0, s>>>(a); break;
+    case 31: classify_kernel<T, 31><<<grid, block, 0, s>>>(a); break;
+    default: classify_kernel<T, -1><<<grid, block, 0, s>>>(a); break;
   }
 }
 
@@ -187,13 +212,14 @@ static int launch_classify(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t
                            const char* name) {
   const uint32_t block = ctx->tune.classify_block;
   const uint64_t npairs = (a.n - a.head) / 2;
-  uint64_t want = (npairs + block - 1) / block;
+  const uint64_t tile_pairs = (uint64_t)block * kPairsPerThread;
+  uint64_t want = (npairs + tile_pairs - 1) / tile_pairs;
   const uint64_t cap = (uint64_t)ctx->sm_count * ctx->tune.blocks_per_sm;
   unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
   TimedLaunch tl;
   int st = launch_begin(ctx, kid, s, &tl);
   if (st) return st;
-  classify_kernel<T><<<grid, block, 0, s>>>(a);
+  launch_classify_kernel<T>(a, grid, block, s);
   return launch_end(ctx, s, &tl, name);
 }
 
@@ -208,7 +234,7 @@ int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s)
 // Launch without a context (explicit grid and block); used by the
 // allocation-free entry point.
 int launch_classify_u64_raw(const ClassifyArgs& a, unsigned grid, unsigned block, cudaStream_t s) {
-  classify_kernel<uint64_t><<<grid, block, 0, s>>>(a);
+  launch_classify_kernel<uint64_t>(a, grid, block, s);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "classify_kernel<u64>");
 }

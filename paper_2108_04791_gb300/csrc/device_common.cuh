@@ -1,0 +1,120 @@
+// device_common.cuh -- device routines shared by the plain and batched kernels.
+//
+// classify_value: the per-element decision of the classify stage (Sec. 1,
+// Sec. 6.1.2-6.1.3): n < 2, even, sieve lookup below S, trial division by the
+// odd primes 3..p_k without division, and the routing of survivors to the
+// 32- or 64-bit Miller-Rabin test.
+// rest64_is_prime: the six bases 325 ... 1795265022 of Eq. 4 for an n >= 2^32
+// that passed base 2.  mr32_is_prime: bases {2, 7, 61} for n < 2^32.
+#pragma once
+#include "arith.cuh"
+#include "tables.cuh"
+
+namespace ip {
+
+// Each translation unit keeps its own copy of the constant tables.
+static __constant__ TdTable c_td = make_td_table();
+static __constant__ BaseTable c_bases = make_base_table();
+
+enum : int { kComposite = 0, kPrime = 1, kMR64 = 2, kMR32 = 3 };
+
+constexpr int kWin = 4;
+constexpr int kTab = 1 << kWin;
+
+// kNtd >= 0: the trial-division count is a compile-time constant, the loops
+// unroll and the inverses and limits become constant operands of the
+// multiply and compare instructions.  kNtd < 0: runtime count a.ntd.
+template <int kNtd, typename P>
+__device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
+  if (n < 2) return kComposite;
+  if ((n & 1) == 0) return n == 2 ? kPrime : kComposite;
+  if (n < a.sieve_limit)
+    return (int)((__ldg(a.sieve + (n >> 6)) >> ((uint32_t)(n >> 1) & 31u)) & 1u);
+  bool hit = false, equal = false;
+  const uint32_t ntd = kNtd >= 0 ? (uint32_t)kNtd : a.ntd;
+  if (n < (1ull << 32)) {
+    const uint32_t v = (uint32_t)n;
+#pragma unroll
+    for (uint32_t i = 0; i < (kNtd >= 0 ? (uint32_t)kNtd : ntd); ++i) {
+      hit |= v * c_td.inv32[i] <= c_td.lim32[i];
+      equal |= v == c_td.p[i];
+    }
+  } else {
+#pragma unroll
+    for (uint32_t i = 0; i < (kNtd >= 0 ? (uint32_t)kNtd : ntd); ++i)
+      hit |= n * c_td.inv64[i] <= c_td.lim64[i];
+  }
+  if (equal) return kPrime;
+  if (hit) return kComposite;
+  if (n < a.td_square) return kPrime;
+  return n < (1ull << 32) ? kMR32 : kMR64;
+}
+
+// a^d mod n in Montgomery form by 4-bit fixed windows over the nibbles of d.
+// tab points at this thread's column of the shared table (stride `ld`).
+template <int kImpl>
+__device__ __forceinline__ uint64_t mont_pow_win4(const Mont64& M, uint64_t aR, uint64_t d,
+                                                  uint64_t* tab, int ld) {
+  using Ops = MontOps<kImpl>;
+  tab[0] = M.one;
+  tab[ld] = aR;
+  uint64_t t = Ops::sqr(aR, M);
+  tab[2 * ld] = t;
+#pragma unroll
+  for (int j = 3; j < kTab; ++j) {
+    t = Ops::mul(t, aR, M);
+    tab[j * ld] = t;
+  }
+  const int nib = (64 - clz64(d) + kWin - 1) / kWin;  // nibbles in d (d >= 1)
+  uint64_t x = tab[(int)((d >> (kWin * (nib - 1))) & (kTab - 1)) * ld];
+  for (int k = nib - 2; k >= 0; --k) {
+#pragma unroll
+    for (int r = 0; r < kWin; ++r) x = Ops::sqr(x, M);
+    x = Ops::mul(x, tab[(int)((d >> (kWin * k)) & (kTab - 1)) * ld], M);
+  }
+  return x;
+}
+
+// The six bases after base 2 (Eq. 4) for odd n >= 2^32 (no base is 0 mod n).
+template <int kImpl>
+__device__ __forceinline__ bool rest64_is_prime(uint64_t n, uint64_t* tab, int ld) {
+  const Mont64 M = mont64_setup(n);
+  const uint64_t r2 = mont64_r2<kImpl>(M);
+  uint64_t d = n - 1;
+  const int s = ctz64(d);
+  d >>= s;
+#pragma unroll 1
+  for (int b = 1; b < kNumBases64; ++b) {
+    const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b], r2, M);
+    const uint64_t x = mont_pow_win4<kImpl>(M, aR, d, tab, ld);
+    if (!sprp_tail64<kImpl>(M, x, s)) return false;
+  }
+  return true;
+}
+
+// Base 2 for odd n >= 2^32.
+template <int kImpl>
+__device__ __forceinline__ bool base2_passes(uint64_t n) {
+  const Mont64 M = mont64_setup(n);
+  uint64_t d = n - 1;
+  const int s = ctz64(d);
+  d >>= s;
+  return sprp2_64<kImpl>(M, d, s);
+}
+
+// Bases {2, 7, 61} for odd n < 2^32 (exact below 4,759,123,141).
+__device__ __forceinline__ bool mr32_is_prime(uint32_t n) {
+  const Mont32 M = mont32_setup(n);
+  uint32_t d = n - 1;
+  const int s = ctz32(d);
+  d >>= s;
+#pragma unroll 1
+  for (int b = 0; b < kNumBases32; ++b) {
+    const uint32_t a = c_bases.b32[b] % n;
+    if (a == 0) continue;  // base divisible by n: skipped (n is 7 or 61 here)
+    if (!sprp32(M, a, d, s)) return false;
+  }
+  return true;
+}
+
+}  // namespace ip

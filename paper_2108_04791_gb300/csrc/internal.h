@@ -33,6 +33,19 @@ struct Queues {
   size_t capacity = 0;
 };
 
+// Batched path: one descriptor per array, and the batch header, in device
+// memory (tile_begin = number of tiles of all earlier arrays).
+struct BatchDesc {
+  const uint64_t* in;
+  uint8_t* out;
+  uint64_t n;
+  uint64_t tile_begin;
+};
+struct BatchHeader {
+  uint64_t n_arrays;
+  uint64_t total_tiles;
+};
+
 struct TimedLaunch {
   int kid;
   cudaEvent_t start, stop;
@@ -43,6 +56,7 @@ struct TimedLaunch {
 struct isprime_ctx {
   int device = 0;
   int sm_count = 0;
+  int smem_optin = 0;                // shared memory a block may opt into
   uint64_t sieve_limit = 0;
   uint32_t* d_sieve = nullptr;       // odd-only bitmap: bit j <-> 2j+1
   uint32_t* d_base_primes = nullptr; // odd primes < 2^16
@@ -66,8 +80,20 @@ struct isprime_ctx {
   uint64_t* d_stage_in = nullptr;
   uint8_t* d_stage_out = nullptr;
   size_t stage_elems = 0;
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t stage_ev[4] = {};
+  cudaStream_t copy_in = nullptr;    // host -> device copies of the host path
+  cudaStream_t copy_out = nullptr;   // device -> host copies of the host path
+  cudaEvent_t stage_ev[6] = {};      // per staging slot: copied in, computed, copied out
+  cudaEvent_t host_last = nullptr;   // end of the previous host-path call
+  // batched path
+  void* d_batch = nullptr;           // BatchHeader + descriptors (device)
+  void* h_batch = nullptr;           // pinned staging of the same
+  size_t batch_cap = 0;
+  cudaEvent_t batch_ev = nullptr;    // the last descriptor upload
+  bool batch_ev_valid = false;
+  uint32_t* d_tile_counter = nullptr;
+  cudaGraphExec_t batch_exec = nullptr;
+  uint64_t batch_key = 0;
+  unsigned batch_grid = 0;
 };
 
 namespace ip {
@@ -113,5 +139,9 @@ int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, 
 int measure_int_rates(int device, isprime_int_rates* out);
 
 uint64_t td_square_for(uint32_t ntd);
+
+// batched.cu
+size_t batched_smem_bytes(uint32_t block, uint32_t tile);
+int batched_run(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays, cudaStream_t s);
 
 }  // namespace ip

@@ -20,17 +20,12 @@
 //                      survivors in [S, 2^32) (only when S < 2^32).
 // All arithmetic is in arith.cuh (ModExp / ModMultiply / ModAdd of
 // Sec. 2.2-2.4 as Montgomery multiplication and doubling).
-#include "arith.cuh"
+#include "device_common.cuh"
 #include "internal.h"
-#include "tables.cuh"
 
 namespace ip {
 
-__constant__ BaseTable c_bases = make_base_table();
-
-constexpr int kWin = 4;
-constexpr int kTab = 1 << kWin;
-
+template <int kImpl>
 __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restrict__ qn,
                                                          uint32_t* __restrict__ counters,
                                                          uint32_t* __restrict__ q64b) {
@@ -41,14 +36,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   for (uint32_t wbase = gtid & ~31u; wbase < count; wbase += nthreads) {
     const uint32_t i = wbase + lane;
     bool pass = false;
-    if (i < count) {
-      const uint64_t n = qn[i];
-      const Mont64 M = mont64_setup(n);
-      uint64_t d = n - 1;
-      const int s = ctz64(d);
-      d >>= s;
-      pass = sprp2_64(M, d, s);
-    }
+    if (i < count) pass = base2_passes<kImpl>(qn[i]);
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, pass);
     if (mask) {
       const int leader = __ffs(mask) - 1;
@@ -60,30 +48,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   }
 }
 
-// a^d mod n in Montgomery form by 4-bit fixed windows over the nibbles of d.
-// tab points at this thread's column of the shared table (stride `ld`).
-__device__ __forceinline__ uint64_t mont_pow_win4(const Mont64& M, uint64_t aR, uint64_t d,
-                                                  uint64_t* tab, int ld) {
-  const uint64_t n = M.n, ninv = M.ninv;
-  tab[0] = M.one;
-  tab[ld] = aR;
-  uint64_t t = mont_sqr(aR, n, ninv);
-  tab[2 * ld] = t;
-#pragma unroll
-  for (int j = 3; j < kTab; ++j) {
-    t = mont_mul(t, aR, n, ninv);
-    tab[j * ld] = t;
-  }
-  const int nib = (64 - clz64(d) + kWin - 1) / kWin;  // nibbles in d (d >= 1)
-  uint64_t x = tab[(int)((d >> (kWin * (nib - 1))) & (kTab - 1)) * ld];
-  for (int k = nib - 2; k >= 0; --k) {
-#pragma unroll
-    for (int q = 0; q < kWin; ++q) x = mont_sqr(x, n, ninv);
-    x = mont_mul(x, tab[(int)((d >> (kWin * k)) & (kTab - 1)) * ld], n, ninv);
-  }
-  return x;
-}
-
+template <int kImpl>
 __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restrict__ qn,
                                                         const uint32_t* __restrict__ qidx,
                                                         const uint32_t* __restrict__ q64b,
@@ -95,24 +60,7 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   const uint32_t count = *(volatile const uint32_t*)&counters[2];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const uint32_t j = q64b[i];
-    const uint64_t n = qn[j];
-    const Mont64 M = mont64_setup(n);
-    const uint64_t r2 = mont64_r2(M);
-    uint64_t d = n - 1;
-    const int s = ctz64(d);
-    d >>= s;
-    bool prime = true;
-    // n >= 2^32 > every base, so no base is 0 mod n.
-#pragma unroll 1
-    for (int b = 1; b < kNumBases64; ++b) {
-      const uint64_t aR = mont_mul((uint64_t)c_bases.b64[b], r2, n, M.ninv);
-      const uint64_t x = mont_pow_win4(M, aR, d, tab, ld);
-      if (!sprp_tail64(M, x, s)) {
-        prime = false;
-        break;
-      }
-    }
-    if (prime) out[qidx[j]] = 1;
+    if (rest64_is_prime<kImpl>(qn[j], tab, ld)) out[qidx[j]] = 1;
   }
 }
 
@@ -121,24 +69,49 @@ __global__ void __launch_bounds__(256) mr32_kernel(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ counters,
                                                    uint8_t* __restrict__ out) {
   const uint32_t count = *(volatile const uint32_t*)&counters[1];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const uint32_t n = qn[i];
-    const Mont32 M = mont32_setup(n);
-    uint32_t d = n - 1;
-    const int s = ctz32(d);
-    d >>= s;
-    bool prime = true;
-#pragma unroll 1
-    for (int b = 0; b < kNumBases32; ++b) {
-      const uint32_t a = c_bases.b32[b] % n;
-      if (a == 0) continue;  // base divisible by n: skipped (n is 7 or 61 here)
-      if (!sprp32(M, a, d, s)) {
-        prime = false;
-        break;
-      }
-    }
-    if (prime) out[qidx[i]] = 1;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    if (mr32_is_prime(qn[i])) out[qidx[i]] = 1;
+}
+
+template <int kImpl>
+static void launch_base2(const Queues& q, unsigned grid, unsigned block, cudaStream_t s) {
+  mr64_base2_kernel<kImpl><<<grid, block, 0, s>>>(q.q64_n, q.counters, q.q64b);
+}
+
+template <int kImpl>
+static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+                        cudaStream_t s) {
+  const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
+  mr64_rest_kernel<kImpl><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+}
+
+// impl_b2 selects the arithmetic of the base-2 kernel, impl that of the
+// six-base kernel (see MontOps).
+static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int impl,
+                       int impl_b2, cudaStream_t s, isprime_ctx* ctx) {
+  int st = ISPRIME_OK;
+  TimedLaunch tl;
+  if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
+  switch (impl_b2) {
+    case 1: launch_base2<1>(q, grid, block, s); break;
+    case 2: launch_base2<2>(q, grid, block, s); break;
+    case 3: launch_base2<3>(q, grid, block, s); break;
+    case 4: launch_base2<4>(q, grid, block, s); break;
+    case 5: launch_base2<5>(q, grid, block, s); break;
+    default: launch_base2<0>(q, grid, block, s); break;
   }
+  if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
+  if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
+  switch (impl) {
+    case 1: launch_rest<1>(q, out, grid, block, s); break;
+    case 2: launch_rest<2>(q, out, grid, block, s); break;
+    case 3: launch_rest<3>(q, out, grid, block, s); break;
+    case 4: launch_rest<4>(q, out, grid, block, s); break;
+    case 5: launch_rest<5>(q, out, grid, block, s); break;
+    default: launch_rest<0>(q, out, grid, block, s); break;
+  }
+  if (ctx) st = launch_end(ctx, s, &tl, "mr64_rest_kernel");
+  return st;
 }
 
 int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
@@ -151,14 +124,8 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
     mr32_kernel<<<grid, block, 0, s>>>(ctx->q.q32_n, ctx->q.q32_idx, ctx->q.counters, out);
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
-  if ((st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
-  mr64_base2_kernel<<<grid, block, 0, s>>>(ctx->q.q64_n, ctx->q.counters, ctx->q.q64b);
-  if ((st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
-  if ((st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
-  const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
-  mr64_rest_kernel<<<grid, block, smem, s>>>(ctx->q.q64_n, ctx->q.q64_idx, ctx->q.q64b,
-                                              ctx->q.counters, out);
-  return launch_end(ctx, s, &tl, "mr64_rest_kernel");
+  return launch_mr64(ctx->q, out, grid, block, (int)ctx->tune.mont_impl,
+                     (int)ctx->tune.mont_impl_base2, s, ctx);
 }
 
 // Launch without a context (explicit grid and block and queue pointers);
@@ -166,9 +133,7 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
 int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, unsigned block,
                   cudaStream_t s) {
   if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
-  mr64_base2_kernel<<<grid, block, 0, s>>>(q.q64_n, q.counters, q.q64b);
-  const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
-  mr64_rest_kernel<<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+  launch_mr64(q, out, grid, block, 0, 5, s, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
 }

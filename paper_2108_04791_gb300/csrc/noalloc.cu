@@ -120,7 +120,7 @@ extern "C" int isprime_u64_noalloc(const uint64_t* d_in, uint8_t* d_out, size_t 
   a.pair_store = (((uintptr_t)(d_out + a.head)) % 2 == 0) ? 1u : 0u;
   const unsigned block = 256;
   const uint64_t npairs = (n - a.head) / 2;
-  const uint64_t want = (npairs + block - 1) / block;
+  const uint64_t want = (npairs + 4 * block - 1) / (4 * block);  // 4 pairs per thread per tile
   const uint64_t cap = (uint64_t)d.sm_count * 8;
   const unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
   if ((st = launch_classify_u64_raw(a, grid, block, s))) return st;

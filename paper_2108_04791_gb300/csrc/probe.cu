@@ -9,6 +9,7 @@
 namespace ip {
 
 constexpr int kChains = 8;
+constexpr int kMontVariants = 8;
 constexpr int kIters = 1024;
 
 template <int kOp>
@@ -56,15 +57,31 @@ __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t* sink, uint32_t 
   }
 }
 
+// kVar 0: 128-bit product form (hi(ab) - hi(mn)); 1: word-level REDC with
+// wide multiply-adds; 2: the word-level dedicated squaring; 3: squaring in
+// the 128-bit form with one cross product; 4: 128-bit product with a PTX
+// word-level REDC; 5: mont_mul(a, a); 6: fused product-scanning
+// multiplication; 7: fused squaring.
+template <int kVar>
 __global__ void __launch_bounds__(256) mont_rate_kernel(uint64_t* sink, uint64_t seed) {
   uint64_t x[kChains];
   const uint64_t n = seed | (1ull << 63) | 1ull;
   const uint64_t ninv = inv64(n);
+  const uint32_t q = 0u - inv32((uint32_t)n);
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) x[k] = (seed * (threadIdx.x + 1) + k) % n;
+  for (int k = 0; k < kChains; ++k) x[k] = (seed * (threadIdx.x + 1) + k) & ~(1ull << 63);
   for (int it = 0; it < kIters / 8; ++it) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) x[k] = mont_mul(x[k], x[(k + 1) & (kChains - 1)] | 1, n, ninv);
+    for (int k = 0; k < kChains; ++k) {
+      if (kVar == 0) x[k] = mont_mul(x[k], x[(k + 1) & (kChains - 1)], n, ninv);
+      if (kVar == 1) x[k] = mont_mul_w(x[k], x[(k + 1) & (kChains - 1)], n, q);
+      if (kVar == 2) x[k] = mont_sqr_w(x[k], n, q);
+      if (kVar == 3) x[k] = mont_sqr_h(x[k], n, ninv);
+      if (kVar == 4) x[k] = mont_mul_p(x[k], x[(k + 1) & (kChains - 1)], n, q);
+      if (kVar == 5) x[k] = mont_mul(x[k], x[k], n, ninv);
+      if (kVar == 6) x[k] = mont_mul_f(x[k], x[(k + 1) & (kChains - 1)], n, q);
+      if (kVar == 7) x[k] = mont_sqr_f(x[k], n, q);
+    }
   }
   uint64_t acc = 0;
 #pragma unroll
@@ -116,21 +133,34 @@ int measure_int_rates(int device, isprime_int_rates* out) {
     }
     rates[op] = lane_ops / (best * 1e-3);
   }
-  float best = 1e30f;
-  for (int rep = 0; rep < 4; ++rep) {
-    IP_CUDA(cudaEventRecord(e0));
-    mont_rate_kernel<<<grid, 256>>>(reinterpret_cast<uint64_t*>(sink), 0x9E3779B97F4A7C15ull + rep);
-    IP_CUDA(cudaGetLastError());
-    IP_CUDA(cudaEventRecord(e1));
-    IP_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    IP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) best = ms;
+  double mont[kMontVariants] = {};
+  for (int var = 0; var < kMontVariants; ++var) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      IP_CUDA(cudaEventRecord(e0));
+      uint64_t* s64 = reinterpret_cast<uint64_t*>(sink);
+      const uint64_t seed = 0x9E3779B97F4A7C15ull + rep;
+      if (var == 0) mont_rate_kernel<0><<<grid, 256>>>(s64, seed);
+      if (var == 1) mont_rate_kernel<1><<<grid, 256>>>(s64, seed);
+      if (var == 2) mont_rate_kernel<2><<<grid, 256>>>(s64, seed);
+      if (var == 3) mont_rate_kernel<3><<<grid, 256>>>(s64, seed);
+      if (var == 4) mont_rate_kernel<4><<<grid, 256>>>(s64, seed);
+      if (var == 5) mont_rate_kernel<5><<<grid, 256>>>(s64, seed);
+      if (var == 6) mont_rate_kernel<6><<<grid, 256>>>(s64, seed);
+      if (var == 7) mont_rate_kernel<7><<<grid, 256>>>(s64, seed);
+      IP_CUDA(cudaGetLastError());
+      IP_CUDA(cudaEventRecord(e1));
+      IP_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      IP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) best = ms;
+    }
+    mont[var] = (double)grid * 256 * (kIters / 8) * kChains / (best * 1e-3);
   }
   out->mad_lo_u32 = rates[0];
   out->mad_hi_u32 = rates[1];
   out->mad_wide_u32 = rates[2];
-  out->mont_mul64 = (double)grid * 256 * (kIters / 8) * kChains / (best * 1e-3);
+  for (int v = 0; v < kMontVariants; ++v) out->mont_variant[v] = mont[v];
   out->sm_clock_mhz = mhz;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

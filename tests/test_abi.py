@@ -79,5 +79,17 @@ def test_argument_checks_without_gpu(L):
     assert L.isprime_ctx_destroy(None) == 0
 
 
-def test_tuning_validation_struct_layout():
-    assert ctypes.sizeof(ipg.Tuning) == 32
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors have the sizes of the C structs in include/isprime.h."""
+    src = tmp_path / "sizes.c"
+    src.write_text('#include "isprime.h"\n#include <stdio.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(isprime_tuning),'
+                   ' sizeof(isprime_stats), sizeof(isprime_kernel_time), sizeof(isprime_int_rates),'
+                   ' sizeof(isprime_array)); return 0;}\n')
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
+                   check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                            check=True).stdout.split()]
+    assert sizes == [ctypes.sizeof(ipg.Tuning), ctypes.sizeof(ipg._Stats), ctypes.sizeof(ipg._KTime),
+                     ctypes.sizeof(ipg._IntRates), ctypes.sizeof(ipg.ArrayDesc)]

@@ -31,7 +31,11 @@ def H(tmp_path_factory):
                             ("h_mont_setup", [u64, p], None), ("h_sprp2_64", [u64], i32),
                             ("h_sprp64", [u64, u64], i32), ("h_mont_mul32", [u32, u32, u32], u32),
                             ("h_sprp32", [u32, u32], i32), ("h_td64", [u64, i32], i32),
-                            ("h_td32", [u32, i32], i32), ("h_td_prime", [i32], u32)]:
+                            ("h_td32", [u32, i32], i32), ("h_td_prime", [i32], u32),
+                            ("h_mont_mul_w", [u64, u64, u64], u64), ("h_mont_sqr_w", [u64, u64], u64),
+                            ("h_mont_sqr_h", [u64, u64], u64),
+                            ("h_mont_mul_f", [u64, u64, u64], u64), ("h_mont_sqr_f", [u64, u64], u64),
+                            ("h_stress", [u64, u64, i32], u64)]:
         f = getattr(L, name)
         f.argtypes, f.restype = args, res
     return L
@@ -52,7 +56,7 @@ def test_inverses(H):
 
 def test_mont_mul_and_setup(H):
     rng = random.Random(2)
-    buf = (ctypes.c_uint64 * 4)()
+    buf = (ctypes.c_uint64 * 6)()
     for n in _moduli(rng):
         rinv = pow(R, -1, n)
         for _ in range(10):
@@ -61,9 +65,30 @@ def test_mont_mul_and_setup(H):
         for a, b in ((n - 1, n - 1), (0, n - 1), (n - 1, 1)):
             assert H.h_mont_mul(a, b, n) == a * b * rinv % n
         H.h_mont_setup(n, buf)
-        ninv, one, mone, r2 = list(buf)
-        assert ninv * n % R == 1
+        q, one, mone, r2, ninv, r2w = list(buf)
+        assert (q * n + 1) % (1 << 32) == 0 and ninv * n % R == 1 and r2w == r2
         assert one == R % n and mone == (n - R % n) and r2 == R * R % n
+
+
+def test_word_level_montgomery(H):
+    """Word-level REDC (wide multiply-adds) and the dedicated squaring."""
+    rng = random.Random(12)
+    for n in _moduli(rng, 1000):
+        rinv = pow(R, -1, n)
+        cases = [(n - 1, n - 1), (0, n - 1), (n - 1, 1), (0, 0), (1, 1), (n // 2, n - 2)]
+        cases += [(rng.randrange(n), rng.randrange(n)) for _ in range(20)]
+        for a, b in cases:
+            assert H.h_mont_mul_w(a, b, n) == a * b * rinv % n, (a, b, n)
+            assert H.h_mont_sqr_w(a, n) == a * a * rinv % n, (a, n)
+            assert H.h_mont_sqr_h(a, n) == a * a * rinv % n, (a, n)
+            assert H.h_mont_mul_f(a, b, n) == a * b * rinv % n, (a, b, n)
+            assert H.h_mont_sqr_f(a, n) == a * a * rinv % n, (a, n)
+
+
+@pytest.mark.parametrize("variant", range(6))
+def test_montgomery_stress(H, variant):
+    """2^20 random triples per formulation against 128-bit reference arithmetic."""
+    assert H.h_stress(1234 + variant, 1 << 20, variant) == 0
 
 
 def test_mod_dbl(H):

@@ -190,7 +190,12 @@ def test_tuning_does_not_change_results():
         for kw in [dict(td_primes=0), dict(td_primes=1), dict(td_primes=53),
                    dict(classify_block=64, mr_block=32, blocks_per_sm=1),
                    dict(classify_block=1024, mr_block=256, blocks_per_sm=16),
-                   dict(chunk_log2=16)]:
+                   dict(chunk_log2=16), dict(mont_impl=1), dict(mont_impl=2),
+                   dict(mont_impl=3), dict(mont_impl=4), dict(mont_impl=5),
+                   dict(mont_impl_base2=0), dict(mont_impl_base2=1), dict(mont_impl_base2=2),
+                   dict(mont_impl_base2=3), dict(mont_impl_base2=4), dict(mont_impl_base2=5),
+                   dict(td_primes=7), dict(td_primes=11), dict(td_primes=23), dict(td_primes=31),
+                   dict(td_primes=40), dict(mont_impl=0, td_primes=15)]:
             c.set_tuning(**kw)
             _assert_same(v, _gpu(v, c), want)
 
@@ -264,4 +269,76 @@ def test_timing_records_every_kernel():
 
 def test_int_rates_probe():
     r = ipg.int_rates(0)
-    assert r["mad_lo_u32"] > 1e12 and r["mont_mul64"] > 1e10 and r["sm_clock_mhz"] > 100
+    assert r["mad_lo_u32"] > 1e12 and r["mont_mul_128"] > 1e10 and r["sm_clock_mhz"] > 100
+
+
+# ------------------------------------------------------------------ batched
+
+def test_batched_matches_oracle_on_ragged_batch():
+    from workloads import batched_arrays
+    vals, offs = batched_arrays(n_arrays=300, max_size=1 << 14, seed=61)
+    sizes = np.diff(offs)
+    # add edge cases: empty arrays, single elements, special values
+    extra = [np.array([], dtype=np.uint64), np.array([2**64 - 59], dtype=np.uint64),
+             np.array(SPECIAL, dtype=np.uint64), np.array([], dtype=np.uint64)]
+    arrays = [vals[offs[i]:offs[i + 1]] for i in range(len(sizes))] + extra
+    c = ipg.Context.default(0)
+    tens = [_to_dev(a) for a in arrays]
+    outs = c.isprime_batched(tens)
+    torch.cuda.synchronize()
+    for a, o in zip(arrays, outs):
+        _assert_same(a, o.cpu().numpy(), oracle.isprime_u64(a))
+
+
+def test_batched_rejects_tuning_beyond_shared_memory():
+    with pytest.raises(ipg.IsPrimeError):
+        ipg.Context.default(0).set_tuning(batch_block=256, batch_tile_log2=14)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(batch_block=64, batch_tile_log2=8),
+                                dict(batch_block=256, batch_tile_log2=13),
+                                dict(batch_block=64, batch_tile_log2=13),
+                                dict(td_primes=23), dict(td_primes=5),
+                                dict(batch_blocks_per_sm=1)])
+def test_batched_tuning_and_small_sieve(kw):
+    from workloads import batched_arrays
+    vals, offs = batched_arrays(n_arrays=64, max_size=1 << 15, seed=62)
+    arrays = [vals[offs[i]:offs[i + 1]] for i in range(64)]
+    with ipg.Context(0, sieve_limit=1 << 20) as c:
+        c.set_tuning(**kw)
+        for _ in range(2):  # second call replays the recorded graph
+            outs = c.isprime_batched([_to_dev(a) for a in arrays])
+            torch.cuda.synchronize()
+            for a, o in zip(arrays, outs):
+                _assert_same(a, o.cpu().numpy(), oracle.isprime_u64(a))
+
+
+def test_batched_equals_plain_calls():
+    vals = plain_mixed(1 << 18, seed=63)
+    parts = np.split(vals, [1, 10, 1000, 50000, 50001])
+    c = ipg.Context.default(0)
+    outs = c.isprime_batched([_to_dev(p) for p in parts])
+    plain = [_gpu(p, c) if p.size else np.zeros(0, np.uint8) for p in parts]
+    torch.cuda.synchronize()
+    for o, p in zip(outs, plain):
+        assert np.array_equal(o.cpu().numpy(), p)
+
+
+# ------------------------------------------------------------------ autotuner
+
+def test_autotune_keeps_results_exact_and_caches(tmp_path):
+    v = np.concatenate([plain_large(1 << 17, seed=81), plain_mixed(1 << 17, seed=82)])
+    want = oracle.isprime_u64(v)
+    cache = str(tmp_path / "tune.txt")
+    with ipg.Context(0, sieve_limit=1 << 24) as c:
+        t1 = c.autotune(_to_dev(v), mode="plain", cache_path=cache)
+        _assert_same(v, _gpu(v, c), want)
+        tb = c.autotune(_to_dev(v), mode="batched", cache_path=cache)
+        outs = c.isprime_batched([_to_dev(v[:1000]), _to_dev(v[1000:])])
+        torch.cuda.synchronize()
+        _assert_same(v, np.concatenate([o.cpu().numpy() for o in outs]), want)
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 2 and all("td_primes=" in l for l in lines)
+    with ipg.Context(0, sieve_limit=1 << 24) as c2:  # a cache hit installs the same tuning
+        assert c2.autotune(_to_dev(v), mode="plain", cache_path=cache) == t1
+        assert c2.autotune(_to_dev(v), mode="batched", cache_path=cache) == tb
