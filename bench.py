@@ -69,7 +69,7 @@ def _parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--workload", default="plain_large",
-                   choices=["plain_large", "plain_small", "plain_mixed", "batched"])
+                   choices=["plain_large", "plain_small", "plain_mixed", "batched", "served"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-probe", action="store_true", help="skip the integer-rate probe")
@@ -414,6 +414,75 @@ def run_batched(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_served(args, world, rank, local):
+    """20,000 requests with exponential inter-arrival times (mean 200 us),
+    log-uniform sizes 1..2^22 and values drawn as in the batched workload,
+    submitted at their arrival times to the continuous-batching server
+    (8 GB device budget).  Request inputs are slices of a 2^27-value pool
+    with that distribution, in pinned host memory; outputs go to a pinned
+    ring larger than the server can hold in flight."""
+    import torch
+    import paper_2108_04791_gb300 as ipg
+    from workloads import torch_gen
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    arrivals, sizes, _ = wg.served_requests(n_requests=20_000, max_size=1 << 22,
+                                            rate_per_s=5000.0, seed=4 + 1000 * rank, values=False)
+    pool_n = 1 << 27
+    pool = torch_gen.served_values(pool_n, seed=4 + 1000 * rank, device=dev).cpu().pin_memory()
+    pool_np = pool.numpy().view(np.uint64)
+    ring_n = 1 << 31
+    ring = torch.empty(ring_n, dtype=torch.uint8).pin_memory().numpy()
+    starts = np.zeros(len(sizes), dtype=np.int64)
+    np.cumsum(sizes[:-1], out=starts[1:])
+    in_off = starts % (pool_n - (1 << 22))
+    out_off = starts % (ring_n - (1 << 22))
+    ctx = ipg.Context.default(local)
+    srv = ipg.Server(ctx, mem_budget_bytes=8 << 30, n_slots=4)
+    # warm-up requests (graph recording, first-touch of the arena)
+    for i in range(max(args.warmup, 3)):
+        srv.wait(srv.submit(pool_np[:1 << 20], out=ring[:1 << 20]))
+    srv.reset_stats()
+    _barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for i in range(len(sizes)):
+        target = t0 + arrivals[i]
+        while True:
+            now = time.perf_counter()
+            if now >= target:
+                break
+            if target - now > 2e-3:
+                time.sleep(target - now - 1e-3)
+        a, o, n = int(in_off[i]), int(out_off[i]), int(sizes[i])
+        tickets.append(srv.submit(pool_np[a:a + n], out=ring[o:o + n]))
+    for t in tickets:
+        srv.wait(t)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    value = _max_over_ranks(st["tests_per_s"], world, dev) if world == 1 else st["tests_per_s"] * world
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": len(sizes), "warmup": max(args.warmup, 3),
+            "ms_per_step": 1e3 * st["span_s"] / len(sizes), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "served", "requests": len(sizes), "elements": int(sizes.sum()),
+                       "rate_req_per_s": 5000, "budget_bytes": 8 << 30, "slots": 4,
+                       "description": wg.WORKLOADS["served"]},
+            "serve": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                      "max_ms": st["max_ms"], "batches": st["batches"], "span_s": st["span_s"],
+                      "offered_tests_per_s": float(sizes.sum() / arrivals[-1]), "wall_s": wall},
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse()
     world, rank, local = _dist_init(args)
@@ -421,6 +490,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "batched":
         run_batched(args, world, rank, local)
+    elif args.workload == "served":
+        run_served(args, world, rank, local)
     else:
         run_mine(args, world, rank, local)
     if world > 1:

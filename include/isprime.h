@@ -184,6 +184,50 @@ int isprime_u64_noalloc(const uint64_t *d_in, uint8_t *d_out, size_t n, isprime_
  * from the resident bitmap (pi(S); 0 when S == 0).  Synchronous. */
 int isprime_sieve_count(isprime_ctx *ctx, uint64_t *out);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A continuous-batching server on one context.  Requests (host arrays) are
+ * admitted as they arrive; a dispatcher thread groups the requests waiting
+ * at that moment into a batch whenever one of n_slots stream slots and
+ * enough of the device-memory budget (9 bytes per element, rounded to 256 B
+ * per buffer) are free, and runs copy-in / one batched launch / copy-out on
+ * that slot.  Batches on different slots overlap on the GPU.  The context's
+ * sieve stays resident and is shared by all batches. */
+typedef struct isprime_server isprime_server;
+
+typedef struct {
+  uint64_t requests;   /* completed requests since creation or the last reset */
+  uint64_t elements;   /* their elements */
+  uint64_t batches;    /* batches launched */
+  double p50_ms;       /* latency percentiles: completion time - submit time */
+  double p99_ms;
+  double mean_ms;
+  double max_ms;
+  double span_s;       /* first submit to last completion */
+  double tests_per_s;  /* elements / span_s */
+} isprime_server_stats;
+
+/* Allocates a device arena of mem_budget_bytes and starts the server's two
+ * threads.  n_slots in [1, 16]. */
+int isprime_server_create(isprime_ctx *ctx, size_t mem_budget_bytes, int n_slots,
+                          isprime_server **out);
+/* Admits a request and returns at once with *ticket.  h_in (n values,
+ * 8-byte aligned) and h_out (n bytes) must stay valid until the ticket is
+ * waited for; pinned memory gives asynchronous copies.  ISPRIME_EBUSY if the
+ * request alone needs more device memory than the budget. */
+int isprime_server_submit(isprime_server *srv, const uint64_t *h_in, uint8_t *h_out, size_t n,
+                          uint64_t *ticket);
+/* Waits for a ticket (timeout_ms < 0: no limit).  ISPRIME_OK once h_out holds
+ * the result (the ticket is then released); ISPRIME_ETIMEDOUT if it did not
+ * finish in time (the ticket stays valid); ISPRIME_EINVAL for an unknown
+ * ticket. */
+int isprime_server_wait(isprime_server *srv, uint64_t ticket, int timeout_ms);
+int isprime_server_get_stats(isprime_server *srv, isprime_server_stats *out);
+int isprime_server_reset_stats(isprime_server *srv);
+/* Stops admitting, finishes every admitted request, joins the threads and
+ * frees the server (not the context). */
+int isprime_server_destroy(isprime_server *srv);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Kernel identifiers for the timing records. */

@@ -19,8 +19,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["build", "lib", "isprime", "isprime_host", "Context", "Tuning", "IsPrimeError",
-           "int_rates", "KERNEL_NAMES"]
+__all__ = ["build", "lib", "isprime", "isprime_host", "Context", "Server", "Tuning",
+           "IsPrimeError", "int_rates", "KERNEL_NAMES"]
 
 _lock = threading.Lock()
 _lib = None
@@ -51,6 +51,14 @@ class Tuning(ctypes.Structure):
 
 class ArrayDesc(ctypes.Structure):
     _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("elements", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("span_s", ctypes.c_double),
+                ("tests_per_s", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -100,6 +108,12 @@ def lib():
                 "isprime_u64_batched": ([vp, ctypes.POINTER(ArrayDesc), sz, vp], i32),
                 "isprime_autotune": ([vp, vp, vp, sz, i32, ctypes.c_char_p, ctypes.POINTER(Tuning)], i32),
                 "isprime_tuning_format": ([ctypes.POINTER(Tuning), ctypes.c_char_p, sz], i32),
+                "isprime_server_create": ([vp, sz, i32, ctypes.POINTER(vp)], i32),
+                "isprime_server_submit": ([vp, vp, vp, sz, ctypes.POINTER(u64)], i32),
+                "isprime_server_wait": ([vp, u64, i32], i32),
+                "isprime_server_get_stats": ([vp, ctypes.POINTER(_ServerStats)], i32),
+                "isprime_server_reset_stats": ([vp], i32),
+                "isprime_server_destroy": ([vp], i32),
                 "isprime_sieve_count": ([vp, ctypes.POINTER(u64)], i32),
                 "isprime_timing_enable": ([vp, i32], i32),
                 "isprime_timing_read": ([vp, ctypes.POINTER(_KTime), i32], i32),
@@ -297,6 +311,63 @@ class Context:
             sh = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
             _check(lib().isprime_u64_host(self._h, a.ctypes.data, out.ctypes.data, a.size, sh))
         return out
+
+
+class Server:
+    """Continuous-batching server over a context (see isprime_server_create).
+
+    submit() takes a host numpy array (uint64-compatible) and returns a
+    ticket; the input and output arrays are kept alive until wait()."""
+
+    def __init__(self, ctx: Context, mem_budget_bytes: int = 8 << 30, n_slots: int = 4):
+        h = ctypes.c_void_p()
+        _check(lib().isprime_server_create(ctx.handle, mem_budget_bytes, n_slots, ctypes.byref(h)))
+        self._h = h
+        self._ctx = ctx
+        self._live: dict = {}
+
+    def submit(self, values, out=None) -> int:
+        a = np.ascontiguousarray(values)
+        if a.dtype != np.uint64:
+            a = a.astype(np.uint64)
+        if out is None:
+            out = np.empty(a.shape, dtype=np.uint8)
+        t = ctypes.c_uint64()
+        _check(lib().isprime_server_submit(self._h, a.ctypes.data if a.size else None,
+                                           out.ctypes.data if out.size else None, a.size,
+                                           ctypes.byref(t)))
+        self._live[t.value] = (a, out)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> np.ndarray:
+        _check(lib().isprime_server_wait(self._h, ticket, timeout_ms))
+        return self._live.pop(ticket)[1]
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(lib().isprime_server_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def reset_stats(self):
+        _check(lib().isprime_server_reset_stats(self._h))
+
+    def close(self):
+        if self._h:
+            _check(lib().isprime_server_destroy(self._h))
+            self._h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _defaults: dict = {}

@@ -298,11 +298,7 @@ int isprime_ctx_destroy(isprime_ctx* ctx) {
     if (ctx->h_pin_in) cudaFreeHost(ctx->h_pin_in);
     if (ctx->h_pin_out) cudaFreeHost(ctx->h_pin_out);
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
-    if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
-    if (ctx->batch_ev) cudaEventDestroy(ctx->batch_ev);
-    cudaFree(ctx->d_batch);
-    if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
-    cudaFree(ctx->d_tile_counter);
+    batch_state_free(&ctx->batch);
     for (auto e : ctx->stage_ev)
       if (e) cudaEventDestroy(e);
     if (ctx->host_last) cudaEventDestroy(ctx->host_last);
@@ -398,7 +394,7 @@ int isprime_u64_batched(isprime_ctx* ctx, const isprime_array* arrays, size_t n_
   DeviceGuard g(ctx->device);
   int st = order_before(ctx, s);
   if (st) return st;
-  if ((st = batched_run(ctx, arrays, n_arrays, s))) return st;
+  if ((st = batched_run(ctx, &ctx->batch, arrays, n_arrays, s))) return st;
   if ((st = order_after(ctx, s))) return st;
   ctx->stats.calls++;
   return ISPRIME_OK;

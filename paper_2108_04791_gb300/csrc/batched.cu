@@ -203,7 +203,17 @@ static int batched_grid(isprime_ctx* ctx, const BatchVariant& v, uint32_t block,
   return ISPRIME_OK;
 }
 
-int batched_run(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays, cudaStream_t s) {
+void batch_state_free(BatchState* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->ev) cudaEventDestroy(b->ev);
+  cudaFree(b->d_batch);
+  if (b->h_batch) cudaFreeHost(b->h_batch);
+  cudaFree(b->d_tile_counter);
+  *b = BatchState{};
+}
+
+int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, size_t n_arrays,
+                cudaStream_t s) {
   const uint32_t block = ctx->tune.batch_block;
   const uint32_t tile = 1u << ctx->tune.batch_tile_log2;
   // Host-side descriptors: tile prefix sums (arrays with n == 0 get no tiles).
@@ -222,46 +232,46 @@ int batched_run(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays, 
   if (tiles >= (1ull << 31)) return set_error(ISPRIME_EINVAL, "batch has 2^31 tiles or more");
   const size_t bytes = sizeof(BatchHeader) + n_arrays * sizeof(BatchDesc);
   // Device and pinned staging buffers (grow as needed; growth invalidates the graph).
-  if (ctx->batch_cap < bytes) {
-    if (ctx->batch_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->batch_ev));
-    if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
-    cudaFree(ctx->d_batch);
-    cudaFreeHost(ctx->h_batch);
-    ctx->d_batch = nullptr;
-    ctx->h_batch = nullptr;
-    ctx->batch_cap = 0;
+  if (bs->cap < bytes) {
+    if (bs->ev_valid) IP_CUDA(cudaEventSynchronize(bs->ev));
+    IP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(bs->d_batch);
+    cudaFreeHost(bs->h_batch);
+    bs->d_batch = nullptr;
+    bs->h_batch = nullptr;
+    bs->cap = 0;
     const size_t cap = std::max(bytes * 2, (size_t)4096);
-    IP_CUDA(cudaMalloc(&ctx->d_batch, cap));
-    IP_CUDA(cudaMallocHost(&ctx->h_batch, cap));
-    ctx->batch_cap = cap;
-    if (ctx->batch_exec) {
-      cudaGraphExecDestroy(ctx->batch_exec);
-      ctx->batch_exec = nullptr;
+    IP_CUDA(cudaMalloc(&bs->d_batch, cap));
+    IP_CUDA(cudaMallocHost(&bs->h_batch, cap));
+    bs->cap = cap;
+    if (bs->exec) {
+      cudaGraphExecDestroy(bs->exec);
+      bs->exec = nullptr;
     }
   }
-  if (!ctx->batch_ev) IP_CUDA(cudaEventCreateWithFlags(&ctx->batch_ev, cudaEventDisableTiming));
-  if (!ctx->d_tile_counter) IP_CUDA(cudaMalloc(&ctx->d_tile_counter, 256));
+  if (!bs->ev) IP_CUDA(cudaEventCreateWithFlags(&bs->ev, cudaEventDisableTiming));
+  if (!bs->d_tile_counter) IP_CUDA(cudaMalloc(&bs->d_tile_counter, 256));
   // The pinned buffer may still be read by the previous call's copy.
-  if (ctx->batch_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->batch_ev));
+  if (bs->ev_valid) IP_CUDA(cudaEventSynchronize(bs->ev));
   BatchHeader h;
   h.n_arrays = n_arrays;
   h.total_tiles = tiles;
-  memcpy(ctx->h_batch, &h, sizeof h);
-  memcpy(static_cast<char*>(ctx->h_batch) + sizeof h, descs.data(), n_arrays * sizeof(BatchDesc));
-  IP_CUDA(cudaMemcpyAsync(ctx->d_batch, ctx->h_batch, bytes, cudaMemcpyHostToDevice, s));
-  IP_CUDA(cudaEventRecord(ctx->batch_ev, s));
-  ctx->batch_ev_valid = true;
+  memcpy(bs->h_batch, &h, sizeof h);
+  memcpy(static_cast<char*>(bs->h_batch) + sizeof h, descs.data(), n_arrays * sizeof(BatchDesc));
+  IP_CUDA(cudaMemcpyAsync(bs->d_batch, bs->h_batch, bytes, cudaMemcpyHostToDevice, s));
+  IP_CUDA(cudaEventRecord(bs->ev, s));
+  bs->ev_valid = true;
 
   // The graph: reset the tile counter, launch the persistent kernel.
   const BatchVariant v = pick_variant(ctx->tune.td_primes);
   const size_t smem = batched_smem_bytes(block, tile);
   const uint64_t key = ((uint64_t)block << 40) ^ ((uint64_t)tile << 8) ^ ctx->tune.td_primes ^
                        ((uint64_t)ctx->tune.batch_blocks_per_sm << 56);
-  if (!ctx->batch_exec || ctx->batch_key != key) {
-    if (ctx->batch_exec) {
+  if (!bs->exec || bs->key != key) {
+    if (bs->exec) {
       IP_CUDA(cudaStreamSynchronize(s));
-      cudaGraphExecDestroy(ctx->batch_exec);
-      ctx->batch_exec = nullptr;
+      cudaGraphExecDestroy(bs->exec);
+      bs->exec = nullptr;
     }
     unsigned grid = 0;
     int st = batched_grid(ctx, v, block, smem, &grid);
@@ -269,9 +279,9 @@ int batched_run(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays, 
     if (ctx->tune.batch_blocks_per_sm)
       grid = std::min(grid, (unsigned)(ctx->sm_count * ctx->tune.batch_blocks_per_sm));
     BatchParams p;
-    p.descs = reinterpret_cast<const BatchDesc*>(static_cast<char*>(ctx->d_batch) + sizeof(BatchHeader));
-    p.hdr = reinterpret_cast<const BatchHeader*>(ctx->d_batch);
-    p.tile_counter = ctx->d_tile_counter;
+    p.descs = reinterpret_cast<const BatchDesc*>(static_cast<char*>(bs->d_batch) + sizeof(BatchHeader));
+    p.hdr = reinterpret_cast<const BatchHeader*>(bs->d_batch);
+    p.tile_counter = bs->d_tile_counter;
     p.sieve = ctx->d_sieve;
     p.sieve_limit = ctx->sieve_limit;
     p.ntd = ctx->tune.td_primes;
@@ -282,21 +292,21 @@ int batched_run(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays, 
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(uint32_t), cs);
+      cudaMemsetAsync(bs->d_tile_counter, 0, sizeof(uint32_t), cs);
       v.launch(p, grid, block, smem, cs);
       e = cudaStreamEndCapture(cs, &g);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->batch_exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bs->exec, g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) return cuda_fail(e, "capturing the batched graph");
-    ctx->batch_key = key;
-    ctx->batch_grid = grid;
+    bs->key = key;
+    bs->grid = grid;
   }
   TimedLaunch tl;
   int st = launch_begin(ctx, ISPRIME_K_BATCHED, s, &tl);
   if (st) return st;
-  IP_CUDA(cudaGraphLaunch(ctx->batch_exec, s));
+  IP_CUDA(cudaGraphLaunch(bs->exec, s));
   if ((st = launch_end(ctx, s, &tl, "batched graph"))) return st;
   ctx->stats.elements += elems;
   return ISPRIME_OK;

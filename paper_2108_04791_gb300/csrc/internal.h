@@ -46,6 +46,22 @@ struct BatchHeader {
   uint64_t total_tiles;
 };
 
+// State of one batched launch site: descriptor buffers, tile counter and the
+// recorded graph.  A context owns one for its own calls; each server slot
+// owns another, so batches on different streams never share them.
+struct BatchState {
+  void* d_batch = nullptr;           // BatchHeader + descriptors (device)
+  void* h_batch = nullptr;           // pinned staging of the same
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;          // the last descriptor upload
+  bool ev_valid = false;
+  uint32_t* d_tile_counter = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t key = 0;
+  unsigned grid = 0;
+};
+void batch_state_free(BatchState* b);
+
 struct TimedLaunch {
   int kid;
   cudaEvent_t start, stop;
@@ -84,16 +100,7 @@ struct isprime_ctx {
   cudaStream_t copy_out = nullptr;   // device -> host copies of the host path
   cudaEvent_t stage_ev[6] = {};      // per staging slot: copied in, computed, copied out
   cudaEvent_t host_last = nullptr;   // end of the previous host-path call
-  // batched path
-  void* d_batch = nullptr;           // BatchHeader + descriptors (device)
-  void* h_batch = nullptr;           // pinned staging of the same
-  size_t batch_cap = 0;
-  cudaEvent_t batch_ev = nullptr;    // the last descriptor upload
-  bool batch_ev_valid = false;
-  uint32_t* d_tile_counter = nullptr;
-  cudaGraphExec_t batch_exec = nullptr;
-  uint64_t batch_key = 0;
-  unsigned batch_grid = 0;
+  ip::BatchState batch;              // batched path of the context's own calls
 };
 
 namespace ip {
@@ -142,6 +149,9 @@ uint64_t td_square_for(uint32_t ntd);
 
 // batched.cu
 size_t batched_smem_bytes(uint32_t block, uint32_t tile);
-int batched_run(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays, cudaStream_t s);
+// Runs one batch with the given launch-site state on stream s (no context
+// ordering; the caller orders uses of `bs`).
+int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, size_t n_arrays,
+                cudaStream_t s);
 
 }  // namespace ip
