@@ -49,17 +49,36 @@ WORK_PLAIN_LARGE = {
     "rest_squarings": 12.5845,
     "rest_multiplies": 6.3263,
 }
-# 32-bit multiply instructions per 64-bit Montgomery operation as written in
-# csrc/arith.cuh: a 64x64->128 product is 4 wide (32x32->64) partial
-# products, the 64x64->64 low product m = lo * n^-1 is 1 wide + 2 low, and
-# hi(m*n) needs all 4 wide products; a wide product counts as 2 issue slots
-# of the integer multiply pipe (measured mad.wide rate = 1/2 mad.lo rate).
-IMAD_SLOTS_PER_MULMOD = 2 * 4 + (2 + 2) + 2 * 4   # 20
-IMAD_SLOTS_PER_SQUARING = IMAD_SLOTS_PER_MULMOD    # squaring uses the same routine
-IMAD_SLOTS_PER_TRIAL_TEST = 4                      # 64-bit low product: 1 wide + 2 low
+# Integer multiply-pipe slots per operation in the schoolbook 2x32-bit-limb
+# form (one slot = one 32-bit low multiply-add; a 32x32->64 wide product or a
+# high product occupies the pipe for two slots, as measured on this GPU):
+#   multiplication: a*b 4 wide (8) + m = lo*n^-1 mod 2^64 1 wide + 2 low (4)
+#                   + hi(m*n) 4 wide (8) = 20
+#   squaring:       a*a 3 wide (6) + 4 + 8 = 18
+#   divisibility test n * p^-1 mod 2^64: 1 wide + 2 low = 4
+IMAD_SLOTS_PER_MULMOD = 20
+IMAD_SLOTS_PER_SQUARING = 18
+IMAD_SLOTS_PER_TRIAL_TEST = 4
 IMAD_PER_SM_PER_CLK = 64                           # 32-bit IMAD issue rate per SM
 SM_COUNT_GB300 = 152
 SM_MAX_MHZ = 2070.0
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of this workload (profiles/*__plain_large_2p24.md); they hold for
+# the kernel sources whose hash is recorded and are reported as null otherwise.
+NCU_TRAFFIC = {"sources": "f7dbaeb15c919994", "mr64_base2": 27.41e6, "mr64_rest": 45.43e6,
+               "classify_u64": 144.89e6}
+
+
+def kernel_sources_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2108_04791_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _parse():
@@ -298,10 +317,13 @@ def run_mine(args, world, rank, local):
         if dom in slots:
             per_launch = slots[dom] * n
             achieved = per_launch / (dom_ms / dom_launches / 1e3)
+            traffic = (NCU_TRAFFIC.get(dom) if NCU_TRAFFIC["sources"] == kernel_sources_hash()
+                       else None)
             roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                    "unit": "T int-mul slots/s", "frac": achieved / peak_ops, "traffic": None,
+                    "unit": "T int-mul slots/s", "frac": achieved / peak_ops, "traffic": traffic,
                     "kernel": dom, "kernel_ms_per_launch": dom_ms / dom_launches,
-                    "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived)",
+                    "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived; the probe measures "
+                                   "64 mad.lo.u32 lanes/clk/SM)",
                     "algorithmic_slots_per_element": slots[dom]}
     kernels = {k: {"ms_per_step": v[0] / max(args.steps, 1), "launches": v[1]}
                for k, v in ktimes.items() if v[1]}
