@@ -222,11 +222,15 @@ def run_reference(args, world, rank):
     vals, desc = _workload(args.workload, 0)
     import oracle
     cores = os.cpu_count() or 1
+    chunk = 1 << 16  # the oracle's multi-threaded driver hands out 64 Ki-element chunks
+    cal = vals[: cores * chunk]
     t0 = time.perf_counter()
-    oracle.isprime_u64(vals[: 1 << 16], threads=cores)
-    rate = (1 << 16) / max(time.perf_counter() - t0, 1e-9)
+    oracle.isprime_u64(cal, threads=cores)
+    rate = cal.size / max(time.perf_counter() - t0, 1e-9)
     budget_s = 60.0
-    per_step = int(max(1 << 12, min(vals.size, rate * budget_s / max(args.steps + args.warmup, 1))))
+    # every step gives each core at least one chunk; the whole run stays near budget_s
+    per_step = int(max(cores * chunk, min(vals.size, rate * budget_s / max(args.steps + args.warmup, 1))))
+    per_step = min(per_step, vals.size)
     for w in range(args.warmup):
         oracle.isprime_u64(vals[:per_step], threads=cores)
     total = 0.0

@@ -69,7 +69,8 @@ typedef struct {
   uint32_t batch_block;    /* threads per block of the batched kernel (64..256, multiple of 32) */
   uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */
   uint32_t batch_blocks_per_sm; /* cap on resident batched blocks per SM (0 = occupancy limit) */
-  uint32_t reserved[3];
+  uint32_t base2_window;   /* base-2 exponentiation: 0 binary with doublings, 4 4-bit windows */
+  uint32_t reserved[2];
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -79,10 +79,11 @@ static isprime_tuning default_tuning() {
   t.td_primes = 15;  // 3..53
   t.chunk_log2 = 24;
   t.mont_impl = 0;
-  t.mont_impl_base2 = 5;
+  t.mont_impl_base2 = 0;
   t.batch_block = 128;
   t.batch_tile_log2 = 10;
   t.batch_blocks_per_sm = 0;
+  t.base2_window = 4;
   return t;
 }
 
@@ -98,6 +99,7 @@ static int check_tuning(const isprime_tuning& t) {
   if (bad_block(t.batch_block, 256)) return set_error(ISPRIME_EINVAL, "batch_block must be a multiple of 32 in [32, 256]");
   if (t.batch_tile_log2 < 8 || t.batch_tile_log2 > 14) return set_error(ISPRIME_EINVAL, "batch_tile_log2 must be in [8, 14]");
   if (t.batch_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "batch_blocks_per_sm must be in [0, 32]");
+  if (t.base2_window != 0 && t.base2_window != 4) return set_error(ISPRIME_EINVAL, "base2_window must be 0 or 4");
   return ISPRIME_OK;
 }
 

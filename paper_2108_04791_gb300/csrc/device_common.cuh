@@ -92,6 +92,44 @@ __device__ __forceinline__ bool rest64_is_prime(uint64_t n, uint64_t* tab, int l
   return true;
 }
 
+// Base 2 with 4-bit windows: T[w] = 2^w R mod n for w < 16 by doublings,
+// then per nibble of d four squarings and one multiplication by T[w]; this
+// replaces a doubling and a select after every squaring with one
+// multiplication every four.  nib_warp (>= this lane's nibble count, the same
+// for the whole warp) keeps the loop uniform: leading zero nibbles square the
+// Montgomery 1, which stays 1.
+template <int kImpl>
+__device__ __forceinline__ bool base2_passes_win(uint64_t n, uint64_t* tab, int ld, int nib_warp) {
+  using Ops = MontOps<kImpl>;
+  const Mont64 M = mont64_setup(n);
+  uint64_t d = n - 1;
+  const int s = ctz64(d);
+  d >>= s;
+  uint64_t t = M.one;
+  tab[0] = t;
+#pragma unroll
+  for (int w = 1; w < 16; ++w) {
+    t = mod_dbl(t, n);
+    tab[w * ld] = t;
+  }
+  uint64_t e = nib_warp >= 16 ? d : d << (64 - 4 * nib_warp);  // left-aligned exponent
+  uint64_t x = tab[(int)(e >> 60) * ld];
+  for (int k = 1; k < nib_warp; ++k) {
+    e <<= 4;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) x = Ops::sqr(x, M);
+    x = Ops::mul(x, tab[(int)(e >> 60) * ld], M);
+  }
+  return sprp_tail64<kImpl>(M, x, s);
+}
+
+// Number of 4-bit nibbles of the odd part of n - 1.
+__device__ __forceinline__ int base2_nibbles(uint64_t n) {
+  uint64_t d = n - 1;
+  d >>= ctz64(d);
+  return (64 - clz64(d) + 3) >> 2;
+}
+
 // Base 2 for odd n >= 2^32.
 template <int kImpl>
 __device__ __forceinline__ bool base2_passes(uint64_t n) {

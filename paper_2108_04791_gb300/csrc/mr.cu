@@ -25,10 +25,11 @@
 
 namespace ip {
 
-template <int kImpl>
+template <int kImpl, bool kWindow>
 __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restrict__ qn,
                                                          uint32_t* __restrict__ counters,
                                                          uint32_t* __restrict__ q64b) {
+  extern __shared__ uint64_t s_tab[];  // kWindow: 16 x blockDim
   const uint32_t count = *(volatile uint32_t*)&counters[0];
   const int lane = threadIdx.x & 31;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,7 +37,15 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   for (uint32_t wbase = gtid & ~31u; wbase < count; wbase += nthreads) {
     const uint32_t i = wbase + lane;
     bool pass = false;
-    if (i < count) pass = base2_passes<kImpl>(qn[i]);
+    if (i < count) {
+      const uint64_t n = qn[i];
+      if (kWindow) {
+        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
+        pass = base2_passes_win<kImpl>(n, s_tab + threadIdx.x, (int)blockDim.x, nib);
+      } else {
+        pass = base2_passes<kImpl>(n);
+      }
+    }
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, pass);
     if (mask) {
       const int leader = __ffs(mask) - 1;
@@ -73,9 +82,28 @@ __global__ void __launch_bounds__(256) mr32_kernel(const uint32_t* __restrict__ 
     if (mr32_is_prime(qn[i])) out[qidx[i]] = 1;
 }
 
+// Grid of a grid-stride kernel: at most the blocks that can be resident.
+static unsigned resident_grid(const void* fn, unsigned block, size_t smem, int sm_count,
+                              unsigned want) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)block, smem) != cudaSuccess ||
+      per_sm < 1)
+    return want;
+  const unsigned cap = (unsigned)(sm_count * per_sm);
+  return want < cap ? want : cap;
+}
+
 template <int kImpl>
-static void launch_base2(const Queues& q, unsigned grid, unsigned block, cudaStream_t s) {
-  mr64_base2_kernel<kImpl><<<grid, block, 0, s>>>(q.q64_n, q.counters, q.q64b);
+static void launch_base2(const Queues& q, unsigned grid, unsigned block, int window, int sm_count,
+                         cudaStream_t s) {
+  if (window) {
+    const size_t smem = (size_t)16 * block * sizeof(uint64_t);
+    const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, true>);
+    grid = resident_grid(fn, block, smem, sm_count, grid);
+    mr64_base2_kernel<kImpl, true><<<grid, block, smem, s>>>(q.q64_n, q.counters, q.q64b);
+  } else {
+    mr64_base2_kernel<kImpl, false><<<grid, block, 0, s>>>(q.q64_n, q.counters, q.q64b);
+  }
 }
 
 template <int kImpl>
@@ -88,17 +116,17 @@ static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned b
 // impl_b2 selects the arithmetic of the base-2 kernel, impl that of the
 // six-base kernel (see MontOps).
 static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int impl,
-                       int impl_b2, cudaStream_t s, isprime_ctx* ctx) {
+                       int impl_b2, int window, int sm_count, cudaStream_t s, isprime_ctx* ctx) {
   int st = ISPRIME_OK;
   TimedLaunch tl;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
   switch (impl_b2) {
-    case 1: launch_base2<1>(q, grid, block, s); break;
-    case 2: launch_base2<2>(q, grid, block, s); break;
-    case 3: launch_base2<3>(q, grid, block, s); break;
-    case 4: launch_base2<4>(q, grid, block, s); break;
-    case 5: launch_base2<5>(q, grid, block, s); break;
-    default: launch_base2<0>(q, grid, block, s); break;
+    case 1: launch_base2<1>(q, grid, block, window, sm_count, s); break;
+    case 2: launch_base2<2>(q, grid, block, window, sm_count, s); break;
+    case 3: launch_base2<3>(q, grid, block, window, sm_count, s); break;
+    case 4: launch_base2<4>(q, grid, block, window, sm_count, s); break;
+    case 5: launch_base2<5>(q, grid, block, window, sm_count, s); break;
+    default: launch_base2<0>(q, grid, block, window, sm_count, s); break;
   }
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
@@ -125,7 +153,8 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
   return launch_mr64(ctx->q, out, grid, block, (int)ctx->tune.mont_impl,
-                     (int)ctx->tune.mont_impl_base2, s, ctx);
+                     (int)ctx->tune.mont_impl_base2, (int)ctx->tune.base2_window, ctx->sm_count, s,
+                     ctx);
 }
 
 // Launch without a context (explicit grid and block and queue pointers);
@@ -133,7 +162,8 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
 int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, unsigned block,
                   cudaStream_t s) {
   if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
-  launch_mr64(q, out, grid, block, 0, 5, s, nullptr);
+  // binary base-2 schedule (no shared memory), as this launcher always used
+  launch_mr64(q, out, grid, block, 0, 5, /*window=*/0, /*sm_count=*/0, s, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
 }

@@ -195,7 +195,8 @@ def test_tuning_does_not_change_results():
                    dict(mont_impl_base2=0), dict(mont_impl_base2=1), dict(mont_impl_base2=2),
                    dict(mont_impl_base2=3), dict(mont_impl_base2=4), dict(mont_impl_base2=5),
                    dict(td_primes=7), dict(td_primes=11), dict(td_primes=23), dict(td_primes=31),
-                   dict(td_primes=40), dict(mont_impl=0, td_primes=15)]:
+                   dict(td_primes=40), dict(base2_window=0), dict(base2_window=4, mont_impl_base2=0),
+                   dict(mont_impl=0, td_primes=15)]:
             c.set_tuning(**kw)
             _assert_same(v, _gpu(v, c), want)
 
