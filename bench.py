@@ -88,7 +88,8 @@ def _parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--workload", default="plain_large",
-                   choices=["plain_large", "plain_small", "plain_mixed", "batched", "served"])
+                   choices=["plain_large", "plain_small", "plain_mixed", "batched", "served",
+                            "range_1e8", "range_unix2021", "range_2p64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-probe", action="store_true", help="skip the integer-rate probe")
@@ -509,6 +510,56 @@ def run_served(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+RANGES = {
+    "range_1e8": (1, 10**8, "1:10^8 (Table 3's largest incrementing sequence)"),
+    "range_unix2021": (1609477200, 3600 * 24 * 365 + 1, "the Unix seconds of 2021 (Table 5)"),
+    "range_2p64": ((1 << 64) - (1 << 28), 1 << 28, "the last 2^28 integers below 2^64"),
+}
+
+
+def run_range(args, world, rank, local):
+    """isprime_range over a window of consecutive integers (no input array)."""
+    import torch
+    import paper_2108_04791_gb300 as ipg
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    lo, count, desc = RANGES[args.workload]
+    ctx = ipg.Context.default(local)
+    out = torch.empty(count, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    steps, warm = max(args.steps, 1), max(args.warmup, 3)
+    for _ in range(warm):
+        ctx.isprime_range(lo, count, out=out)
+    ctx.timing_reset()
+    ctx.timing(True)
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.isprime_range(lo, count, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.timing(False)
+    t = _max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+    kt = ctx.timing_read()
+    value = count * world * steps / t
+    primes = int(out.sum().item())
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+                "warmup": warm, "ms_per_step": 1e3 * t / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": args.workload, "lo": lo, "count": count, "description": desc,
+                           "primes_found": primes},
+                "roofline": {"bound": "hbm", "bytes_per_value": 1 + (1 / 16 if lo < (1 << 32) else 0),
+                             "achieved_gbs": count * (1 + 1 / 16) * steps / t / 1e9},
+                "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]} for k, v in kt.items()
+                            if v[1]}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse()
     world, rank, local = _dist_init(args)
@@ -518,6 +569,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "served":
         run_served(args, world, rank, local)
+    elif args.workload.startswith("range"):
+        run_range(args, world, rank, local)
     else:
         run_mine(args, world, rank, local)
     if world > 1:

@@ -124,6 +124,16 @@ int isprime_f64(const double *d_in, uint8_t *d_out, size_t n, unsigned long long
 int isprime_f64_ctx(isprime_ctx *ctx, const double *d_in, uint8_t *d_out, size_t n,
                     unsigned long long *d_invalid, isprime_stream stream);
 
+/* Range form: d_out[i] = isprime(lo + i) for i < count, with no input array
+ * (the incrementing sequences 1:N of Sec. 6.1.3 / Table 3 and the windows of
+ * consecutive integers of Table 5).  Requires lo + count <= 2^64.  Values
+ * below the context's sieve limit are read from the resident bitmap; the
+ * rest are sieved in shared memory by the odd primes below 2^16 and the
+ * survivors above 65537^2 finish with the 64-bit Miller-Rabin kernels.
+ * Asynchronous on `stream`. */
+int isprime_range(isprime_ctx *ctx, uint64_t lo, uint64_t count, uint8_t *d_out,
+                  isprime_stream stream);
+
 /* One array of a batch: n values at d_in (8-byte aligned), n bytes at d_out. */
 typedef struct {
   const uint64_t *d_in;
@@ -242,7 +252,8 @@ enum {
   ISPRIME_K_MR32 = 6,
   ISPRIME_K_SIEVE_COUNT = 7,
   ISPRIME_K_BATCHED = 8,
-  ISPRIME_K_COUNT = 9
+  ISPRIME_K_RANGE = 9,
+  ISPRIME_K_COUNT = 10
 };
 
 typedef struct {

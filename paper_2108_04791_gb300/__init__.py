@@ -28,7 +28,7 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ETIMEDOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6
 SIEVE_DEFAULT = (1 << 64) - 1
 KERNEL_NAMES = ["sieve_base", "sieve_segment", "classify_u64", "classify_f64",
-                "mr64_base2", "mr64_rest", "mr32", "sieve_count", "batched"]
+                "mr64_base2", "mr64_rest", "mr32", "sieve_count", "batched", "range"]
 
 
 class IsPrimeError(RuntimeError):
@@ -105,6 +105,7 @@ def lib():
                 "isprime_f64": ([vp, vp, sz, vp, vp], i32),
                 "isprime_f64_ctx": ([vp, vp, vp, sz, vp, vp], i32),
                 "isprime_u64_host": ([vp, vp, vp, sz, vp], i32),
+                "isprime_range": ([vp, u64, u64, vp, vp], i32),
                 "isprime_u64_batched": ([vp, ctypes.POINTER(ArrayDesc), sz, vp], i32),
                 "isprime_autotune": ([vp, vp, vp, sz, i32, ctypes.c_char_p, ctypes.POINTER(Tuning)], i32),
                 "isprime_tuning_format": ([ctypes.POINTER(Tuning), ctypes.c_char_p, sz], i32),
@@ -302,6 +303,17 @@ class Context:
             _check(lib().isprime_u64_batched(self._h, descs, len(srcs), sh))
         self._keep = srcs  # keep converted inputs alive until the stream runs them
         return outs
+
+    def isprime_range(self, lo: int, count: int, out=None, stream=None):
+        """uint8 CUDA tensor r with r[i] = isprime(lo + i), i < count."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        if out is None:
+            out = torch.empty(count, dtype=torch.uint8, device=dev)
+        if count:
+            sh = ctypes.c_void_p((stream or torch.cuda.current_stream(dev)).cuda_stream)
+            _check(lib().isprime_range(self._h, lo, count, out.data_ptr(), sh))
+        return out
 
     def isprime_host(self, values, stream=None) -> np.ndarray:
         """End-to-end call on a host array (copies in, classifies, copies out)."""

@@ -169,8 +169,8 @@ static int ctx_create(int device, uint64_t sieve_limit, isprime_ctx** out) {
   if (sieve_limit) {
     cudaError_t e = cudaMalloc(&ctx->d_sieve, sieve_limit / 16);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(sieve)");
-    if (!st) st = sieve_build(ctx.get(), s);
   }
+  if (!st) st = sieve_build(ctx.get(), s);
   if (!st) st = ensure_queues(ctx.get(), (size_t)1 << 20);
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
@@ -295,6 +295,7 @@ int isprime_ctx_destroy(isprime_ctx* ctx) {
     free_queues(ctx->q);
     cudaFree(ctx->d_sieve);
     cudaFree(ctx->d_base_primes);
+    cudaFree(ctx->d_nprimes);
     cudaFree(ctx->d_stage_in);
     cudaFree(ctx->d_stage_out);
     if (ctx->h_pin_in) cudaFreeHost(ctx->h_pin_in);
@@ -380,6 +381,27 @@ int isprime_f64(const double* d_in, uint8_t* d_out, size_t n, unsigned long long
   st = current_default(&ctx);
   if (st) return st;
   return run_array<true>(ctx, d_in, d_out, n, d_invalid, (cudaStream_t)stream);
+}
+
+int isprime_range(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out,
+                  isprime_stream stream) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  if (count == 0) return ISPRIME_OK;
+  if (!d_out) return set_error(ISPRIME_EINVAL, "d_out is NULL with count > 0");
+  if (count - 1 > UINT64_MAX - lo) return set_error(ISPRIME_EINVAL, "lo + count exceeds 2^64");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard g(ctx->device);
+  const size_t chunk = (size_t)1 << ctx->tune.chunk_log2;
+  int st = ensure_queues(ctx, std::min(chunk, std::max((size_t)std::min<uint64_t>(count, chunk),
+                                                       (size_t)kRangeChunkAlign)));
+  if (st) return st;
+  if ((st = order_before(ctx, s))) return st;
+  if ((st = range_run(ctx, lo, count, d_out, s))) return st;
+  if ((st = order_after(ctx, s))) return st;
+  ctx->stats.calls++;
+  ctx->stats.elements += count;
+  return ISPRIME_OK;
 }
 
 int isprime_u64_batched(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays,

@@ -76,6 +76,7 @@ struct isprime_ctx {
   uint64_t sieve_limit = 0;
   uint32_t* d_sieve = nullptr;       // odd-only bitmap: bit j <-> 2j+1
   uint32_t* d_base_primes = nullptr; // odd primes < 2^16
+  uint32_t* d_nprimes = nullptr;     // their count (device)
   uint32_t n_base_primes = 0;
   ip::Queues q;
   isprime_tuning tune{};
@@ -111,6 +112,11 @@ int launch_end(isprime_ctx* ctx, cudaStream_t s, TimedLaunch* tl, const char* na
 
 // sieve.cu
 int sieve_build(isprime_ctx* ctx, cudaStream_t s);
+int ensure_base_primes(isprime_ctx* ctx, cudaStream_t s);
+
+// range.cu
+int range_run(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out, cudaStream_t s);
+constexpr uint64_t kRangeChunkAlign = 1u << 15;  // integers per sieve segment
 int sieve_count(isprime_ctx* ctx, cudaStream_t s, uint64_t* d_out);
 
 // classify.cu

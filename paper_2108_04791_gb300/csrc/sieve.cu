@@ -169,25 +169,34 @@ __global__ void sieve_count_kernel(const uint32_t* bitmap, uint64_t total_words,
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, (unsigned long long)acc);
 }
 
-int sieve_build(isprime_ctx* ctx, cudaStream_t s) {
-  if (ctx->sieve_limit == 0) return ISPRIME_OK;
-  const uint64_t total_words = ctx->sieve_limit / 64;
-  uint32_t* d_count = nullptr;
+// The odd primes below 2^16 and their count, kept on the device by every
+// context (the segmented sieves of sieve_build and of range.cu use them).
+int ensure_base_primes(isprime_ctx* ctx, cudaStream_t s) {
+  if (ctx->d_base_primes) return ISPRIME_OK;
   IP_CUDA(cudaMalloc(&ctx->d_base_primes, 8192 * sizeof(uint32_t)));
-  IP_CUDA(cudaMalloc(&d_count, sizeof(uint32_t)));
+  IP_CUDA(cudaMalloc(&ctx->d_nprimes, sizeof(uint32_t)));
   TimedLaunch tl;
   int st = launch_begin(ctx, ISPRIME_K_SIEVE_BASE, s, &tl);
   if (st) return st;
-  sieve_base_kernel<<<1, kBaseThreads, 0, s>>>(ctx->d_base_primes, d_count);
+  sieve_base_kernel<<<1, kBaseThreads, 0, s>>>(ctx->d_base_primes, ctx->d_nprimes);
   if ((st = launch_end(ctx, s, &tl, "sieve_base_kernel"))) return st;
+  IP_CUDA(cudaMemcpyAsync(&ctx->n_base_primes, ctx->d_nprimes, sizeof(uint32_t),
+                          cudaMemcpyDeviceToHost, s));
+  IP_CUDA(cudaStreamSynchronize(s));
+  return ISPRIME_OK;
+}
+
+int sieve_build(isprime_ctx* ctx, cudaStream_t s) {
+  int st = ensure_base_primes(ctx, s);
+  if (st || ctx->sieve_limit == 0) return st;
+  const uint64_t total_words = ctx->sieve_limit / 64;
   const uint64_t nseg = (total_words + kSegWords - 1) / kSegWords;
+  TimedLaunch tl;
   if ((st = launch_begin(ctx, ISPRIME_K_SIEVE_SEGMENT, s, &tl))) return st;
   sieve_segment_kernel<<<(unsigned)nseg, kSegThreads, 0, s>>>(ctx->d_sieve, total_words,
-                                                               ctx->d_base_primes, d_count);
+                                                               ctx->d_base_primes, ctx->d_nprimes);
   if ((st = launch_end(ctx, s, &tl, "sieve_segment_kernel"))) return st;
-  IP_CUDA(cudaMemcpyAsync(&ctx->n_base_primes, d_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   IP_CUDA(cudaStreamSynchronize(s));
-  IP_CUDA(cudaFree(d_count));
   return ISPRIME_OK;
 }
 

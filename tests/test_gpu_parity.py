@@ -343,3 +343,55 @@ def test_autotune_keeps_results_exact_and_caches(tmp_path):
     with ipg.Context(0, sieve_limit=1 << 24) as c2:  # a cache hit installs the same tuning
         assert c2.autotune(_to_dev(v), mode="plain", cache_path=cache) == t1
         assert c2.autotune(_to_dev(v), mode="batched", cache_path=cache) == tb
+
+
+# ------------------------------------------------------------------ range form
+
+def _range(ctx, lo, count):
+    out = ctx.isprime_range(lo, count)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("lo,count", [(0, 10**6), (1, 999_999), (7, 1), (2, 3),
+                                      ((1 << 32) - 100_000, 200_000),
+                                      ((1 << 40) + 1, (1 << 21) + 3),
+                                      ((1 << 64) - (1 << 20), 1 << 20),
+                                      ((1 << 64) - 5, 5)])
+def test_range_matches_oracle(lo, count, ctx_nosieve, ctx_small_sieve):
+    vals = np.uint64(lo) + np.arange(count, dtype=np.uint64)
+    want = oracle.isprime_u64(vals)
+    for ctx in (ipg.Context.default(0), ctx_nosieve, ctx_small_sieve):
+        _assert_same(vals, _range(ctx, lo, count), want)
+
+
+def test_range_unix_seconds_2021_and_pi_1e8():
+    """Table 5's window (the Unix seconds of 2021) and Table 3's 1:10^8."""
+    lo, count = 1609477200, 3600 * 24 * 365 + 1
+    vals = np.uint64(lo) + np.arange(count, dtype=np.uint64)
+    ctx = ipg.Context.default(0)
+    _assert_same(vals, _range(ctx, lo, count), oracle.isprime_u64(vals))
+    out = ctx.isprime_range(1, 10**8)
+    assert int(out.sum().item()) == 5761455  # pi(10^8)
+    with ipg.Context(0, sieve_limit=0) as c0:  # the sieve path gives the same count
+        assert int(c0.isprime_range(1, 10**8).sum().item()) == 5761455
+
+
+def test_range_misaligned_output_and_argument_checks():
+    ctx = ipg.Context.default(0)
+    buf = torch.zeros(1003, dtype=torch.uint8, device="cuda")
+    ctx.isprime_range(999_983, 1000, out=buf[3:])   # output starts at an odd address
+    torch.cuda.synchronize()
+    vals = np.uint64(999_983) + np.arange(1000, dtype=np.uint64)
+    assert buf[3:].cpu().numpy().tolist() == oracle.isprime_u64(vals).tolist()
+    with pytest.raises(ipg.IsPrimeError):
+        ctx.isprime_range((1 << 64) - 3, 4)          # lo + count > 2^64
+
+
+def test_range_expand_ends_at_the_sieve_limit():
+    """Windows that end exactly at S (the last bitmap word) and cross it."""
+    with ipg.Context(0, sieve_limit=1 << 20) as c:
+        for lo, count in [((1 << 20) - 4096, 4096), ((1 << 20) - 17, 17), ((1 << 20) - 33, 100),
+                          ((1 << 20) - 16, 16)]:
+            vals = np.uint64(lo) + np.arange(count, dtype=np.uint64)
+            _assert_same(vals, _range(c, lo, count), oracle.isprime_u64(vals))
