@@ -70,7 +70,11 @@ typedef struct {
   uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */
   uint32_t batch_blocks_per_sm; /* cap on resident batched blocks per SM (0 = occupancy limit) */
   uint32_t base2_window;   /* base-2 exponentiation: 0 binary with doublings, 4 4-bit windows */
-  uint32_t reserved[2];
+  uint32_t rest_test;      /* after base 2: 0 the six remaining bases of Eq. 4 (default), 1 the
+                              strong Lucas test with Selfridge's parameters (Baillie-PSW).
+                              Both are exact below 2^64; 1 rests on the published search
+                              finding no Baillie-PSW pseudoprime below 2^64. */
+  uint32_t reserved[1];
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -43,7 +43,8 @@ class Tuning(ctypes.Structure):
                 ("chunk_log2", ctypes.c_uint32), ("mont_impl", ctypes.c_uint32),
                 ("mont_impl_base2", ctypes.c_uint32), ("batch_block", ctypes.c_uint32),
                 ("batch_tile_log2", ctypes.c_uint32), ("batch_blocks_per_sm", ctypes.c_uint32),
-                ("base2_window", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+                ("base2_window", ctypes.c_uint32), ("rest_test", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -84,6 +84,7 @@ static isprime_tuning default_tuning() {
   t.batch_tile_log2 = 10;
   t.batch_blocks_per_sm = 0;
   t.base2_window = 4;
+  t.rest_test = 0;
   return t;
 }
 
@@ -100,6 +101,7 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.batch_tile_log2 < 8 || t.batch_tile_log2 > 14) return set_error(ISPRIME_EINVAL, "batch_tile_log2 must be in [8, 14]");
   if (t.batch_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "batch_blocks_per_sm must be in [0, 32]");
   if (t.base2_window != 0 && t.base2_window != 4) return set_error(ISPRIME_EINVAL, "base2_window must be 0 or 4");
+  if (t.rest_test > 1) return set_error(ISPRIME_EINVAL, "rest_test must be 0 or 1");
   return ISPRIME_OK;
 }
 

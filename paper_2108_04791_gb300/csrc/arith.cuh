@@ -16,6 +16,7 @@
 #define IP_HD __host__ __device__ __forceinline__
 #else
 #define IP_HD inline
+#include <math.h>
 #endif
 
 namespace ip {
@@ -423,6 +424,159 @@ IP_HD uint64_t mont_pow_binary(const Mont64& M, uint64_t aR, uint64_t d) {
     if ((d >> b) & 1) x = MontOps<kImpl>::mul(x, aR, M);
   }
   return x;
+}
+
+// ---------------------------------------------------------------------------
+// Strong Lucas probable-prime test with Selfridge's parameters (Baillie and
+// Wagstaff, Math. Comp. 35, 1980): D is the first of 5, -7, 9, -11, ... with
+// Jacobi symbol (D/n) = -1, P = 1, Q = (1 - D)/4; with n + 1 = 2^s d, d odd,
+// n passes if U_d = 0 or V_(d 2^r) = 0 (mod n) for some 0 <= r < s.  After
+// the base-2 strong test this is the Baillie-PSW test.
+// ---------------------------------------------------------------------------
+
+// Jacobi symbol (a/n) for odd n > 0 and |a| < 2^62, binary algorithm.
+IP_HD int jacobi_symbol(int64_t a, uint64_t n) {
+  uint64_t x = a >= 0 ? (uint64_t)a % n : (n - ((uint64_t)(-a) % n)) % n;
+  uint64_t m = n;
+  int t = 1;
+  while (x != 0) {
+    while ((x & 1) == 0) {
+      x >>= 1;
+      const uint64_t r = m & 7;
+      if (r == 3 || r == 5) t = -t;
+    }
+    const uint64_t tmp = x;
+    x = m;
+    m = tmp;
+    if ((x & 3) == 3 && (m & 3) == 3) t = -t;
+    x %= m;
+  }
+  return m == 1 ? t : 0;
+}
+
+// Jacobi symbol (D/n) for odd n > 0 and a small odd D (|D| < 2^16): by
+// reciprocity (D/n) = sign * (n mod |D| / |D|), and n mod |D| splits into
+// 32-bit steps (n = h 2^32 + l), so everything after that is 32-bit.
+IP_HD int jacobi_small(int32_t D, uint64_t n) {
+  int t = 1;
+  uint32_t a = (uint32_t)(D < 0 ? -D : D);
+  if (D < 0 && (n & 3) == 3) t = -t;  // (-1/n) = (-1)^((n-1)/2)
+  if ((a & 3) == 3 && (n & 3) == 3) t = -t;  // reciprocity for odd a, n
+  const uint32_t h = (uint32_t)(n >> 32), l = (uint32_t)n;
+  const uint32_t c = (0xFFFFFFFFu % a + 1u) % a;  // 2^32 mod a
+  uint32_t x = ((h % a) * c % a + l % a) % a;     // n mod a; (h % a) * c < a^2 < 2^32
+  uint32_t m = a;
+  while (x != 0) {
+    while ((x & 1) == 0) {
+      x >>= 1;
+      const uint32_t r = m & 7;
+      if (r == 3 || r == 5) t = -t;
+    }
+    const uint32_t tmp = x;
+    x = m;
+    m = tmp;
+    if ((x & 3) == 3 && (m & 3) == 3) t = -t;
+    x %= m;
+  }
+  return m == 1 ? t : 0;
+}
+
+// floor(sqrt(n))^2 == n for n < 2^64.
+IP_HD bool is_square64(uint64_t n) {
+  uint64_t r = (uint64_t)sqrt((double)n);
+  if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
+  while (r * r > n) --r;
+  while (r < 0xFFFFFFFFull && (r + 1) * (r + 1) <= n) ++r;
+  return r * r == n;
+}
+
+IP_HD uint64_t mod_add(uint64_t a, uint64_t b, uint64_t n) {  // a, b < n
+  const uint64_t s = a + b;
+  return (s < a || s >= n) ? s - n : s;
+}
+IP_HD uint64_t mod_sub(uint64_t a, uint64_t b, uint64_t n) {  // a, b < n
+  return a >= b ? a - b : a - b + n;
+}
+IP_HD uint64_t mod_half(uint64_t x, uint64_t n) {  // x / 2 mod n for odd n, x < n
+  return (x & 1) ? (x >> 1) + (n >> 1) + 1 : x >> 1;
+}
+
+// Montgomery form of a small signed integer c (|c| < n).
+template <int kImpl>
+IP_HD uint64_t mont_from_small(int64_t c, uint64_t r2, const Mont64& M) {
+  const uint64_t m = MontOps<kImpl>::mul(c >= 0 ? (uint64_t)c : (uint64_t)(-c), r2, M);
+  return (c >= 0 || m == 0) ? m : M.n - m;
+}
+
+// Selfridge's D for odd n: the first of 5, -7, 9, -11, ... with (D/n) = -1.
+// Returns 0 with *D set, or 1 if the search shows n composite (a D sharing a
+// factor with n, or n a perfect square, for which no such D exists).
+IP_HD int lucas_next_D(uint64_t n, int32_t* D, int* k) {  // one search step: -1 still searching
+  const int j = jacobi_small(*D, n);
+  if (j == -1) return 0;
+  if (j == 0) return 1;                          // gcd(D, n) > 1 and |D| < n
+  if (*k == 8 && is_square64(n)) return 1;       // squares have no D with (D/n) = -1
+  *D = *D > 0 ? -(*D + 2) : -*D + 2;
+  ++*k;
+  return -1;
+}
+
+// The Lucas ladder for U_d, V_d (P = 1, Q = (1 - D)/4) over the low `nbits`
+// bits of d (nbits >= bitlen(d)), then the strong condition.  It starts from
+// k = 0: (U_0, V_0, Q^0) = (0, 2, 1) is fixed by doubling, so leading zero
+// bits cost time but not correctness; a warp can run one uniform count.
+template <int kImpl>
+IP_HD bool lucas_ladder(uint64_t n, int32_t D, int nbits) {
+  using Ops = MontOps<kImpl>;
+  const int64_t Q = (1 - (int64_t)D) / 4;
+  const Mont64 M = mont64_setup(n);
+  const uint64_t r2 = mont64_r2<kImpl>(M);
+  const uint64_t Dm = mont_from_small<kImpl>(D, r2, M);
+  const uint64_t Qm = mont_from_small<kImpl>(Q, r2, M);
+  uint64_t d = n + 1;
+  const int s = ctz64(d);
+  d >>= s;
+  uint64_t U = 0, V = mod_dbl(M.one, n), Qk = M.one;
+  for (int b = nbits - 1; b >= 0; --b) {
+    // k -> 2k
+    U = Ops::mul(U, V, M);
+    V = mod_sub(Ops::sqr(V, M), mod_dbl(Qk, n), n);
+    Qk = Ops::sqr(Qk, M);
+    // 2k -> 2k + 1 when the bit is set (computed always and selected)
+    const uint64_t U1 = mod_half(mod_add(U, V, n), n);
+    const uint64_t V1 = mod_half(mod_add(Ops::mul(Dm, U, M), V, n), n);
+    const uint64_t Q1 = Ops::mul(Qk, Qm, M);
+    const bool bit = (d >> b) & 1;
+    U = bit ? U1 : U;
+    V = bit ? V1 : V;
+    Qk = bit ? Q1 : Qk;
+  }
+  if (U == 0 || V == 0) return true;
+  for (int r = 1; r < s; ++r) {
+    V = mod_sub(Ops::sqr(V, M), mod_dbl(Qk, n), n);
+    if (V == 0) return true;
+    Qk = Ops::sqr(Qk, M);
+  }
+  return false;
+}
+
+IP_HD int lucas_bits(uint64_t n) {  // bit length of the odd part of n + 1
+  uint64_t d = n + 1;
+  d >>= ctz64(d);
+  return 64 - clz64(d);
+}
+
+// n odd, n > 2^32, not divisible by small primes.  Returns the strong
+// Lucas probable-prime verdict (single-lane form).
+template <int kImpl>
+IP_HD bool strong_lucas_selfridge(uint64_t n) {
+  if (n == ~0ull) return false;  // 2^64 - 1 = 3 * 5 * 17 * 257 * 641 * 65537 * 6700417
+  int32_t D = 5;
+  int k = 0, st;
+  while ((st = lucas_next_D(n, &D, &k)) < 0) {
+  }
+  if (st) return false;
+  return lucas_ladder<kImpl>(n, D, lucas_bits(n));
 }
 
 // ---------------------------------------------------------------------------

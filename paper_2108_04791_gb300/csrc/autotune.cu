@@ -60,14 +60,14 @@ std::string cache_key(int device, size_t n, int mode) {
 
 const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_primes", "chunk_log2",
                          "mont_impl", "mont_impl_base2", "batch_block", "batch_tile_log2",
-                         "batch_blocks_per_sm", "base2_window"};
+                         "batch_blocks_per_sm", "base2_window", "rest_test"};
 uint32_t isprime_tuning::*kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
     &isprime_tuning::mont_impl_base2, &isprime_tuning::batch_block,
     &isprime_tuning::batch_tile_log2, &isprime_tuning::batch_blocks_per_sm,
-    &isprime_tuning::base2_window};
-constexpr int kNumFields = 11;
+    &isprime_tuning::base2_window, &isprime_tuning::rest_test};
+constexpr int kNumFields = 12;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

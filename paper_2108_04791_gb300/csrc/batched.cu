@@ -64,7 +64,7 @@ size_t batched_smem_bytes(uint32_t block, uint32_t tile) {
 // squaring (MontOps<0>); the better choice for each stage on this GPU.
 constexpr int kImplB2 = 5, kImplRest = 0;
 
-template <int kNtd>
+template <int kNtd, bool kLucas>
 __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
   extern __shared__ __align__(16) uint64_t s_dyn[];
   __shared__ uint32_t s_n1, s_n2, s_tile, s_arr;
@@ -114,7 +114,11 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
     }
     __syncthreads();
     if (tid == 0) s_n2 = n2 - cnt;
-    if (mine && rest64_is_prime<kImplRest>(v, tab, (int)B)) *reinterpret_cast<uint8_t*>(a) = 1;
+    if (kLucas) {  // every thread of the block takes part (warp-synchronous test)
+      if (lucas_warp<kImplRest>(mine ? v : 0xFFFFFFFFFFFFFFC5ull, mine)) *reinterpret_cast<uint8_t*>(a) = 1;
+    } else if (mine && rest64_is_prime<kImplRest>(v, tab, (int)B)) {
+      *reinterpret_cast<uint8_t*>(a) = 1;
+    }
     __syncthreads();
   };
 
@@ -172,10 +176,10 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
 
 using BatchLauncher = void (*)(const BatchParams&, unsigned, unsigned, size_t, cudaStream_t);
 
-template <int kNtd>
+template <int kNtd, bool kLucas>
 static void launch_batched_t(const BatchParams& p, unsigned grid, unsigned block, size_t smem,
                              cudaStream_t s) {
-  batched_kernel<kNtd><<<grid, block, smem, s>>>(p);
+  batched_kernel<kNtd, kLucas><<<grid, block, smem, s>>>(p);
 }
 
 struct BatchVariant {
@@ -184,12 +188,17 @@ struct BatchVariant {
 };
 
 // Compiled trial-division counts; other counts use the runtime-count kernel.
-static BatchVariant pick_variant(uint32_t ntd) {
+template <bool kLucas>
+static BatchVariant pick_ntd(uint32_t ntd) {
   switch (ntd) {
-    case 15: return {launch_batched_t<15>, reinterpret_cast<const void*>(&batched_kernel<15>)};
-    case 23: return {launch_batched_t<23>, reinterpret_cast<const void*>(&batched_kernel<23>)};
-    default: return {launch_batched_t<-1>, reinterpret_cast<const void*>(&batched_kernel<-1>)};
+    case 15: return {launch_batched_t<15, kLucas>, reinterpret_cast<const void*>(&batched_kernel<15, kLucas>)};
+    case 23: return {launch_batched_t<23, kLucas>, reinterpret_cast<const void*>(&batched_kernel<23, kLucas>)};
+    default: return {launch_batched_t<-1, kLucas>, reinterpret_cast<const void*>(&batched_kernel<-1, kLucas>)};
   }
+}
+
+static BatchVariant pick_variant(uint32_t ntd, uint32_t lucas) {
+  return lucas ? pick_ntd<true>(ntd) : pick_ntd<false>(ntd);
 }
 
 // Grid: every SM full of resident blocks (occupancy with this shared memory).
@@ -263,10 +272,11 @@ int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, s
   bs->ev_valid = true;
 
   // The graph: reset the tile counter, launch the persistent kernel.
-  const BatchVariant v = pick_variant(ctx->tune.td_primes);
+  const BatchVariant v = pick_variant(ctx->tune.td_primes, ctx->tune.rest_test);
   const size_t smem = batched_smem_bytes(block, tile);
   const uint64_t key = ((uint64_t)block << 40) ^ ((uint64_t)tile << 8) ^ ctx->tune.td_primes ^
-                       ((uint64_t)ctx->tune.batch_blocks_per_sm << 56);
+                       ((uint64_t)ctx->tune.batch_blocks_per_sm << 56) ^
+                       ((uint64_t)ctx->tune.rest_test << 62);
   if (!bs->exec || bs->key != key) {
     if (bs->exec) {
       IP_CUDA(cudaStreamSynchronize(s));

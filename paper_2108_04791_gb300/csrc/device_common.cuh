@@ -130,6 +130,23 @@ __device__ __forceinline__ int base2_nibbles(uint64_t n) {
   return (64 - clz64(d) + 3) >> 2;
 }
 
+// Warp-synchronous strong Lucas test: all 32 lanes of a converged warp call
+// it (lanes with valid == false pass any odd n and ignore the result).  The
+// D search advances in lock step until every lane has its D, and the ladder
+// runs the warp's largest bit count, so the lanes never split into groups
+// that would run the ladder one after another.
+template <int kImpl>
+__device__ __forceinline__ bool lucas_warp(uint64_t n, bool valid) {
+  int32_t D = 5;
+  int k = 0, st = (n == ~0ull) ? 1 : -1;
+  while (__any_sync(0xFFFFFFFFu, st < 0)) {
+    if (st < 0) st = lucas_next_D(n, &D, &k);
+  }
+  const int nb = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)lucas_bits(n));
+  const bool prime = lucas_ladder<kImpl>(n, st ? 5 : D, nb);
+  return valid && st == 0 && prime;
+}
+
 // Base 2 for odd n >= 2^32.
 template <int kImpl>
 __device__ __forceinline__ bool base2_passes(uint64_t n) {

@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   }
 }
 
-template <int kImpl>
+// kLucas: the strong Lucas test (Baillie-PSW with the base-2 stage) instead
+// of the six remaining Miller-Rabin bases.
+template <int kImpl, bool kLucas>
 __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restrict__ qn,
                                                         const uint32_t* __restrict__ qidx,
                                                         const uint32_t* __restrict__ q64b,
@@ -67,6 +69,19 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   uint64_t* tab = s_tab + threadIdx.x;
   const int ld = blockDim.x;
   const uint32_t count = *(volatile const uint32_t*)&counters[2];
+  if (kLucas) {  // whole warps per iteration: lucas_warp is warp-synchronous
+    const int lane = threadIdx.x & 31;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    for (uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; wbase < count;
+         wbase += nthreads) {
+      const uint32_t i = wbase + lane;
+      const bool valid = i < count;
+      const uint32_t j = valid ? q64b[i] : 0u;
+      const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
+      if (lucas_warp<kImpl>(n, valid)) out[qidx[j]] = 1;
+    }
+    return;
+  }
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const uint32_t j = q64b[i];
     if (rest64_is_prime<kImpl>(qn[j], tab, ld)) out[qidx[j]] = 1;
@@ -107,16 +122,21 @@ static void launch_base2(const Queues& q, unsigned grid, unsigned block, int win
 }
 
 template <int kImpl>
-static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int lucas,
                         cudaStream_t s) {
-  const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
-  mr64_rest_kernel<kImpl><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+  if (lucas) {
+    mr64_rest_kernel<kImpl, true><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+  } else {
+    const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
+    mr64_rest_kernel<kImpl, false><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+  }
 }
 
 // impl_b2 selects the arithmetic of the base-2 kernel, impl that of the
 // six-base kernel (see MontOps).
 static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int impl,
-                       int impl_b2, int window, int sm_count, cudaStream_t s, isprime_ctx* ctx) {
+                       int impl_b2, int window, int lucas, int sm_count, cudaStream_t s,
+                       isprime_ctx* ctx) {
   int st = ISPRIME_OK;
   TimedLaunch tl;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
@@ -131,12 +151,12 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
   switch (impl) {
-    case 1: launch_rest<1>(q, out, grid, block, s); break;
-    case 2: launch_rest<2>(q, out, grid, block, s); break;
-    case 3: launch_rest<3>(q, out, grid, block, s); break;
-    case 4: launch_rest<4>(q, out, grid, block, s); break;
-    case 5: launch_rest<5>(q, out, grid, block, s); break;
-    default: launch_rest<0>(q, out, grid, block, s); break;
+    case 1: launch_rest<1>(q, out, grid, block, lucas, s); break;
+    case 2: launch_rest<2>(q, out, grid, block, lucas, s); break;
+    case 3: launch_rest<3>(q, out, grid, block, lucas, s); break;
+    case 4: launch_rest<4>(q, out, grid, block, lucas, s); break;
+    case 5: launch_rest<5>(q, out, grid, block, lucas, s); break;
+    default: launch_rest<0>(q, out, grid, block, lucas, s); break;
   }
   if (ctx) st = launch_end(ctx, s, &tl, "mr64_rest_kernel");
   return st;
@@ -153,8 +173,8 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
   return launch_mr64(ctx->q, out, grid, block, (int)ctx->tune.mont_impl,
-                     (int)ctx->tune.mont_impl_base2, (int)ctx->tune.base2_window, ctx->sm_count, s,
-                     ctx);
+                     (int)ctx->tune.mont_impl_base2, (int)ctx->tune.base2_window,
+                     (int)ctx->tune.rest_test, ctx->sm_count, s, ctx);
 }
 
 // Launch without a context (explicit grid and block and queue pointers);
@@ -163,7 +183,7 @@ int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, 
                   cudaStream_t s) {
   if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
   // binary base-2 schedule (no shared memory), as this launcher always used
-  launch_mr64(q, out, grid, block, 0, 5, /*window=*/0, /*sm_count=*/0, s, nullptr);
+  launch_mr64(q, out, grid, block, 0, 5, /*window=*/0, /*lucas=*/0, /*sm_count=*/0, s, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
 }

@@ -98,3 +98,13 @@ extern "C" uint64_t h_stress(uint64_t seed, uint64_t count, int variant) {
   }
   return bad;
 }
+
+extern "C" {
+int h_jacobi(int64_t a, uint64_t n) { return ip::jacobi_symbol(a, n); }
+int h_jacobi_small(int32_t a, uint64_t n) { return ip::jacobi_small(a, n); }
+int h_is_square(uint64_t n) { return ip::is_square64(n); }
+int h_strong_lucas(uint64_t n) {
+  const int r0 = ip::strong_lucas_selfridge<0>(n), r5 = ip::strong_lucas_selfridge<5>(n);
+  return r0 == r5 ? r0 : -1;
+}
+}

@@ -167,3 +167,50 @@ def strong_base2(n: int) -> bool:
         if x == n - 1:
             return True
     return False
+
+
+def jacobi(a: int, n: int) -> int:
+    """Jacobi symbol (a/n), n odd positive (quadratic reciprocity, Python ints)."""
+    a %= n
+    t = 1
+    while a:
+        while a % 2 == 0:
+            a //= 2
+            if n % 8 in (3, 5):
+                t = -t
+        a, n = n, a
+        if a % 4 == 3 and n % 4 == 3:
+            t = -t
+        a %= n
+    return t if n == 1 else 0
+
+
+def strong_lucas(n: int) -> bool:
+    """Strong Lucas probable prime, Selfridge's method A (D = 5, -7, 9, ...,
+    P = 1, Q = (1 - D)/4), from the Lucas sequences' definition with
+    exact integer doubling formulas.  n odd, not a perfect square."""
+    D = 5
+    while jacobi(D, n) != -1:
+        if jacobi(D, n) == 0 and abs(D) != n:
+            return False
+        D = -(D + 2) if D > 0 else -D + 2
+    P, Q = 1, (1 - D) // 4
+    d, s = n + 1, 0
+    while d % 2 == 0:
+        d //= 2
+        s += 1
+    inv2 = (n + 1) // 2
+    U, V, Qk = 1, P, Q % n
+    for bit in bin(d)[3:]:
+        U, V, Qk = U * V % n, (V * V - 2 * Qk) % n, Qk * Qk % n
+        if bit == "1":
+            U, V = (P * U + V) * inv2 % n, (D * U + P * V) * inv2 % n
+            Qk = Qk * Q % n
+    if U == 0 or V == 0:
+        return True
+    for _ in range(s - 1):
+        V = (V * V - 2 * Qk) % n
+        if V == 0:
+            return True
+        Qk = Qk * Qk % n
+    return False

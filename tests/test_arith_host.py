@@ -7,6 +7,7 @@ divisibility test, and the strong tests.  The GPU kernels use the same
 source; the GPU parity tests cover the kernels themselves.
 """
 import ctypes
+import math
 import os
 import random
 import subprocess
@@ -35,7 +36,10 @@ def H(tmp_path_factory):
                             ("h_mont_mul_w", [u64, u64, u64], u64), ("h_mont_sqr_w", [u64, u64], u64),
                             ("h_mont_sqr_h", [u64, u64], u64),
                             ("h_mont_mul_f", [u64, u64, u64], u64), ("h_mont_sqr_f", [u64, u64], u64),
-                            ("h_stress", [u64, u64, i32], u64)]:
+                            ("h_stress", [u64, u64, i32], u64),
+                            ("h_jacobi", [ctypes.c_int64, u64], i32), ("h_is_square", [u64], i32),
+                            ("h_jacobi_small", [ctypes.c_int32, u64], i32),
+                            ("h_strong_lucas", [u64], i32)]:
         f = getattr(L, name)
         f.argtypes, f.restype = args, res
     return L
@@ -142,3 +146,44 @@ def test_divisibility_by_inverse(H):
             assert bool(H.h_td64(v, i)) == (v % p == 0)
             v32 = v & 0xFFFFFFFF
             assert bool(H.h_td32(v32, i)) == (v32 % p == 0)
+
+
+def test_jacobi_and_squares(H):
+    rng = random.Random(21)
+    for _ in range(3000):
+        n = rng.randrange(3, R) | 1
+        a = rng.randrange(-1000, 1000)
+        assert H.h_jacobi(a, n) == nt.jacobi(a, n), (a, n)
+        D = rng.choice([5, -7, 9, -11, 13, -15, 17, -19, 21, -23, 25, -27, 29, -31, 65535, -65535])
+        assert H.h_jacobi_small(D, n) == nt.jacobi(D, n), (D, n)
+    for _ in range(2000):
+        r = rng.randrange(1, 1 << 32)
+        assert H.h_is_square(r * r) == 1
+        assert H.h_is_square(r * r - 1) == (r == 1)  # r^2 - 1 is a square only for r = 1
+    assert H.h_is_square((1 << 64) - 1) == 0 and H.h_is_square(0) == 1
+
+
+STRONG_LUCAS_PSEUDOPRIMES = [5459, 5777, 10877, 16109, 18971, 22499, 24569, 25199, 40309, 58519]
+
+
+def test_strong_lucas_against_independent_python():
+    """The independent Python test reproduces the known Selfridge strong Lucas
+    pseudoprimes (OEIS A217255's first terms) and nothing else below 6*10^4."""
+    found = [n for n in range(3, 60000, 2) if not nt.trial_is_prime(n)
+             and int(math.isqrt(n)) ** 2 != n and nt.strong_lucas(n)]
+    assert found == STRONG_LUCAS_PSEUDOPRIMES
+
+
+def test_strong_lucas_device_source_on_large_values(H):
+    rng = random.Random(22)
+    vals = [rng.randrange(1 << 32, R) | 1 for _ in range(4000)]
+    vals += [p for p in (2**61 - 1, 2**63 - 25, 2**64 - 59)]
+    vals += [p * q for p, q in ((4294967291, 4294967279), (3037000493, 3037000453))]
+    for n in vals:
+        if any(n % p == 0 for p in (3, 5, 7, 11, 13)):
+            continue
+        if int(math.isqrt(n)) ** 2 == n:
+            continue
+        assert H.h_strong_lucas(n) == int(nt.strong_lucas(n)), n
+    # squares are rejected
+    assert H.h_strong_lucas(4294967291 ** 2) == 0

@@ -196,6 +196,7 @@ def test_tuning_does_not_change_results():
                    dict(mont_impl_base2=3), dict(mont_impl_base2=4), dict(mont_impl_base2=5),
                    dict(td_primes=7), dict(td_primes=11), dict(td_primes=23), dict(td_primes=31),
                    dict(td_primes=40), dict(base2_window=0), dict(base2_window=4, mont_impl_base2=0),
+                   dict(rest_test=1), dict(rest_test=1, mont_impl=5), dict(rest_test=0),
                    dict(mont_impl=0, td_primes=15)]:
             c.set_tuning(**kw)
             _assert_same(v, _gpu(v, c), want)
@@ -395,3 +396,49 @@ def test_range_expand_ends_at_the_sieve_limit():
                           ((1 << 20) - 16, 16)]:
             vals = np.uint64(lo) + np.arange(count, dtype=np.uint64)
             _assert_same(vals, _range(c, lo, count), oracle.isprime_u64(vals))
+
+
+# ------------------------------------------------------------------ Baillie-PSW option
+
+@pytest.fixture(scope="module")
+def ctx_bpsw():
+    _dev()
+    with ipg.Context(0) as c:
+        c.set_tuning(rest_test=1)
+        yield c
+
+
+def test_bpsw_full_bench_array_and_mixed(ctx_bpsw):
+    for v in (plain_large(), plain_mixed(1 << 22, seed=101), np.array(SPECIAL, dtype=np.uint64)):
+        _assert_same(v, _gpu(v, ctx_bpsw), oracle.isprime_u64(v))
+
+
+def test_bpsw_rejects_base2_strong_pseudoprimes(ctx_bpsw):
+    """Composites that pass the base-2 stage: the Lucas stage must reject them."""
+    import random
+    import numtheory as nt
+    rng = random.Random(103)
+    spsp = []
+    while len(spsp) < 40:  # p (2p - 1) with both prime, near 2^63, that pass base 2
+        p = rng.randrange(2**31, 3_000_000_000) | 1
+        q = 2 * p - 1
+        if nt.trial_is_prime(p) and nt.trial_is_prime(q) and nt.strong_base2(p * q):
+            spsp.append(p * q)
+    N = 2_000_000
+    comp = ~nt.simple_sieve(N)
+    small = [n for n in range(9, N, 2) if comp[n] and nt.strong_base2(n)]
+    v = np.array(spsp + small, dtype=np.uint64)
+    assert not _gpu(v, ctx_bpsw).any()
+    with ipg.Context(0, sieve_limit=0) as c0:  # small ones through MR32 / Lucas, no sieve
+        c0.set_tuning(rest_test=1)
+        assert not _gpu(v, c0).any()
+
+
+def test_bpsw_batched(ctx_bpsw):
+    from workloads import batched_arrays
+    vals, offs = batched_arrays(n_arrays=64, max_size=1 << 15, seed=104)
+    arrays = [vals[offs[i]:offs[i + 1]] for i in range(64)]
+    outs = ctx_bpsw.isprime_batched([_to_dev(a) for a in arrays])
+    torch.cuda.synchronize()
+    for a, o in zip(arrays, outs):
+        _assert_same(a, o.cpu().numpy(), oracle.isprime_u64(a))
