@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
     if (tid == 0) s_n2 = n2 - cnt;
     if (kLucas) {  // every thread of the block takes part (warp-synchronous test)
       if (lucas_warp<kImplRest>(mine ? v : 0xFFFFFFFFFFFFFFC5ull, mine)) *reinterpret_cast<uint8_t*>(a) = 1;
-    } else if (mine && rest64_is_prime<kImplRest>(v, tab, (int)B)) {
+    } else if (rest64_is_prime_warp<kImplRest>(mine ? v : 0xFFFFFFFFFFFFFFC5ull, mine, tab, (int)B)) {
       *reinterpret_cast<uint8_t*>(a) = 1;
     }
     __syncthreads();

@@ -54,7 +54,7 @@ __device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
 // tab points at this thread's column of the shared table (stride `ld`).
 template <int kImpl>
 __device__ __forceinline__ uint64_t mont_pow_win4(const Mont64& M, uint64_t aR, uint64_t d,
-                                                  uint64_t* tab, int ld) {
+                                                  uint64_t* tab, int ld, int nib_warp = 0) {
   using Ops = MontOps<kImpl>;
   tab[0] = M.one;
   tab[ld] = aR;
@@ -65,7 +65,8 @@ __device__ __forceinline__ uint64_t mont_pow_win4(const Mont64& M, uint64_t aR, 
     t = Ops::mul(t, aR, M);
     tab[j * ld] = t;
   }
-  const int nib = (64 - clz64(d) + kWin - 1) / kWin;  // nibbles in d (d >= 1)
+  int nib = (64 - clz64(d) + kWin - 1) / kWin;  // nibbles in d (d >= 1)
+  if (nib_warp > nib) nib = nib_warp;  // leading zero nibbles select tab[0] = 1
   uint64_t x = tab[(int)((d >> (kWin * (nib - 1))) & (kTab - 1)) * ld];
   for (int k = nib - 2; k >= 0; --k) {
 #pragma unroll
@@ -90,6 +91,28 @@ __device__ __forceinline__ bool rest64_is_prime(uint64_t n, uint64_t* tab, int l
     if (!sprp_tail64<kImpl>(M, x, s)) return false;
   }
   return true;
+}
+
+// Warp-synchronous form of rest64_is_prime: all 32 lanes call it; the six
+// exponentiations run the warp's largest nibble count and every base runs
+// (the inputs are almost all primes, which need all six anyway), so the warp
+// never splits.  Lanes with valid == false pass any odd n >= 2^32.
+template <int kImpl>
+__device__ __forceinline__ bool rest64_is_prime_warp(uint64_t n, bool valid, uint64_t* tab, int ld) {
+  const Mont64 M = mont64_setup(n);
+  const uint64_t r2 = mont64_r2<kImpl>(M);
+  uint64_t d = n - 1;
+  const int s = ctz64(d);
+  d >>= s;
+  const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)((64 - clz64(d) + kWin - 1) / kWin));
+  bool prime = true;
+#pragma unroll 1
+  for (int b = 1; b < kNumBases64; ++b) {
+    const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b], r2, M);
+    const uint64_t x = mont_pow_win4<kImpl>(M, aR, d, tab, ld, nib);
+    prime = prime && sprp_tail64<kImpl>(M, x, s);
+  }
+  return valid && prime;
 }
 
 // Base 2 with 4-bit windows: T[w] = 2^w R mod n for w < 16 by doublings,

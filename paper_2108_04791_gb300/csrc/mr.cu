@@ -69,22 +69,17 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   uint64_t* tab = s_tab + threadIdx.x;
   const int ld = blockDim.x;
   const uint32_t count = *(volatile const uint32_t*)&counters[2];
-  if (kLucas) {  // whole warps per iteration: lucas_warp is warp-synchronous
-    const int lane = threadIdx.x & 31;
-    const uint32_t nthreads = gridDim.x * blockDim.x;
-    for (uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; wbase < count;
-         wbase += nthreads) {
-      const uint32_t i = wbase + lane;
-      const bool valid = i < count;
-      const uint32_t j = valid ? q64b[i] : 0u;
-      const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
-      if (lucas_warp<kImpl>(n, valid)) out[qidx[j]] = 1;
-    }
-    return;
-  }
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const uint32_t j = q64b[i];
-    if (rest64_is_prime<kImpl>(qn[j], tab, ld)) out[qidx[j]] = 1;
+  // whole warps per iteration: both tests are warp-synchronous
+  const int lane = threadIdx.x & 31;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  for (uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; wbase < count;
+       wbase += nthreads) {
+    const uint32_t i = wbase + lane;
+    const bool valid = i < count;
+    const uint32_t j = valid ? q64b[i] : 0u;
+    const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
+    const bool prime = kLucas ? lucas_warp<kImpl>(n, valid) : rest64_is_prime_warp<kImpl>(n, valid, tab, ld);
+    if (prime) out[qidx[j]] = 1;
   }
 }
 
