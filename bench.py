@@ -89,7 +89,7 @@ def _parse():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--workload", default="plain_large",
                    choices=["plain_large", "plain_small", "plain_mixed", "batched", "served",
-                            "range_1e8", "range_unix2021", "range_2p64"])
+                            "range_1e8", "range_unix2021", "range_2p64", "scalar_t4"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-probe", action="store_true", help="skip the integer-rate probe")
@@ -560,6 +560,102 @@ def run_range(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# isprime_fast's mean time per call for prime scalars of each bit size
+# (Table 4; MATLAB R2020b on an i7-9750H): context, not a target.
+TABLE4_ISPRIME_FAST_S = {4: 7.7654e-07, 8: 1.0120e-06, 16: 1.8106e-06, 24: 5.8244e-06,
+                         32: 5.3932e-05, 36: 0.0002828, 40: 0.001766, 44: 0.005818, 48: 0.02718,
+                         50: 0.0326, 52: 0.0431, 56: 0.0552, 60: 0.0755, 64: 0.1194}
+
+
+def run_scalar(args, world, rank, local):
+    """Latency of one-value calls (isprime_u64_scalar) on Table 4's inputs:
+    100 primes of each bit size, every call synchronous, timed on the host
+    around the C call; plus the device time of the one-warp kernel, and the
+    one-launch path against the queue path for short device arrays."""
+    import torch
+    import paper_2108_04791_gb300 as ipg
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ctx = ipg.Context.default(local)
+    L = ipg.lib()
+    res = ipg.ctypes.c_uint8()
+    pools = wg.load_primes_by_bits()
+    reps = max(1, min(args.steps, 20))
+    for b in pools:                                 # warm-up: every kernel and code path
+        for v in pools[b][:max(args.warmup, 3)].tolist():
+            L.isprime_u64_scalar(ctx.handle, v, ipg.ctypes.byref(res))
+    clocks = ClockSampler(local)
+    clocks.start()
+    per_bits, all_us, found = {}, [], 0
+    for b, vals in sorted(pools.items()):
+        lat = []
+        for _ in range(reps):
+            for v in vals.tolist():
+                t0 = time.perf_counter_ns()
+                st = L.isprime_u64_scalar(ctx.handle, v, ipg.ctypes.byref(res))
+                lat.append((time.perf_counter_ns() - t0) / 1e3)
+                if st:
+                    ipg._check(st)
+                found += res.value
+        lat.sort()
+        all_us += lat
+        per_bits[b] = {"p50_us": lat[len(lat) // 2], "p99_us": lat[int(len(lat) * 0.99)],
+                       "mean_us": sum(lat) / len(lat),
+                       "paper_isprime_fast_s": TABLE4_ISPRIME_FAST_S.get(b)}
+    clk = clocks.stop()
+    # device time of the warp kernel per bit size (CUDA events, separate pass)
+    ctx.timing_reset()
+    ctx.timing(True)
+    for b, vals in sorted(pools.items()):
+        ctx.timing_reset()
+        for v in vals.tolist():
+            L.isprime_u64_scalar(ctx.handle, v, ipg.ctypes.byref(res))
+        ms, cnt = ctx.timing_read()["small"]
+        per_bits[b]["kernel_us"] = 1e3 * ms / max(cnt, 1)
+    ctx.timing(False)
+    # short device arrays: one-launch warp path vs the queue path (device time per call)
+    stream = torch.cuda.current_stream(dev)
+    arrays = {}
+    old = ctx.tuning.small_max
+    for n in (1, 32, 256, 1024, 4096, 16384, 65536):
+        v = wg.plain_mixed(n, seed=5)
+        t = torch.from_numpy(v.view(np.int64)).to(dev)
+        out = torch.empty(n, dtype=torch.uint8, device=dev)
+        row = {}
+        for name, sm in (("warp", 1 << 20), ("queue", 0)):
+            ctx.set_tuning(small_max=sm)
+            for _ in range(5):
+                ctx.isprime(t, out=out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = 200
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(k):
+                ctx.isprime(t, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            row[name + "_us"] = 1e3 * e0.elapsed_time(e1) / k
+        arrays[n] = row
+    ctx.set_tuning(small_max=old)
+    all_us.sort()
+    mean_us = sum(all_us) / len(all_us)
+    if rank == 0:
+        line = {"metric": METRIC, "value": 1e6 / mean_us, "unit": "tests/s (one value per call)",
+                "n_gpus": world, "steps": reps, "warmup": args.warmup,
+                "ms_per_step": mean_us * len(all_us) / reps / 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "scalar_t4",
+                           "description": "100 primes of each bit size of Table 4, one "
+                                          "isprime_u64_scalar call per value, host-timed",
+                           "calls": len(all_us), "primes_found": found},
+                "latency": {"p50_us": all_us[len(all_us) // 2],
+                            "p99_us": all_us[int(len(all_us) * 0.99)], "mean_us": mean_us},
+                "per_bits": per_bits, "short_arrays_device_us": arrays, "clocks": clk,
+                "tuning": ctx.tuning.as_dict()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse()
     world, rank, local = _dist_init(args)
@@ -571,6 +667,8 @@ def main():
         run_served(args, world, rank, local)
     elif args.workload.startswith("range"):
         run_range(args, world, rank, local)
+    elif args.workload == "scalar_t4":
+        run_scalar(args, world, rank, local)
     else:
         run_mine(args, world, rank, local)
     if world > 1:

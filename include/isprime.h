@@ -74,7 +74,16 @@ typedef struct {
                               strong Lucas test with Selfridge's parameters (Baillie-PSW).
                               Both are exact below 2^64; 1 rests on the published search
                               finding no Baillie-PSW pseudoprime below 2^64. */
-  uint32_t reserved[1];
+  uint32_t small_max;      /* arrays of at most small_max elements take the one-launch latency
+                              path (one warp per element, no queues; 0..2^20, 0 = never) */
+  uint32_t compact_min;    /* survivor compaction after base 2: a warp with at least
+                              compact_min survivors finishes them in place (the rest_test
+                              stage run by the same warp) instead of appending them to the
+                              survivor queue; 0..33, 33 = always compact.  In-place finishing
+                              needs base2_window 4 (with 0 the survivors are always compacted) */
+  uint32_t sieve_cutover_log2; /* sieve / Miller-Rabin cutover of the array paths: the resident
+                              sieve answers n < min(S, 2^k); values from there up to 2^32 take
+                              trial division and the 32-bit Miller-Rabin test (0..32) */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */
@@ -178,6 +187,18 @@ int isprime_tuning_format(const isprime_tuning *t, char *buf, size_t cap);
 int isprime_u64_host(isprime_ctx *ctx, const uint64_t *h_in, uint8_t *h_out, size_t n,
                      isprime_stream stream);
 
+/* Latency path for one value (the paper's scalar calls, Sec. 1 and Table 4):
+ * *result = isprime(value).  The value travels in the kernel's parameters and
+ * the answer comes back through mapped pinned host memory, so a call is one
+ * kernel launch (one warp: trial division spread over the lanes, the seven
+ * bases of Eq. 4 on seven lanes at once) and one synchronisation of the
+ * context's own stream.  Synchronous; thread-safe. */
+int isprime_u64_scalar(isprime_ctx *ctx, uint64_t value, uint8_t *result);
+
+/* isprime_u64_host sends arrays of at most ISPRIME_HOST_INLINE_MAX values
+ * the same way (no copies); longer arrays take the staged, pipelined path. */
+#define ISPRIME_HOST_INLINE_MAX 256
+
 /* Allocation-free variant of isprime_u64 (the paper has no counterpart;
  * this exists for callers that cannot allocate device memory when they need
  * the test -- e.g. code running under an allocator that owns all device
@@ -257,7 +278,8 @@ enum {
   ISPRIME_K_SIEVE_COUNT = 7,
   ISPRIME_K_BATCHED = 8,
   ISPRIME_K_RANGE = 9,
-  ISPRIME_K_COUNT = 10
+  ISPRIME_K_SMALL = 10,
+  ISPRIME_K_COUNT = 11
 };
 
 typedef struct {

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["build", "lib", "isprime", "isprime_host", "Context", "Server", "Tuning",
+__all__ = ["build", "lib", "isprime", "isprime_host", "isprime_scalar", "Context", "Server", "Tuning",
            "IsPrimeError", "int_rates", "KERNEL_NAMES"]
 
 _lock = threading.Lock()
@@ -28,7 +28,7 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ETIMEDOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6
 SIEVE_DEFAULT = (1 << 64) - 1
 KERNEL_NAMES = ["sieve_base", "sieve_segment", "classify_u64", "classify_f64",
-                "mr64_base2", "mr64_rest", "mr32", "sieve_count", "batched", "range"]
+                "mr64_base2", "mr64_rest", "mr32", "sieve_count", "batched", "range", "small"]
 
 
 class IsPrimeError(RuntimeError):
@@ -44,10 +44,11 @@ class Tuning(ctypes.Structure):
                 ("mont_impl_base2", ctypes.c_uint32), ("batch_block", ctypes.c_uint32),
                 ("batch_tile_log2", ctypes.c_uint32), ("batch_blocks_per_sm", ctypes.c_uint32),
                 ("base2_window", ctypes.c_uint32), ("rest_test", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 1)]
+                ("small_max", ctypes.c_uint32), ("compact_min", ctypes.c_uint32),
+                ("sieve_cutover_log2", ctypes.c_uint32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class ArrayDesc(ctypes.Structure):
@@ -106,6 +107,7 @@ def lib():
                 "isprime_f64": ([vp, vp, sz, vp, vp], i32),
                 "isprime_f64_ctx": ([vp, vp, vp, sz, vp, vp], i32),
                 "isprime_u64_host": ([vp, vp, vp, sz, vp], i32),
+                "isprime_u64_scalar": ([vp, u64, ctypes.POINTER(ctypes.c_uint8)], i32),
                 "isprime_range": ([vp, u64, u64, vp, vp], i32),
                 "isprime_u64_batched": ([vp, ctypes.POINTER(ArrayDesc), sz, vp], i32),
                 "isprime_autotune": ([vp, vp, vp, sz, i32, ctypes.c_char_p, ctypes.POINTER(Tuning)], i32),
@@ -325,6 +327,14 @@ class Context:
             _check(lib().isprime_u64_host(self._h, a.ctypes.data, out.ctypes.data, a.size, sh))
         return out
 
+    def isprime_scalar(self, value: int) -> bool:
+        """isprime(value) for one Python int in [0, 2^64), one launch, synchronous."""
+        if not 0 <= int(value) < 1 << 64:
+            raise IsPrimeError(EINVAL, "value out of the uint64 range")
+        r = ctypes.c_uint8()
+        _check(lib().isprime_u64_scalar(self._h, int(value), ctypes.byref(r)))
+        return bool(r.value)
+
 
 class Server:
     """Continuous-batching server over a context (see isprime_server_create).
@@ -400,6 +410,10 @@ def isprime(t, out=None, stream=None, invalid=None):
 
 def isprime_host(values, device: int = 0) -> np.ndarray:
     return _default_ctx(device).isprime_host(values)
+
+
+def isprime_scalar(value: int, device: int = 0) -> bool:
+    return _default_ctx(device).isprime_scalar(value)
 
 
 def int_rates(device: int = 0) -> dict:

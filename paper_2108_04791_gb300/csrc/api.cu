@@ -85,6 +85,9 @@ static isprime_tuning default_tuning() {
   t.batch_blocks_per_sm = 0;
   t.base2_window = 4;
   t.rest_test = 0;
+  t.small_max = 16384;
+  t.compact_min = 33;
+  t.sieve_cutover_log2 = 32;
   return t;
 }
 
@@ -102,6 +105,9 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.batch_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "batch_blocks_per_sm must be in [0, 32]");
   if (t.base2_window != 0 && t.base2_window != 4) return set_error(ISPRIME_EINVAL, "base2_window must be 0 or 4");
   if (t.rest_test > 1) return set_error(ISPRIME_EINVAL, "rest_test must be 0 or 1");
+  if (t.small_max > (1u << 20)) return set_error(ISPRIME_EINVAL, "small_max must be in [0, 2^20]");
+  if (t.compact_min > 33) return set_error(ISPRIME_EINVAL, "compact_min must be in [0, 33]");
+  if (t.sieve_cutover_log2 > 32) return set_error(ISPRIME_EINVAL, "sieve_cutover_log2 must be in [0, 32]");
   return ISPRIME_OK;
 }
 
@@ -221,8 +227,17 @@ static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t 
   if (st0) return st0;
   std::lock_guard<std::mutex> lock(ctx->mu);
   DeviceGuard g(ctx->device);
+  int st;
+  if (n <= ctx->tune.small_max) {  // one launch, no queues: no ordering needed
+    st = kF64 ? launch_small_f64(ctx, static_cast<const double*>(d_in), d_out, n, d_invalid, s)
+              : launch_small_u64(ctx, static_cast<const uint64_t*>(d_in), d_out, n, s);
+    if (st) return st;
+    ctx->stats.calls++;
+    ctx->stats.elements += n;
+    return ISPRIME_OK;
+  }
   const size_t chunk = (size_t)1 << ctx->tune.chunk_log2;
-  int st = ensure_queues(ctx, std::min(chunk, std::max(n, (size_t)1 << 16)));
+  st = ensure_queues(ctx, std::min(chunk, std::max(n, (size_t)1 << 16)));
   if (st) return st;
   if ((st = order_before(ctx, s))) return st;
   const size_t step = std::min(chunk, ctx->q.capacity);
@@ -234,7 +249,7 @@ static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t 
     a.out = d_out + off;
     a.n = len;
     a.sieve = ctx->d_sieve;
-    a.sieve_limit = ctx->sieve_limit;
+    a.sieve_limit = sieve_cut(ctx);
     a.ntd = ctx->tune.td_primes;
     a.td_square = td_square_for(ctx->tune.td_primes);
     a.q64_n = ctx->q.q64_n;
@@ -248,7 +263,7 @@ static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t 
     a.pair_store = (((uintptr_t)(a.out + a.head)) % 2 == 0) ? 1u : 0u;
     st = kF64 ? launch_classify_f64(ctx, a, s) : launch_classify_u64(ctx, a, s);
     if (st) return st;
-    if ((st = launch_mr(ctx, a.out, s))) return st;
+    if ((st = launch_mr(ctx, a.out, len, s))) return st;
   }
   if ((st = order_after(ctx, s))) return st;
   ctx->stats.calls++;
@@ -310,6 +325,8 @@ int isprime_ctx_destroy(isprime_ctx* ctx) {
     if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
     if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
+    if (ctx->scalar_s) cudaStreamSynchronize(ctx->scalar_s), cudaStreamDestroy(ctx->scalar_s);
+    if (ctx->h_inline_out) cudaFreeHost(ctx->h_inline_out);
   }
   for (int d = 0; d < 64; ++d) {
     std::lock_guard<std::mutex> lock(g_default_mu);
@@ -426,6 +443,16 @@ int isprime_u64_batched(isprime_ctx* ctx, const isprime_array* arrays, size_t n_
   return ISPRIME_OK;
 }
 
+int isprime_u64_scalar(isprime_ctx* ctx, uint64_t value, uint8_t* result) {
+  if (!ctx || !result) return set_error(ISPRIME_EINVAL, "NULL argument");
+  DeviceGuard g(ctx->device);
+  {
+    std::lock_guard<std::mutex> lock(ctx->inline_mu);
+    if (!ctx->scalar_s) IP_CUDA(cudaStreamCreateWithFlags(&ctx->scalar_s, cudaStreamNonBlocking));
+  }
+  return inline_run(ctx, &value, result, 1, ctx->scalar_s);
+}
+
 int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n,
                      isprime_stream stream) {
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
@@ -433,8 +460,9 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
   int st = check_array_args(h_in, h_out, n, 8);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> host_lock(ctx->host_mu);
   DeviceGuard g(ctx->device);
+  if (n <= (size_t)kInlineMax) return inline_run(ctx, h_in, h_out, n, s);
+  std::lock_guard<std::mutex> host_lock(ctx->host_mu);
   // Pipeline: chunk k is copied in on copy_in, classified on `stream`, and
   // copied out on copy_out, through staging slot k % 2, so the copy-in of
   // chunk k+1 and the copy-out of chunk k-1 overlap the kernels of chunk k.

@@ -3,8 +3,10 @@
 // The paper chooses between its two array paths with linear fits measured on
 // one machine (Sec. 6.2, Eqs. 7-8).  The GPU analogue here chooses the
 // parameters that only affect speed (block sizes, grid occupancy, trial
-// division count, Montgomery formulation, batched tile size) by timing the
-// caller's own sample on this GPU.  Search: coordinate descent (each
+// division count, Montgomery formulation, survivor-compaction threshold,
+// sieve / Miller-Rabin cutover, batched tile size, and the array length up
+// to which the one-launch path beats the queue path) by timing the caller's
+// own sample on this GPU.  Search: coordinate descent (each
 // parameter swept over its candidate values with the others held, two
 // passes), every candidate timed as the best of three runs with CUDA events.
 // Results are cached in a text file keyed by GPU name, SM count, CUDA
@@ -39,6 +41,8 @@ std::vector<Param> params() {
       {"mont_impl", &isprime_tuning::mont_impl, {0, 5}, P},
       {"mont_impl_base2", &isprime_tuning::mont_impl_base2, {0, 5}, P},
       {"base2_window", &isprime_tuning::base2_window, {0, 4}, P},
+      {"compact_min", &isprime_tuning::compact_min, {33, 28, 24, 16}, P},
+      {"sieve_cutover_log2", &isprime_tuning::sieve_cutover_log2, {32, 28, 24, 20}, P | B},
       {"batch_block", &isprime_tuning::batch_block, {64, 128, 256}, B},
       {"batch_tile_log2", &isprime_tuning::batch_tile_log2, {8, 9, 10, 11, 12}, B},
   };
@@ -60,14 +64,16 @@ std::string cache_key(int device, size_t n, int mode) {
 
 const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_primes", "chunk_log2",
                          "mont_impl", "mont_impl_base2", "batch_block", "batch_tile_log2",
-                         "batch_blocks_per_sm", "base2_window", "rest_test"};
+                         "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
+                         "compact_min", "sieve_cutover_log2"};
 uint32_t isprime_tuning::*kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
     &isprime_tuning::mont_impl_base2, &isprime_tuning::batch_block,
     &isprime_tuning::batch_tile_log2, &isprime_tuning::batch_blocks_per_sm,
-    &isprime_tuning::base2_window, &isprime_tuning::rest_test};
-constexpr int kNumFields = 12;
+    &isprime_tuning::base2_window, &isprime_tuning::rest_test, &isprime_tuning::small_max,
+    &isprime_tuning::compact_min, &isprime_tuning::sieve_cutover_log2};
+constexpr int kNumFields = 15;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;
@@ -196,6 +202,27 @@ int autotune(isprime_ctx* ctx, const uint64_t* d_sample, uint8_t* d_out, size_t 
       }
       if (st) break;
     }
+  }
+  // Array-level path choice (what Sec. 6.2's Eqs. 7-8 decide between the
+  // paper's two array paths, here measured rather than fitted): the one-
+  // launch warp-per-element path against the queue path on prefixes of the
+  // sample of 64 ... 2^20 elements; small_max becomes the largest length at
+  // which the warp path is still faster.
+  if (!st && !batched) {
+    uint32_t best_small = 0;
+    for (size_t m = 64; m <= std::min(n, (size_t)1 << 20) && !st; m *= 2) {
+      float ms_warp = 0, ms_queue = 0;
+      isprime_tuning cand = t;
+      cand.small_max = 1u << 20;
+      if ((st = isprime_ctx_set_tuning(ctx, &cand))) break;
+      if ((st = time_config(ctx, d_sample, d_out, m, batch, false, s, e0, e1, 10, &ms_warp))) break;
+      cand.small_max = 0;
+      if ((st = isprime_ctx_set_tuning(ctx, &cand))) break;
+      if ((st = time_config(ctx, d_sample, d_out, m, batch, false, s, e0, e1, 10, &ms_queue))) break;
+      if (ms_warp >= ms_queue) break;
+      best_small = (uint32_t)m;
+    }
+    t.small_max = best_small;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

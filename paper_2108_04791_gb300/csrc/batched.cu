@@ -274,9 +274,12 @@ int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, s
   // The graph: reset the tile counter, launch the persistent kernel.
   const BatchVariant v = pick_variant(ctx->tune.td_primes, ctx->tune.rest_test);
   const size_t smem = batched_smem_bytes(block, tile);
-  const uint64_t key = ((uint64_t)block << 40) ^ ((uint64_t)tile << 8) ^ ctx->tune.td_primes ^
-                       ((uint64_t)ctx->tune.batch_blocks_per_sm << 56) ^
-                       ((uint64_t)ctx->tune.rest_test << 62);
+  // every parameter the recorded graph depends on, in disjoint bit fields
+  const uint64_t key = (uint64_t)block | ((uint64_t)tile << 10) |
+                       ((uint64_t)ctx->tune.td_primes << 26) |
+                       ((uint64_t)ctx->tune.batch_blocks_per_sm << 32) |
+                       ((uint64_t)ctx->tune.rest_test << 40) |
+                       ((uint64_t)ctx->tune.sieve_cutover_log2 << 42);
   if (!bs->exec || bs->key != key) {
     if (bs->exec) {
       IP_CUDA(cudaStreamSynchronize(s));
@@ -293,7 +296,7 @@ int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, s
     p.hdr = reinterpret_cast<const BatchHeader*>(bs->d_batch);
     p.tile_counter = bs->d_tile_counter;
     p.sieve = ctx->d_sieve;
-    p.sieve_limit = ctx->sieve_limit;
+    p.sieve_limit = sieve_cut(ctx);
     p.ntd = ctx->tune.td_primes;
     p.td_square = td_square_for(ctx->tune.td_primes);
     p.tile = tile;

@@ -18,6 +18,14 @@ static __constant__ BaseTable c_bases = make_base_table();
 
 enum : int { kComposite = 0, kPrime = 1, kMR64 = 2, kMR32 = 3 };
 
+// Double input: finite, >= 0, integral and <= 2^53 (Sec. 8.1) converts
+// exactly; anything else is invalid (output 0, counted).
+__device__ __forceinline__ bool f64_to_u64(double x, uint64_t* v) {
+  const bool ok = (x >= 0.0) && (x <= 9007199254740992.0) && (floor(x) == x);
+  *v = ok ? (uint64_t)x : 0ull;
+  return ok;
+}
+
 constexpr int kWin = 4;
 constexpr int kTab = 1 << kWin;
 

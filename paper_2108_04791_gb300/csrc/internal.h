@@ -102,9 +102,21 @@ struct isprime_ctx {
   cudaEvent_t stage_ev[6] = {};      // per staging slot: copied in, computed, copied out
   cudaEvent_t host_last = nullptr;   // end of the previous host-path call
   ip::BatchState batch;              // batched path of the context's own calls
+  // latency path (small.cu): results of inline calls land in mapped host memory
+  std::mutex inline_mu;
+  uint8_t* h_inline_out = nullptr;   // pinned, mapped, ISPRIME_HOST_INLINE_MAX bytes
+  uint8_t* d_inline_out = nullptr;   // its device address
+  cudaStream_t scalar_s = nullptr;   // stream of isprime_u64_scalar
 };
 
 namespace ip {
+
+// The limit below which the array paths answer from the sieve: min(S, 2^k)
+// for the tuned cutover k.
+inline uint64_t sieve_cut(const isprime_ctx* c) {
+  const uint64_t k = c->tune.sieve_cutover_log2 >= 32 ? (1ull << 32) : (1ull << c->tune.sieve_cutover_log2);
+  return c->sieve_limit < k ? c->sieve_limit : k;
+}
 
 // Launch bracket: timing events + launch counting + error check.
 int launch_begin(isprime_ctx* ctx, int kid, cudaStream_t s, TimedLaunch* tl);
@@ -141,7 +153,8 @@ int launch_classify_u64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s)
 int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s);
 
 // mr.cu
-int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s);
+// len: elements of the chunk just classified (bounds the queue lengths).
+int launch_mr(isprime_ctx* ctx, uint8_t* out, uint64_t len, cudaStream_t s);
 
 // Context-free launchers (explicit launch shape), used by noalloc.cu.
 int launch_classify_u64_raw(const ClassifyArgs& a, unsigned grid, unsigned block, cudaStream_t s);
@@ -152,6 +165,16 @@ int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, 
 int measure_int_rates(int device, isprime_int_rates* out);
 
 uint64_t td_square_for(uint32_t ntd);
+
+// small.cu: one warp per element, one launch, no queues.
+constexpr int kInlineMax = ISPRIME_HOST_INLINE_MAX;
+int launch_small_u64(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
+                     cudaStream_t s);
+int launch_small_f64(isprime_ctx* ctx, const double* d_in, uint8_t* d_out, size_t n,
+                     unsigned long long* d_invalid, cudaStream_t s);
+// Host values in (n <= kInlineMax), host bytes out; takes ctx->inline_mu and
+// ctx->mu itself and synchronises s.
+int inline_run(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n, cudaStream_t s);
 
 // batched.cu
 size_t batched_smem_bytes(uint32_t block, uint32_t tile);

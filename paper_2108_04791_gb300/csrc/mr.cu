@@ -13,6 +13,9 @@
 //                      compacted with warp ballots into a second queue, so
 //                      the next kernel runs on dense warps of likely primes
 //                      instead of idling behind early-exiting composites.
+//                      With the compaction threshold compact_min <= 32, a warp
+//                      left with at least that many survivors finishes them
+//                      itself (few idle lanes, no queue round trip).
 //   mr64_rest_kernel   the six remaining bases, 4-bit fixed-window
 //                      exponentiation with the per-thread window table in
 //                      shared memory; writes 1 for primes.
@@ -25,10 +28,16 @@
 
 namespace ip {
 
-template <int kImpl, bool kWindow>
+// kRest (needs kWindow): 0 compact every survivor into q64b; 1 or 2 a warp
+// with at least compact_min survivors finishes them itself, with the six
+// remaining bases (1) or the strong Lucas test (2), and compacts nothing.
+template <int kImpl, bool kWindow, int kRest>
 __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restrict__ qn,
+                                                         const uint32_t* __restrict__ qidx,
                                                          uint32_t* __restrict__ counters,
-                                                         uint32_t* __restrict__ q64b) {
+                                                         uint32_t* __restrict__ q64b,
+                                                         uint8_t* __restrict__ out,
+                                                         uint32_t compact_min) {
   extern __shared__ uint64_t s_tab[];  // kWindow: 16 x blockDim
   const uint32_t count = *(volatile uint32_t*)&counters[0];
   const int lane = threadIdx.x & 31;
@@ -37,8 +46,9 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   for (uint32_t wbase = gtid & ~31u; wbase < count; wbase += nthreads) {
     const uint32_t i = wbase + lane;
     bool pass = false;
+    uint64_t n = 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 (prime) for lanes past the end
     if (i < count) {
-      const uint64_t n = qn[i];
+      n = qn[i];
       if (kWindow) {
         const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
         pass = base2_passes_win<kImpl>(n, s_tab + threadIdx.x, (int)blockDim.x, nib);
@@ -47,7 +57,14 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
       }
     }
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, pass);
-    if (mask) {
+    if (kRest != 0 && mask && (uint32_t)__popc(mask) >= compact_min) {
+      // dense warp: finishing here costs fewer idle lanes than a queue round trip
+      const uint64_t m = pass ? n : 0xFFFFFFFFFFFFFFC5ull;
+      const bool prime = kRest == 2 ? lucas_warp<kImpl>(m, pass)
+                                    : rest64_is_prime_warp<kImpl>(m, pass, s_tab + threadIdx.x,
+                                                                  (int)blockDim.x);
+      if (prime) out[qidx[i]] = 1;
+    } else if (mask) {
       const int leader = __ffs(mask) - 1;
       uint32_t base = 0;
       if (lane == leader) base = atomicAdd(&counters[2], (uint32_t)__popc(mask));
@@ -103,16 +120,29 @@ static unsigned resident_grid(const void* fn, unsigned block, size_t smem, int s
   return want < cap ? want : cap;
 }
 
+template <int kImpl, int kRest>
+static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+                             uint32_t compact_min, int sm_count, cudaStream_t s) {
+  const size_t smem = (size_t)16 * block * sizeof(uint64_t);
+  const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, true, kRest>);
+  grid = resident_grid(fn, block, smem, sm_count, grid);
+  mr64_base2_kernel<kImpl, true, kRest><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.counters,
+                                                                  q.q64b, out, compact_min);
+}
+
 template <int kImpl>
-static void launch_base2(const Queues& q, unsigned grid, unsigned block, int window, int sm_count,
-                         cudaStream_t s) {
+static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int window,
+                         int lucas, uint32_t compact_min, int sm_count, cudaStream_t s) {
   if (window) {
-    const size_t smem = (size_t)16 * block * sizeof(uint64_t);
-    const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, true>);
-    grid = resident_grid(fn, block, smem, sm_count, grid);
-    mr64_base2_kernel<kImpl, true><<<grid, block, smem, s>>>(q.q64_n, q.counters, q.q64b);
+    if (compact_min > 32)
+      launch_base2_win<kImpl, 0>(q, out, grid, block, compact_min, sm_count, s);
+    else if (lucas)
+      launch_base2_win<kImpl, 2>(q, out, grid, block, compact_min, sm_count, s);
+    else
+      launch_base2_win<kImpl, 1>(q, out, grid, block, compact_min, sm_count, s);
   } else {
-    mr64_base2_kernel<kImpl, false><<<grid, block, 0, s>>>(q.q64_n, q.counters, q.q64b);
+    mr64_base2_kernel<kImpl, false, 0><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.counters,
+                                                              q.q64b, out, 33u);
   }
 }
 
@@ -130,18 +160,19 @@ static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned b
 // impl_b2 selects the arithmetic of the base-2 kernel, impl that of the
 // six-base kernel (see MontOps).
 static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int impl,
-                       int impl_b2, int window, int lucas, int sm_count, cudaStream_t s,
-                       isprime_ctx* ctx) {
+                       int impl_b2, int window, int lucas, uint32_t compact_min, int sm_count,
+                       cudaStream_t s, isprime_ctx* ctx) {
   int st = ISPRIME_OK;
   TimedLaunch tl;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
+  const uint32_t cm = compact_min;
   switch (impl_b2) {
-    case 1: launch_base2<1>(q, grid, block, window, sm_count, s); break;
-    case 2: launch_base2<2>(q, grid, block, window, sm_count, s); break;
-    case 3: launch_base2<3>(q, grid, block, window, sm_count, s); break;
-    case 4: launch_base2<4>(q, grid, block, window, sm_count, s); break;
-    case 5: launch_base2<5>(q, grid, block, window, sm_count, s); break;
-    default: launch_base2<0>(q, grid, block, window, sm_count, s); break;
+    case 1: launch_base2<1>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
+    case 2: launch_base2<2>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
+    case 3: launch_base2<3>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
+    case 4: launch_base2<4>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
+    case 5: launch_base2<5>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
+    default: launch_base2<0>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
   }
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
@@ -157,19 +188,23 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
   return st;
 }
 
-int launch_mr(isprime_ctx* ctx, uint8_t* out, cudaStream_t s) {
+int launch_mr(isprime_ctx* ctx, uint8_t* out, uint64_t len, cudaStream_t s) {
   const uint32_t block = ctx->tune.mr_block;
-  const unsigned grid = (unsigned)ctx->sm_count * ctx->tune.blocks_per_sm;
+  // The queues hold at most `len` elements (one per thread and pass), so a
+  // short chunk gets a short grid.
+  const uint64_t cap = (uint64_t)ctx->sm_count * ctx->tune.blocks_per_sm;
+  const uint64_t want = (len + block - 1) / block;
+  const unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
   TimedLaunch tl;
   int st;
-  if (ctx->sieve_limit < (1ull << 32)) {
+  if (sieve_cut(ctx) < (1ull << 32)) {
     if ((st = launch_begin(ctx, ISPRIME_K_MR32, s, &tl))) return st;
     mr32_kernel<<<grid, block, 0, s>>>(ctx->q.q32_n, ctx->q.q32_idx, ctx->q.counters, out);
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
   return launch_mr64(ctx->q, out, grid, block, (int)ctx->tune.mont_impl,
                      (int)ctx->tune.mont_impl_base2, (int)ctx->tune.base2_window,
-                     (int)ctx->tune.rest_test, ctx->sm_count, s, ctx);
+                     (int)ctx->tune.rest_test, ctx->tune.compact_min, ctx->sm_count, s, ctx);
 }
 
 // Launch without a context (explicit grid and block and queue pointers);
@@ -178,7 +213,8 @@ int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, 
                   cudaStream_t s) {
   if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
   // binary base-2 schedule (no shared memory), as this launcher always used
-  launch_mr64(q, out, grid, block, 0, 5, /*window=*/0, /*lucas=*/0, /*sm_count=*/0, s, nullptr);
+  launch_mr64(q, out, grid, block, 0, 5, /*window=*/0, /*lucas=*/0, /*compact_min=*/33,
+              /*sm_count=*/0, s, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
 }

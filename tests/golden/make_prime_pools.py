@@ -6,6 +6,8 @@ touches the CUDA library.
 
   primes_near_2p64.txt  4096 distinct primes in [2^64 - 2^40, 2^64)
   primes_near_2p32.txt  4096 distinct primes in [2^32 - 2^24, 2^32)
+  primes_by_bits.txt    100 random primes of each bit size of Table 4 (4 ... 64
+                        bits, i.e. in [2^(b-1), 2^b)), drawn with replacement
 
 Run from the repository root:  python tests/golden/make_prime_pools.py
 """
@@ -38,6 +40,21 @@ def pool(lo, hi, count, seed):
     return got
 
 
+T4_BITS = (4, 8, 16, 24, 32, 36, 40, 44, 48, 50, 52, 56, 60, 64)
+
+
+def primes_of_bits(b, count, seed):
+    """`count` primes in [2^(b-1), 2^b), uniform candidates, repeats allowed."""
+    got = []
+    offset = 0
+    while len(got) < count:
+        cand = uniform_range(seed, 1 << 12, 1 << (b - 1), 1 << b, offset=offset)
+        offset += 1 << 12
+        flags = oracle.isprime_u64(cand)
+        got.extend(v for v, f in zip(cand.tolist(), flags.tolist()) if f)
+    return got[:count]
+
+
 def write(name, vals, header):
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
     with open(path, "w") as f:
@@ -51,3 +68,10 @@ if __name__ == "__main__":
           "4096 distinct primes in [2^64 - 2^40, 2^64), hex")
     write("primes_near_2p32.txt", pool((1 << 32) - (1 << 24), 1 << 32, 4096, 32),
           "4096 distinct primes in [2^32 - 2^24, 2^32), hex")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "primes_by_bits.txt")
+    with open(path, "w") as f:
+        f.write("# 100 random primes of each bit size b of Table 4, in [2^(b-1), 2^b): "
+                "bits hex\n# written by tests/golden/make_prime_pools.py (CPU oracle)\n")
+        for b in T4_BITS:
+            for v in primes_of_bits(b, 100, 1000 + b):
+                f.write(f"{b} {v:016x}\n")

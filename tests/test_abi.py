@@ -76,6 +76,8 @@ def test_argument_checks_without_gpu(L):
     assert b"overlap" in L.isprime_last_error()
     # NULL context
     assert L.isprime_u64_ctx(None, p_in, p_out, 4, None) == ipg.EINVAL
+    assert L.isprime_u64_scalar(None, 5, ctypes.byref(ctypes.c_uint8())) == ipg.EINVAL
+    assert L.isprime_u64_host(None, p_in, p_out, 4, None) == ipg.EINVAL
     assert L.isprime_ctx_destroy(None) == 0
 
 

@@ -103,18 +103,23 @@ def test_mixed_doubles():
     assert int(inv.item()) == bad == 0
 
 
-def test_f64_domain_and_invalid_count():
+def test_f64_domain_and_invalid_count(ctx_small_sieve):
     x = np.array([0.0, -0.0, 1.0, 2.0, 7.0, 9.0, 2.0**53, 2.0**53 - 111, float("nan"),
                   float("inf"), -float("inf"), -7.0, 2.5, 2.0**53 + 2, 1e300, 97.0, 3.0],
                  dtype=np.float64)
-    for k in (1, 2, 3, len(x)):  # ragged lengths through head/tail paths
-        t = torch.from_numpy(x[:k].copy()).to(_dev())
-        inv = torch.zeros(1, dtype=torch.int64, device=_dev())
-        out = ipg.isprime(t, invalid=inv)
-        torch.cuda.synchronize()
-        want, bad = oracle.isprime_f64(x[:k])
-        assert out.cpu().numpy().tolist() == want.tolist()
-        assert int(inv.item()) == bad
+    old = ctx_small_sieve.tuning.small_max
+    ctx_small_sieve.set_tuning(small_max=0)  # the queue path (classify_kernel<f64>)
+    try:
+        for k in (1, 2, 3, len(x)):  # ragged lengths through head/tail paths
+            t = torch.from_numpy(x[:k].copy()).to(_dev())
+            inv = torch.zeros(1, dtype=torch.int64, device=_dev())
+            out = ctx_small_sieve.isprime(t, invalid=inv)
+            torch.cuda.synchronize()
+            want, bad = oracle.isprime_f64(x[:k])
+            assert out.cpu().numpy().tolist() == want.tolist()
+            assert int(inv.item()) == bad
+    finally:
+        ctx_small_sieve.set_tuning(small_max=old)
 
 
 # ------------------------------------------------------------------ edge cases
@@ -131,7 +136,15 @@ SPECIAL = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 25, 49, 121, 169, 251, 253, 257, 65521,
 def test_special_values(which, ctx_nosieve, ctx_small_sieve):
     ctx = {"default": None, "nosieve": ctx_nosieve, "smallsieve": ctx_small_sieve}[which]
     v = np.array(SPECIAL, dtype=np.uint64)
-    _assert_same(v, _gpu(v, ctx), oracle.isprime_u64(v))
+    want = oracle.isprime_u64(v)
+    _assert_same(v, _gpu(v, ctx), want)  # short array: the one-warp-per-element path
+    if ctx is not None:                  # and the queue path of the same context
+        old = ctx.tuning.small_max
+        ctx.set_tuning(small_max=0)
+        try:
+            _assert_same(v, _gpu(v, ctx), want)
+        finally:
+            ctx.set_tuning(small_max=old)
 
 
 def test_empty_input():
@@ -139,17 +152,26 @@ def test_empty_input():
     assert ipg.isprime(t).numel() == 0
 
 
-def test_ragged_lengths_and_offsets():
+@pytest.mark.parametrize("small_max", [0, None])
+def test_ragged_lengths_and_offsets(small_max, ctx_small_sieve):
+    """Short arrays on the queue path (small_max = 0: head element, pair
+    stores, odd tails) and on the one-launch warp path (the default)."""
     base = plain_mixed(4096, seed=9)
     big = _to_dev(base)
     want_all = oracle.isprime_u64(base)
-    for off in (0, 1, 2, 3):
-        for n in list(range(1, 70)) + [127, 128, 129, 1023, 1025]:
-            t = big[off:off + n]          # misaligned by 8 bytes for odd off
-            out = torch.zeros(n + 3, dtype=torch.uint8, device=_dev())[1:n + 1]  # odd output address
-            ipg.isprime(t, out=out)
-            torch.cuda.synchronize()
-            assert out.cpu().numpy().tolist() == want_all[off:off + n].tolist(), (off, n)
+    old = ctx_small_sieve.tuning.small_max
+    if small_max is not None:
+        ctx_small_sieve.set_tuning(small_max=small_max)
+    try:
+        for off in (0, 1, 2, 3):
+            for n in list(range(1, 70)) + [127, 128, 129, 1023, 1025, 4093]:
+                t = big[off:off + n]          # misaligned by 8 bytes for odd off
+                out = torch.zeros(n + 3, dtype=torch.uint8, device=_dev())[1:n + 1]  # odd output address
+                ctx_small_sieve.isprime(t, out=out)
+                torch.cuda.synchronize()
+                assert out.cpu().numpy().tolist() == want_all[off:off + n].tolist(), (off, n)
+    finally:
+        ctx_small_sieve.set_tuning(small_max=old)
 
 
 def test_no_sieve_and_small_sieve_contexts(ctx_nosieve, ctx_small_sieve):
@@ -197,7 +219,12 @@ def test_tuning_does_not_change_results():
                    dict(td_primes=7), dict(td_primes=11), dict(td_primes=23), dict(td_primes=31),
                    dict(td_primes=40), dict(base2_window=0), dict(base2_window=4, mont_impl_base2=0),
                    dict(rest_test=1), dict(rest_test=1, mont_impl=5), dict(rest_test=0),
-                   dict(mont_impl=0, td_primes=15)]:
+                   dict(mont_impl=0, td_primes=15),
+                   dict(compact_min=0), dict(compact_min=1), dict(compact_min=16),
+                   dict(compact_min=4, rest_test=1), dict(compact_min=8, mont_impl_base2=5),
+                   dict(compact_min=2, base2_window=0), dict(compact_min=33),
+                   dict(sieve_cutover_log2=0), dict(sieve_cutover_log2=20),
+                   dict(sieve_cutover_log2=23, td_primes=0), dict(sieve_cutover_log2=32)]:
             c.set_tuning(**kw)
             _assert_same(v, _gpu(v, c), want)
 
@@ -301,7 +328,8 @@ def test_batched_rejects_tuning_beyond_shared_memory():
                                 dict(batch_block=256, batch_tile_log2=13),
                                 dict(batch_block=64, batch_tile_log2=13),
                                 dict(td_primes=23), dict(td_primes=5),
-                                dict(batch_blocks_per_sm=1)])
+                                dict(batch_blocks_per_sm=1), dict(sieve_cutover_log2=16),
+                                dict(sieve_cutover_log2=0, td_primes=0)])
 def test_batched_tuning_and_small_sieve(kw):
     from workloads import batched_arrays
     vals, offs = batched_arrays(n_arrays=64, max_size=1 << 15, seed=62)

@@ -48,3 +48,20 @@ def test_distribution_shapes():
     arr, sizes, _ = g.served_requests(n_requests=2000, values=False)
     gaps = np.diff(arr)
     assert abs(gaps.mean() - 1 / 5000) < 0.1 / 5000
+
+
+def test_stored_primes_by_bits_have_their_bit_size_and_are_prime():
+    """Table 4's scalar inputs: 100 primes per bit size, each in [2^(b-1), 2^b);
+    primality re-checked by trial division (<= 32 bits) or a Pratt certificate."""
+    import numtheory as nt
+    pools = g.load_primes_by_bits()
+    assert sorted(pools) == [4, 8, 16, 24, 32, 36, 40, 44, 48, 50, 52, 56, 60, 64]
+    for b, vals in pools.items():
+        assert vals.size == 100
+        for v in vals.tolist():
+            assert v.bit_length() == b
+        for v in sorted(set(vals.tolist()))[:5]:
+            if b <= 32:
+                assert nt.trial_is_prime(v)
+            else:
+                assert nt.pratt_prime(v) is True

@@ -107,6 +107,19 @@ def load_pool(name: str) -> np.ndarray:
     return np.array(vals, dtype=np.uint64)
 
 
+def load_primes_by_bits() -> dict:
+    """bits -> uint64 array of the stored primes of that bit size (Table 4's
+    scalar inputs; written by tests/golden/make_prime_pools.py)."""
+    out: dict = {}
+    with open(os.path.join(_POOL_DIR, "primes_by_bits.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                b, v = line.split()
+                out.setdefault(int(b), []).append(int(v, 16))
+    return {b: np.array(v, dtype=np.uint64) for b, v in out.items()}
+
+
 # --- the five workloads --------------------------------------------------
 
 def plain_small(n: int = 100_000, seed: int = 0) -> np.ndarray:
