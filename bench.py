@@ -97,6 +97,11 @@ def _parse():
     return p.parse_args()
 
 
+def _apply_tune(ctx, args):
+    if args.tune:
+        ctx.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
+
+
 def _workload(name: str, rank: int) -> tuple[np.ndarray, str]:
     if name == "plain_large":
         n = 1 << 24
@@ -267,8 +272,7 @@ def run_mine(args, world, rank, local):
     d_in = torch.from_numpy(vals.view(np.int64)).to(dev)
     out = torch.empty(n, dtype=torch.uint8, device=dev)
     ctx = ipg.Context.default(local)              # builds the resident sieve (untimed)
-    if args.tune:
-        ctx.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
+    _apply_tune(ctx, args)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
 
@@ -466,6 +470,7 @@ def run_served(args, world, rank, local):
     in_off = starts % (pool_n - (1 << 22))
     out_off = starts % (ring_n - (1 << 22))
     ctx = ipg.Context.default(local)
+    _apply_tune(ctx, args)
     srv = ipg.Server(ctx, mem_budget_bytes=8 << 30, n_slots=4)
     # warm-up requests (graph recording, first-touch of the arena)
     for i in range(max(args.warmup, 3)):
@@ -504,6 +509,10 @@ def run_served(args, world, rank, local):
                        "description": wg.WORKLOADS["served"]},
             "serve": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                       "max_ms": st["max_ms"], "batches": st["batches"], "span_s": st["span_s"],
+                      "short_requests": st["short_requests"],
+                      "short_max_elements": ctx.tuning.small_max,
+                      "p50_short_ms": st["p50_short_ms"], "p99_short_ms": st["p99_short_ms"],
+                      "p50_long_ms": st["p50_long_ms"], "p99_long_ms": st["p99_long_ms"],
                       "offered_tests_per_s": float(sizes.sum() / arrivals[-1]), "wall_s": wall},
             "clocks": clk,
         }

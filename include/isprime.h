@@ -241,6 +241,11 @@ typedef struct {
   double max_ms;
   double span_s;       /* first submit to last completion */
   double tests_per_s;  /* elements / span_s */
+  uint64_t short_requests; /* requests of at most small_max elements (batched apart) */
+  double p50_short_ms; /* latency percentiles of the short requests */
+  double p99_short_ms;
+  double p50_long_ms;  /* and of the others */
+  double p99_long_ms;
 } isprime_server_stats;
 
 /* Allocates a device arena of mem_budget_bytes and starts the server's two

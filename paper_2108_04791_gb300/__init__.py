@@ -60,7 +60,9 @@ class _ServerStats(ctypes.Structure):
                 ("batches", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("span_s", ctypes.c_double),
-                ("tests_per_s", ctypes.c_double)]
+                ("tests_per_s", ctypes.c_double), ("short_requests", ctypes.c_uint64),
+                ("p50_short_ms", ctypes.c_double), ("p99_short_ms", ctypes.c_double),
+                ("p50_long_ms", ctypes.c_double), ("p99_long_ms", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):

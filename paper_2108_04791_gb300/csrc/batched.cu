@@ -224,19 +224,23 @@ void batch_state_free(BatchState* b) {
 int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, size_t n_arrays,
                 cudaStream_t s) {
   const uint32_t block = ctx->tune.batch_block;
-  const uint32_t tile = 1u << ctx->tune.batch_tile_log2;
+  uint64_t elems = 0;
+  for (size_t i = 0; i < n_arrays; ++i) elems += arrays[i].n;
+  if (elems == 0) return ISPRIME_OK;
+  // A batch of at most small_max elements in all takes the one-launch warp
+  // path (lowest latency); its descriptors carry element prefix sums.
+  const bool warp_form = elems <= ctx->tune.small_max && n_arrays < (1ull << 32);
+  const uint32_t tile = warp_form ? 1u : 1u << ctx->tune.batch_tile_log2;
   // Host-side descriptors: tile prefix sums (arrays with n == 0 get no tiles).
   std::vector<BatchDesc> descs(n_arrays);
-  uint64_t tiles = 0, elems = 0;
+  uint64_t tiles = 0;
   for (size_t i = 0; i < n_arrays; ++i) {
     descs[i].in = arrays[i].d_in;
     descs[i].out = arrays[i].d_out;
     descs[i].n = arrays[i].n;
     descs[i].tile_begin = tiles;
     tiles += (arrays[i].n + tile - 1) / tile;
-    elems += arrays[i].n;
   }
-  if (tiles == 0) return ISPRIME_OK;
   // The counter overshoots by one fetch per block: keep it far from wrapping.
   if (tiles >= (1ull << 31)) return set_error(ISPRIME_EINVAL, "batch has 2^31 tiles or more");
   const size_t bytes = sizeof(BatchHeader) + n_arrays * sizeof(BatchDesc);
@@ -270,6 +274,14 @@ int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, s
   IP_CUDA(cudaMemcpyAsync(bs->d_batch, bs->h_batch, bytes, cudaMemcpyHostToDevice, s));
   IP_CUDA(cudaEventRecord(bs->ev, s));
   bs->ev_valid = true;
+  if (warp_form) {
+    const BatchDesc* d_descs =
+        reinterpret_cast<const BatchDesc*>(static_cast<char*>(bs->d_batch) + sizeof(BatchHeader));
+    int st = launch_small_batched(ctx, d_descs, (uint32_t)n_arrays, elems, s);
+    if (st) return st;
+    ctx->stats.elements += elems;
+    return ISPRIME_OK;
+  }
 
   // The graph: reset the tile counter, launch the persistent kernel.
   const BatchVariant v = pick_variant(ctx->tune.td_primes, ctx->tune.rest_test);

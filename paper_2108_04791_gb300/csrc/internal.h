@@ -172,6 +172,10 @@ int launch_small_u64(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, siz
                      cudaStream_t s);
 int launch_small_f64(isprime_ctx* ctx, const double* d_in, uint8_t* d_out, size_t n,
                      unsigned long long* d_invalid, cudaStream_t s);
+// A batch in one-warp-per-element form: d_descs[i].tile_begin holds the
+// element prefix sum of array i (total elements in all arrays).
+int launch_small_batched(isprime_ctx* ctx, const BatchDesc* d_descs, uint32_t n_arrays,
+                         uint64_t total, cudaStream_t s);
 // Host values in (n <= kInlineMax), host bytes out; takes ctx->inline_mu and
 // ctx->mu itself and synchronises s.
 int inline_run(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n, cudaStream_t s);

@@ -202,3 +202,54 @@ int inline_run(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n,
 }
 
 }  // namespace ip
+
+namespace ip {
+
+namespace {
+
+// Element e of a batch whose descriptors hold element prefix sums in
+// tile_begin: the array is the last one whose prefix is <= e, found by a
+// 32-way search with one probe per lane per round (ceil(log32(arrays))
+// rounds; every lane of the warp holds the same e).
+__device__ __forceinline__ uint32_t find_array(const BatchDesc* __restrict__ descs,
+                                               uint32_t n_arrays, uint64_t e, int lane) {
+  uint32_t lo = 0, hi = n_arrays;  // answer in [lo, hi), prefix(lo) <= e
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t idx = lo + (uint32_t)lane * step;
+    const bool ok = idx < hi && __ldg(&descs[idx].tile_begin) <= e;
+    const unsigned m = __ballot_sync(kFull, ok);  // lanes 0..k-1 set, lane 0 always
+    const uint32_t last = 31u - (uint32_t)__clz((int)m);
+    lo = lo + last * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kSmallBlock)
+    small_batched_kernel(const BatchDesc* __restrict__ descs, uint32_t n_arrays, uint64_t total,
+                         const uint32_t* __restrict__ sieve, uint64_t S) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t e = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += nwarps) {
+    const uint32_t a = find_array(descs, n_arrays, e, lane);
+    const uint64_t j = e - descs[a].tile_begin;
+    // a plain load: the array may be mapped host memory (the server's short requests)
+    const bool prime = warp_isprime(descs[a].in[j], sieve, S, lane);
+    if (lane == 0) descs[a].out[j] = prime ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+int launch_small_batched(isprime_ctx* ctx, const BatchDesc* d_descs, uint32_t n_arrays,
+                         uint64_t total, cudaStream_t s) {
+  TimedLaunch tl;
+  int st = launch_begin(ctx, ISPRIME_K_SMALL, s, &tl);
+  if (st) return st;
+  small_batched_kernel<<<small_grid(ctx, total), kSmallBlock, 0, s>>>(d_descs, n_arrays, total,
+                                                                      ctx->d_sieve, sieve_cut(ctx));
+  return launch_end(ctx, s, &tl, "small_batched_kernel");
+}
+
+}  // namespace ip

@@ -343,6 +343,32 @@ def test_batched_tuning_and_small_sieve(kw):
                 _assert_same(a, o.cpu().numpy(), oracle.isprime_u64(a))
 
 
+@pytest.mark.parametrize("n_arrays", [1, 2, 31, 33, 700, 1500])
+def test_batched_short_batch_takes_the_warp_form(n_arrays):
+    """A batch of at most small_max elements runs as one warp-per-element
+    launch (element prefix sums, 32-way array search); results equal the
+    persistent kernel's and the oracle's, empty arrays included."""
+    rng = np.random.default_rng(n_arrays)
+    sizes = rng.integers(0, 12, size=n_arrays)
+    sizes[::5] = 0
+    vals = np.concatenate([np.array(SPECIAL * 3, dtype=np.uint64), plain_mixed(20000, seed=64)])
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    arrays = [vals[offs[i]:offs[i + 1]] for i in range(n_arrays)]
+    with ipg.Context(0) as c:
+        for small_max in (1 << 20, 0):
+            c.set_tuning(small_max=small_max)
+            c.timing_reset()
+            c.timing(True)
+            outs = c.isprime_batched([_to_dev(a) for a in arrays])
+            torch.cuda.synchronize()
+            rec = c.timing_read()
+            c.timing(False)
+            for a, o in zip(arrays, outs):
+                _assert_same(a, o.cpu().numpy(), oracle.isprime_u64(a))
+            if sizes.sum():
+                assert (rec["small"][1], rec["batched"][1]) == ((1, 0) if small_max else (0, 1))
+
+
 def test_batched_equals_plain_calls():
     vals = plain_mixed(1 << 18, seed=63)
     parts = np.split(vals, [1, 10, 1000, 50000, 50001])

@@ -26,7 +26,10 @@ def _requests(n_req, max_size, seed):
     return [np.ascontiguousarray(vals[offs[i]:offs[i + 1]]) for i in range(n_req)]
 
 
-def test_mixed_concurrent_requests_equal_results_alone():
+@pytest.mark.parametrize("n_slots,small_max", [(3, None), (1, None), (2, 1 << 12), (3, 0)])
+def test_mixed_concurrent_requests_equal_results_alone(n_slots, small_max):
+    """Short and long requests from four client threads; short ones (at most
+    small_max elements) are batched apart and keep the last slot."""
     reqs = _requests(240, 1 << 15, seed=91) + [np.zeros(0, np.uint64),
                                                np.array([2**64 - 59, 1, 2], np.uint64)]
     ctx = ipg.Context.default(0)
@@ -34,7 +37,10 @@ def test_mixed_concurrent_requests_equal_results_alone():
     for r in reqs:  # each request alone, through the plain path
         t = torch.from_numpy(r.view(np.int64)).cuda()
         alone.append(ctx.isprime(t).cpu().numpy() if r.size else np.zeros(0, np.uint8))
-    with ipg.Server(ctx, mem_budget_bytes=64 << 20, n_slots=3) as srv:
+    sctx = ipg.Context(0) if small_max is not None else ctx
+    if small_max is not None:
+        sctx.set_tuning(small_max=small_max)
+    with ipg.Server(sctx, mem_budget_bytes=64 << 20, n_slots=n_slots) as srv:
         results = [None] * len(reqs)
 
         def client(idx):
@@ -55,6 +61,35 @@ def test_mixed_concurrent_requests_equal_results_alone():
     assert st["requests"] == len(reqs) and st["elements"] == sum(r.size for r in reqs)
     assert 0 <= st["p50_ms"] <= st["p99_ms"] <= st["max_ms"] and st["tests_per_s"] > 0
     assert 1 <= st["batches"] <= len(reqs)
+    if sctx is not ctx:
+        sctx.close()
+
+
+def test_pinned_short_requests_are_served_in_place():
+    """Short requests in pinned host memory are read and written by the kernel
+    directly (no arena copies); long ones in the same stream of requests are
+    copied.  Every result equals the oracle's."""
+    reqs = _requests(120, 1 << 14, seed=93)
+    pool = torch.empty(sum(r.size for r in reqs), dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+    outs = torch.zeros(pool.size + 8 * len(reqs), dtype=torch.uint8).pin_memory().numpy()
+    views, ov, a, o = [], [], 0, 0
+    for r in reqs:
+        pool[a:a + r.size] = r
+        views.append(pool[a:a + r.size])
+        ov.append(outs[o + 1:o + 1 + r.size])  # odd output offsets
+        a += r.size
+        o += r.size + 8
+    ctx = ipg.Context(0)
+    ctx.set_tuning(small_max=1 << 12)
+    with ipg.Server(ctx, mem_budget_bytes=32 << 20, n_slots=2) as srv:
+        tickets = [srv.submit(v, out=w) for v, w in zip(views, ov)]
+        got = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    ctx.close()
+    for r, g_ in zip(reqs, got):
+        assert np.array_equal(g_, oracle.isprime_u64(r))
+    assert st["short_requests"] == sum(1 for r in reqs if r.size <= 1 << 12) > 0
+    assert st["p50_short_ms"] <= st["p99_short_ms"]
 
 
 def test_budget_refusal_unknown_ticket_and_timeout():
