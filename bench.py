@@ -49,15 +49,16 @@ WORK_PLAIN_LARGE = {
     "rest_squarings": 12.5845,
     "rest_multiplies": 6.3263,
 }
-# Integer multiply-pipe slots per operation in the schoolbook 2x32-bit-limb
-# form (one slot = one 32-bit low multiply-add; a 32x32->64 wide product or a
-# high product occupies the pipe for two slots, as measured on this GPU):
+# Integer multiply-pipe slots per operation of the library's Montgomery
+# arithmetic in 2x32-bit limbs (csrc/arith.cuh, mont_mul_c / mont_sqr_c; one
+# slot = one 32-bit low multiply-add; a 32x32->64 wide product occupies the
+# pipe for two slots, as measured on this GPU):
 #   multiplication: a*b 4 wide (8) + m = lo*n^-1 mod 2^64 1 wide + 2 low (4)
-#                   + hi(m*n) 4 wide (8) = 20
-#   squaring:       a*a 3 wide (6) + 4 + 8 = 18
+#                   + hi(m*n) from 3 wide (6; the m0*n0 product is not needed) = 18
+#   squaring:       a*a 3 wide (6) + 4 + 6 = 16
 #   divisibility test n * p^-1 mod 2^64: 1 wide + 2 low = 4
-IMAD_SLOTS_PER_MULMOD = 20
-IMAD_SLOTS_PER_SQUARING = 18
+IMAD_SLOTS_PER_MULMOD = 18
+IMAD_SLOTS_PER_SQUARING = 16
 IMAD_SLOTS_PER_TRIAL_TEST = 4
 IMAD_PER_SM_PER_CLK = 64                           # 32-bit IMAD issue rate per SM
 SM_COUNT_GB300 = 152

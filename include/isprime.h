@@ -64,8 +64,9 @@ typedef struct {
                               product (squaring with one cross product), 1 word-level, 2 128-bit
                               product with PTX word-level reduction, 3 fused product scanning,
                               4 128-bit multiply with fused squaring, 5 128-bit product with
-                              squaring as a general multiply */
-  uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..5) */
+                              squaring as a general multiply, 6 128-bit form in 32-bit words
+                              (PTX, wide products and carry chains, no m0 n0 product; default) */
+  uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..6) */
   uint32_t batch_block;    /* threads per block of the batched kernel (64..256, multiple of 32) */
   uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */
   uint32_t batch_blocks_per_sm; /* cap on resident batched blocks per SM (0 = occupancy limit) */

@@ -78,8 +78,8 @@ static isprime_tuning default_tuning() {
   t.blocks_per_sm = 16;
   t.td_primes = 15;  // 3..53
   t.chunk_log2 = 24;
-  t.mont_impl = 0;
-  t.mont_impl_base2 = 0;
+  t.mont_impl = 6;
+  t.mont_impl_base2 = 6;
   t.batch_block = 128;
   t.batch_tile_log2 = 10;
   t.batch_blocks_per_sm = 0;
@@ -98,8 +98,8 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.blocks_per_sm < 1 || t.blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "blocks_per_sm must be in [1, 32]");
   if (t.td_primes > 53) return set_error(ISPRIME_EINVAL, "td_primes must be in [0, 53]");
   if (t.chunk_log2 < 16 || t.chunk_log2 > 28) return set_error(ISPRIME_EINVAL, "chunk_log2 must be in [16, 28]");
-  if (t.mont_impl > 5) return set_error(ISPRIME_EINVAL, "mont_impl must be in [0, 5]");
-  if (t.mont_impl_base2 > 5) return set_error(ISPRIME_EINVAL, "mont_impl_base2 must be in [0, 5]");
+  if (t.mont_impl > 6) return set_error(ISPRIME_EINVAL, "mont_impl must be in [0, 6]");
+  if (t.mont_impl_base2 > 6) return set_error(ISPRIME_EINVAL, "mont_impl_base2 must be in [0, 6]");
   if (bad_block(t.batch_block, 256)) return set_error(ISPRIME_EINVAL, "batch_block must be a multiple of 32 in [32, 256]");
   if (t.batch_tile_log2 < 8 || t.batch_tile_log2 > 14) return set_error(ISPRIME_EINVAL, "batch_tile_log2 must be in [8, 14]");
   if (t.batch_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "batch_blocks_per_sm must be in [0, 32]");

@@ -166,6 +166,102 @@ __device__ __forceinline__ uint64_t mont_mul_p(uint64_t a, uint64_t b, uint64_t 
 }
 #endif
 
+#if defined(__CUDACC__)
+// The 128-bit form in 32-bit words as PTX, so that each partial product is
+// one wide multiply and each sum one add with carry (inputs a, b < n, odd n):
+//   a b       = p00 + (p01 + p10) 2^32 + p11 2^64        4 wide products
+//   m         = lo64(a b) n^-1 mod 2^64                 1 wide + 2 low products
+//   hi64(m n) = q11 + hi(q01) + hi(q10) + c1 + c         3 wide products
+// with q_ij = m_i n_j and c1 the carry of lo(q01) + lo(q10) = sl.  The high
+// word of m0 n0 is never formed: lo64(m n) = lo64(a b), so bits 32..63 of
+// m n are t1 (bits 32..63 of a b), and the carry that word adds at bit 64 is
+// c = [sl > t1].  c enters as the borrow of t1 - sl in the subtraction
+// r = hi64(a b) - hi64(m n), and n is added back when r < 0.
+#define IP_MONT_C_DECL                                                  \
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);            \
+  const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);            \
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);            \
+  const uint32_t i0 = (uint32_t)ninv, i1 = (uint32_t)(ninv >> 32);      \
+  uint32_t r0, r1;
+// Operands: %0 %1 result words; %2 %3 a; %4 %5 b; %6 %7 n; %8 %9 n^-1.
+#define IP_MONT_C_REGS                                                          \
+  ".reg .u32 p00l, p00h, p01l, p01h, p10l, p10h, p11l, p11h, t1, t2, t3;\n\t" \
+  ".reg .u32 m0, m1, q01l, q01h, q10l, q10h, q11l, q11h, sl, x, y, bo;\n\t"   \
+  ".reg .u64 w;\n\t"
+// After p00, p01 and p10: the rest of a b, then m, hi64(m n) and r.
+#define IP_MONT_C_TAIL                                                          \
+  /* p11 and t = a b = t3:t2:t1:p00l */                                         \
+  "mul.wide.u32 w, %3, %5;\n\t"                                                 \
+  "mov.b64 {p11l, p11h}, w;\n\t"                                                \
+  "add.cc.u32 t1, p00h, p01l;\n\t"                                              \
+  "addc.cc.u32 t2, p01h, p11l;\n\t"                                             \
+  "addc.u32 t3, p11h, 0;\n\t"                                                   \
+  "add.cc.u32 t1, t1, p10l;\n\t"                                                \
+  "addc.cc.u32 t2, t2, p10h;\n\t"                                               \
+  "addc.u32 t3, t3, 0;\n\t"                                                     \
+  /* m = (t1:p00l) n^-1 mod 2^64 */                                             \
+  "mul.wide.u32 w, p00l, %8;\n\t"                                               \
+  "mov.b64 {m0, m1}, w;\n\t"                                                    \
+  "mad.lo.u32 m1, p00l, %9, m1;\n\t"                                            \
+  "mad.lo.u32 m1, t1, %8, m1;\n\t"                                              \
+  /* q01, q10, q11; (y:x) = q11 + hi(q01) + hi(q10) + c1 */                      \
+  "mul.wide.u32 w, m0, %7;\n\t"                                                 \
+  "mov.b64 {q01l, q01h}, w;\n\t"                                                \
+  "mul.wide.u32 w, m1, %6;\n\t"                                                 \
+  "mov.b64 {q10l, q10h}, w;\n\t"                                                \
+  "mul.wide.u32 w, m1, %7;\n\t"                                                 \
+  "mov.b64 {q11l, q11h}, w;\n\t"                                                \
+  "add.cc.u32 sl, q01l, q10l;\n\t"                                              \
+  "addc.cc.u32 x, q11l, q01h;\n\t"                                              \
+  "addc.u32 y, q11h, 0;\n\t"                                                    \
+  "add.cc.u32 x, x, q10h;\n\t"                                                  \
+  "addc.u32 y, y, 0;\n\t"                                                       \
+  /* r = (t3:t2) - (y:x) - c, c = borrow of t1 - sl; + n if negative */         \
+  "sub.cc.u32 bo, t1, sl;\n\t"                                                  \
+  "subc.cc.u32 %0, t2, x;\n\t"                                                  \
+  "subc.cc.u32 %1, t3, y;\n\t"                                                  \
+  "subc.u32 bo, 0, 0;\n\t"                                                      \
+  "and.b32 x, bo, %6;\n\t"                                                      \
+  "and.b32 y, bo, %7;\n\t"                                                      \
+  "add.cc.u32 %0, %0, x;\n\t"                                                   \
+  "addc.u32 %1, %1, y;\n\t"
+#define IP_MONT_C_OPERANDS                                                      \
+  : "=r"(r0), "=r"(r1)                                                          \
+  : "r"(a0), "r"(a1), "r"(b0), "r"(b1), "r"(n0), "r"(n1), "r"(i0), "r"(i1)
+
+__device__ __forceinline__ uint64_t mont_mul_c(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) {
+  IP_MONT_C_DECL
+  asm("{\n\t" IP_MONT_C_REGS
+      "mul.wide.u32 w, %2, %4;\n\t"
+      "mov.b64 {p00l, p00h}, w;\n\t"
+      "mul.wide.u32 w, %2, %5;\n\t"
+      "mov.b64 {p01l, p01h}, w;\n\t"
+      "mul.wide.u32 w, %3, %4;\n\t"
+      "mov.b64 {p10l, p10h}, w;\n\t"
+      IP_MONT_C_TAIL "}" IP_MONT_C_OPERANDS);
+  return ((uint64_t)r1 << 32) | r0;
+}
+
+// Squaring: b = a, and the cross product a0 a1 serves as both p01 and p10.
+__device__ __forceinline__ uint64_t mont_sqr_c(uint64_t a, uint64_t n, uint64_t ninv) {
+  const uint64_t b = a;
+  IP_MONT_C_DECL
+  asm("{\n\t" IP_MONT_C_REGS
+      "mul.wide.u32 w, %2, %4;\n\t"
+      "mov.b64 {p00l, p00h}, w;\n\t"
+      "mul.wide.u32 w, %2, %5;\n\t"
+      "mov.b64 {p01l, p01h}, w;\n\t"
+      "mov.u32 p10l, p01l;\n\t"
+      "mov.u32 p10h, p01h;\n\t"
+      IP_MONT_C_TAIL "}" IP_MONT_C_OPERANDS);
+  return ((uint64_t)r1 << 32) | r0;
+}
+#undef IP_MONT_C_DECL
+#undef IP_MONT_C_REGS
+#undef IP_MONT_C_TAIL
+#undef IP_MONT_C_OPERANDS
+#endif
+
 // Word-level Montgomery multiplication (Montgomery 1985, two 32-bit words
 // of reduction per 64-bit product), written with 32x32+64 -> 64 wide
 // multiply-adds so that every partial product and its carry-in take one
@@ -291,6 +387,15 @@ IP_HD uint64_t mod_dbl(uint64_t x, uint64_t n) {
   return ((int64_t)x < 0 || y >= n) ? y - n : y;
 }
 
+// 2^64 mod n for odd n > 1 without a division: with k the bit length of n,
+// 2^(k-1) < n < 2^k, so 2^k mod n = 2^k - n; then 64 - k modular doublings.
+IP_HD uint64_t pow2_64_mod(uint64_t n) {
+  const int k = 64 - clz64(n);
+  uint64_t x = (k == 64) ? (0 - n) : ((1ull << k) - n);
+  for (int i = k; i < 64; ++i) x = mod_dbl(x, n);
+  return x;
+}
+
 IP_HD Mont64 mont64_setup(uint64_t n) {
   Mont64 m;
   m.n = n;
@@ -299,8 +404,7 @@ IP_HD Mont64 mont64_setup(uint64_t n) {
   i64 *= 2 - n * i64;  // one Newton step lifts the 32-bit inverse to 64 bits
   m.ninv = i64;
   m.q = 0u - i32;
-  // 2^64 mod n: for n > 2^63 it is 2^64 - n, otherwise reduce (0 - n) mod n.
-  m.one = ((int64_t)n < 0) ? (0 - n) : (0 - n) % n;
+  m.one = pow2_64_mod(n);  // R mod n
   m.mone = n - m.one;
   return m;
 }
@@ -313,6 +417,7 @@ IP_HD Mont64 mont64_setup(uint64_t n) {
 //   3: fused product-scanning multiplication and squaring (mont_mul_f/_sqr_f)
 //   4: 128-bit multiplication with the fused squaring
 //   5: 128-bit multiplication, squaring as a general multiplication
+//   6: 128-bit form in 32-bit words as PTX, no m0 n0 product (device)
 template <int kImpl>
 struct MontOps;
 
@@ -349,6 +454,17 @@ struct MontOps<5> {
 };
 
 #if defined(__CUDACC__)
+// 6: the word-level PTX form of the 128-bit REDC (mont_mul_c / mont_sqr_c)
+template <>
+struct MontOps<6> {
+  static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
+    return mont_mul_c(a, b, M.n, M.ninv);
+  }
+  static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
+    return mont_sqr_c(a, M.n, M.ninv);
+  }
+};
+
 template <>
 struct MontOps<2> {
   static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
@@ -600,13 +716,30 @@ IP_HD uint32_t mod_dbl32(uint32_t x, uint32_t n) {
   return ((int32_t)x < 0 || y >= n) ? y - n : y;
 }
 
+// 2^32 mod n for odd n > 1, as pow2_64_mod: 2^k - n, then 32 - k doublings.
+IP_HD uint32_t pow2_32_mod(uint32_t n) {
+  const int k = 32 - clz32(n);
+  uint32_t x = (k == 32) ? (0u - n) : ((1u << k) - n);
+  for (int i = k; i < 32; ++i) x = mod_dbl32(x, n);
+  return x;
+}
+
 IP_HD Mont32 mont32_setup(uint32_t n) {
   Mont32 m;
   m.n = n;
   m.ninv = inv32(n);
-  m.one = (uint32_t)((0x100000000ULL) % n);
+  m.one = pow2_32_mod(n);
   m.mone = n - m.one;
   return m;
+}
+
+// R^2 mod n (R = 2^32) from R mod n: 8 doublings give R 2^8, two Montgomery
+// squarings map it to R 2^16 and R 2^32 = R^2.
+IP_HD uint32_t mont32_r2(const Mont32& M) {
+  uint32_t x = M.one;
+  for (int i = 0; i < 8; ++i) x = mod_dbl32(x, M.n);
+  x = mont_mul32(x, x, M.n, M.ninv);
+  return mont_mul32(x, x, M.n, M.ninv);
 }
 
 // Strong test of odd n < 2^32 to base a (1 < a < n).  Base 2 multiplies by
@@ -623,7 +756,7 @@ IP_HD bool sprp32(const Mont32& M, uint32_t a, uint32_t d, int s) {
       x = ((d >> b) & 1) ? y : x;
     }
   } else {
-    uint32_t aR = (uint32_t)(((uint64_t)a << 32) % n);
+    const uint32_t aR = mont_mul32(a, mont32_r2(M), n, ninv);  // a R mod n
     x = aR;
     for (int b = top - 1; b >= 0; --b) {
       x = mont_mul32(x, x, n, ninv);

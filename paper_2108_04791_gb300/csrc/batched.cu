@@ -62,7 +62,7 @@ size_t batched_smem_bytes(uint32_t block, uint32_t tile) {
 // Arithmetic: the base-2 test squares with the general 128-bit-form
 // multiplication (MontOps<5>), the six-base test uses the one-cross-product
 // squaring (MontOps<0>); the better choice for each stage on this GPU.
-constexpr int kImplB2 = 5, kImplRest = 0;
+constexpr int kImplB2 = 6, kImplRest = 6;
 
 template <int kNtd, bool kLucas>
 __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {

@@ -172,6 +172,7 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
     case 3: launch_base2<3>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
     case 4: launch_base2<4>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
     case 5: launch_base2<5>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
+    case 6: launch_base2<6>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
     default: launch_base2<0>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
   }
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
@@ -182,6 +183,7 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
     case 3: launch_rest<3>(q, out, grid, block, lucas, s); break;
     case 4: launch_rest<4>(q, out, grid, block, lucas, s); break;
     case 5: launch_rest<5>(q, out, grid, block, lucas, s); break;
+    case 6: launch_rest<6>(q, out, grid, block, lucas, s); break;
     default: launch_rest<0>(q, out, grid, block, lucas, s); break;
   }
   if (ctx) st = launch_end(ctx, s, &tl, "mr64_rest_kernel");
