@@ -197,8 +197,8 @@ static BatchVariant pick_ntd(uint32_t ntd) {
   }
 }
 
-static BatchVariant pick_variant(uint32_t ntd, uint32_t lucas) {
-  return lucas ? pick_ntd<true>(ntd) : pick_ntd<false>(ntd);
+static BatchVariant pick_variant(uint32_t ntd, uint32_t rest_test) {
+  return rest_test == 1 ? pick_ntd<true>(ntd) : pick_ntd<false>(ntd);
 }
 
 // Grid: every SM full of resident blocks (occupancy with this shared memory).

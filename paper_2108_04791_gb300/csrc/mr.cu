@@ -136,7 +136,7 @@ static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned 
   if (window) {
     if (compact_min > 32)
       launch_base2_win<kImpl, 0>(q, out, grid, block, compact_min, sm_count, s);
-    else if (lucas)
+    else if (lucas == 1)
       launch_base2_win<kImpl, 2>(q, out, grid, block, compact_min, sm_count, s);
     else
       launch_base2_win<kImpl, 1>(q, out, grid, block, compact_min, sm_count, s);
