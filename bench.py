@@ -527,6 +527,16 @@ RANGES = {
 }
 
 
+def _measured_hbm_gbs() -> dict:
+    """HBM copy bandwidth measured on this GPU type (MEASURED_PEAKS.json), else the
+    earlier fallback measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return {"value": float(json.load(f)["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"value": 6800.0, "source": "fallback"}
+
+
 def run_range(args, world, rank, local):
     """isprime_range over a window of consecutive integers (no input array)."""
     import torch
@@ -557,14 +567,24 @@ def run_range(args, world, rank, local):
     kt = ctx.timing_read()
     value = count * world * steps / t
     primes = int(out.sum().item())
+    # Roofline of the range kernel (the one below S expands the bitmap: 1 byte written and
+    # 1/16 byte of bitmap read per value; above S the sieve kernel writes 1 byte per value).
+    below = max(0, min(lo + count, 1 << 32) - lo)
+    algo_bytes = count + below / 16
+    rk_ms, rk_n = kt.get("range", (0.0, 0))
+    peak = _measured_hbm_gbs()
+    achieved = algo_bytes / (rk_ms / max(rk_n, 1) / 1e3) / 1e9 if rk_n else None
+    range_roof = {"bound": "hbm", "achieved": achieved, "peak": peak["value"], "unit": "GB/s",
+                  "frac": achieved / peak["value"] if achieved else None, "traffic": None,
+                  "kernel": "range", "algorithmic_bytes_per_launch": algo_bytes,
+                  "peak_source": peak["source"]}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
                 "warmup": warm, "ms_per_step": 1e3 * t / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": args.workload, "lo": lo, "count": count, "description": desc,
                            "primes_found": primes},
-                "roofline": {"bound": "hbm", "bytes_per_value": 1 + (1 / 16 if lo < (1 << 32) else 0),
-                             "achieved_gbs": count * (1 + 1 / 16) * steps / t / 1e9},
+                "roofline": range_roof,
                 "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]} for k, v in kt.items()
                             if v[1]}}
         print(json.dumps(line), flush=True)
