@@ -18,7 +18,10 @@
 //                      itself (few idle lanes, no queue round trip).
 //   mr64_rest_kernel   the six remaining bases, 4-bit fixed-window
 //                      exponentiation with the per-thread window table in
-//                      shared memory; writes 1 for primes.
+//                      shared memory; the base-2 kernel wrote 1 for each
+//                      survivor, and a failing base writes 0.  A queue too
+//                      short to fill the grid six times over is spread one
+//                      (survivor, base) pair per thread.
 //   mr32_kernel        bases 2, 7, 61 in 32-bit Montgomery arithmetic for
 //                      survivors in [S, 2^32) (only when S < 2^32).
 // All arithmetic is in arith.cuh (ModExp / ModMultiply / ModAdd of
@@ -69,14 +72,17 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
       uint32_t base = 0;
       if (lane == leader) base = atomicAdd(&counters[2], (uint32_t)__popc(mask));
       base = __shfl_sync(0xFFFFFFFFu, base, leader);
-      if (pass) q64b[base + __popc(mask & ((1u << lane) - 1u))] = i;
+      if (pass) {
+        q64b[base + __popc(mask & ((1u << lane) - 1u))] = i;
+        out[qidx[i]] = 1;  // prime unless a later base rejects it
+      }
     }
   }
 }
 
 // kLucas: the strong Lucas test (Baillie-PSW with the base-2 stage) instead
 // of the six remaining Miller-Rabin bases.
-template <int kImpl, bool kLucas>
+template <int kImpl, bool kLucas, bool kSpread>
 __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restrict__ qn,
                                                         const uint32_t* __restrict__ qidx,
                                                         const uint32_t* __restrict__ q64b,
@@ -89,14 +95,31 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   // whole warps per iteration: both tests are warp-synchronous
   const int lane = threadIdx.x & 31;
   const uint32_t nthreads = gridDim.x * blockDim.x;
-  for (uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; wbase < count;
-       wbase += nthreads) {
+  const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+  constexpr uint32_t kRestBases = kNumBases64 - 1;
+  // The base-2 kernel wrote 1 for every survivor; a failing base writes 0.
+  if (kSpread && !kLucas && (uint64_t)count * kRestBases <= nthreads) {
+    // Few survivors: one (survivor, base) pair per thread, so a short queue
+    // takes the time of one exponentiation instead of six in a row.
+    const uint32_t pairs = count * kRestBases;
+    for (uint32_t wbase = first; wbase < pairs; wbase += nthreads) {
+      const uint32_t g = wbase + lane;
+      const bool valid = g < pairs;
+      const uint32_t e = valid ? g / kRestBases : 0u;
+      const uint32_t j = valid ? q64b[e] : 0u;
+      const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
+      const bool pass = base_passes_warp<kImpl>(n, 1 + (int)(g - e * kRestBases), tab, ld);
+      if (valid && !pass) out[qidx[j]] = 0;
+    }
+    return;
+  }
+  for (uint32_t wbase = first; wbase < count; wbase += nthreads) {
     const uint32_t i = wbase + lane;
     const bool valid = i < count;
     const uint32_t j = valid ? q64b[i] : 0u;
     const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
     const bool prime = kLucas ? lucas_warp<kImpl>(n, valid) : rest64_is_prime_warp<kImpl>(n, valid, tab, ld);
-    if (prime) out[qidx[j]] = 1;
+    if (valid && !prime) out[qidx[j]] = 0;
   }
 }
 
@@ -146,14 +169,20 @@ static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned 
   }
 }
 
+// spread_grid > 0: launch the variant that spreads (survivor, base) pairs
+// over the threads whenever the queue is at most a sixth of its threads.
 template <int kImpl>
 static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int lucas,
-                        cudaStream_t s) {
+                        unsigned spread_grid, cudaStream_t s) {
+  const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
   if (lucas) {
-    mr64_rest_kernel<kImpl, true><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+    mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+  } else if (spread_grid) {
+    mr64_rest_kernel<kImpl, false, true><<<spread_grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
+                                                                         q.counters, out);
   } else {
-    const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
-    mr64_rest_kernel<kImpl, false><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+    mr64_rest_kernel<kImpl, false, false><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
+                                                                   q.counters, out);
   }
 }
 
@@ -161,7 +190,7 @@ static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned b
 // six-base kernel (see MontOps).
 static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int impl,
                        int impl_b2, int window, int lucas, uint32_t compact_min, int sm_count,
-                       cudaStream_t s, isprime_ctx* ctx) {
+                       unsigned spread_grid, cudaStream_t s, isprime_ctx* ctx) {
   int st = ISPRIME_OK;
   TimedLaunch tl;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
@@ -178,13 +207,13 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
   switch (impl) {
-    case 1: launch_rest<1>(q, out, grid, block, lucas, s); break;
-    case 2: launch_rest<2>(q, out, grid, block, lucas, s); break;
-    case 3: launch_rest<3>(q, out, grid, block, lucas, s); break;
-    case 4: launch_rest<4>(q, out, grid, block, lucas, s); break;
-    case 5: launch_rest<5>(q, out, grid, block, lucas, s); break;
-    case 6: launch_rest<6>(q, out, grid, block, lucas, s); break;
-    default: launch_rest<0>(q, out, grid, block, lucas, s); break;
+    case 1: launch_rest<1>(q, out, grid, block, lucas, spread_grid, s); break;
+    case 2: launch_rest<2>(q, out, grid, block, lucas, spread_grid, s); break;
+    case 3: launch_rest<3>(q, out, grid, block, lucas, spread_grid, s); break;
+    case 4: launch_rest<4>(q, out, grid, block, lucas, spread_grid, s); break;
+    case 5: launch_rest<5>(q, out, grid, block, lucas, spread_grid, s); break;
+    case 6: launch_rest<6>(q, out, grid, block, lucas, spread_grid, s); break;
+    default: launch_rest<0>(q, out, grid, block, lucas, spread_grid, s); break;
   }
   if (ctx) st = launch_end(ctx, s, &tl, "mr64_rest_kernel");
   return st;
@@ -197,6 +226,13 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, uint64_t len, cudaStream_t s) {
   const uint64_t cap = (uint64_t)ctx->sm_count * ctx->tune.blocks_per_sm;
   const uint64_t want = (len + block - 1) / block;
   const unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+  // Chunks up to 2^22 elements take the rest kernel that can spread a short
+  // queue over (survivor, base) pairs (it decides on the device from the
+  // queue length); longer chunks take the variant without that mode, whose
+  // register allocation suits long queues.
+  const uint64_t want6 = (6 * len + block - 1) / block;  // six threads per element of the chunk
+  const unsigned spread_grid =
+      len <= ((uint64_t)1 << 22) ? (unsigned)(want6 < cap ? (want6 ? want6 : 1) : cap) : 0u;
   TimedLaunch tl;
   int st;
   if (sieve_cut(ctx) < (1ull << 32)) {
@@ -206,7 +242,8 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, uint64_t len, cudaStream_t s) {
   }
   return launch_mr64(ctx->q, out, grid, block, (int)ctx->tune.mont_impl,
                      (int)ctx->tune.mont_impl_base2, (int)ctx->tune.base2_window,
-                     (int)ctx->tune.rest_test, ctx->tune.compact_min, ctx->sm_count, s, ctx);
+                     (int)ctx->tune.rest_test, ctx->tune.compact_min, ctx->sm_count, spread_grid,
+                     s, ctx);
 }
 
 // Launch without a context (explicit grid and block and queue pointers);
@@ -216,7 +253,7 @@ int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, 
   if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
   // binary base-2 schedule (no shared memory), as this launcher always used
   launch_mr64(q, out, grid, block, 0, 5, /*window=*/0, /*lucas=*/0, /*compact_min=*/33,
-              /*sm_count=*/0, s, nullptr);
+              /*sm_count=*/0, /*spread_grid=*/0, s, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
 }

@@ -490,6 +490,40 @@ def test_bpsw_rejects_base2_strong_pseudoprimes(ctx_bpsw):
         assert not _gpu(v, c0).any()
 
 
+def _spsp_near_2p63(count, seed):
+    import random
+    import numtheory as nt
+    rng = random.Random(seed)
+    out = []
+    while len(out) < count:  # p (2p - 1) with both prime, near 2^63, that pass base 2
+        p = rng.randrange(2**31, 3_000_000_000) | 1
+        q = 2 * p - 1
+        if nt.trial_is_prime(p) and nt.trial_is_prime(q) and nt.strong_base2(p * q):
+            out.append(p * q)
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 1000, 5000, 40000])
+def test_short_queues_spread_over_bases(n, ctx_small_sieve):
+    """Chunks short enough for one (survivor, base) pair per thread: primes near
+    2^64 (every base passes) mixed with base-2 strong pseudoprimes (a later base
+    fails) and random large values, on the queue path (small_max = 0)."""
+    from workloads import load_pool
+    rng = np.random.default_rng(n)
+    primes = load_pool("primes_near_2p64.txt")
+    spsp = np.array(_spsp_near_2p63(12, seed=n), dtype=np.uint64)
+    v = np.concatenate([primes[rng.integers(0, primes.size, n)], spsp, plain_large(n, seed=n + 5)])
+    rng.shuffle(v)
+    v = v[:max(n, 1)] if n < spsp.size else v
+    want = oracle.isprime_u64(v)
+    old = ctx_small_sieve.tuning.small_max
+    ctx_small_sieve.set_tuning(small_max=0)
+    try:
+        _assert_same(v, _gpu(v, ctx_small_sieve), want)
+    finally:
+        ctx_small_sieve.set_tuning(small_max=old)
+
+
 def test_bpsw_batched(ctx_bpsw):
     from workloads import batched_arrays
     vals, offs = batched_arrays(n_arrays=64, max_size=1 << 15, seed=104)
