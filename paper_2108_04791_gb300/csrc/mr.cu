@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
                                                          uint32_t* __restrict__ counters,
                                                          uint32_t* __restrict__ q64b,
                                                          uint8_t* __restrict__ out,
-                                                         uint32_t compact_min) {
+                                                         uint32_t compact_min, uint32_t mark) {
   extern __shared__ uint64_t s_tab[];  // kWindow: 16 x blockDim
   const uint32_t count = *(volatile uint32_t*)&counters[0];
   const int lane = threadIdx.x & 31;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
       base = __shfl_sync(0xFFFFFFFFu, base, leader);
       if (pass) {
         q64b[base + __popc(mask & ((1u << lane) - 1u))] = i;
-        out[qidx[i]] = 1;  // prime unless a later base rejects it
+        if (mark) out[qidx[i]] = 1;  // prime unless a later base clears it (spread rest kernel)
       }
     }
   }
@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   const uint32_t nthreads = gridDim.x * blockDim.x;
   const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
   constexpr uint32_t kRestBases = kNumBases64 - 1;
-  // The base-2 kernel wrote 1 for every survivor; a failing base writes 0.
+  // kSpread: the base-2 kernel wrote 1 for every survivor and a failing base
+  // writes 0; otherwise a survivor found prime gets its 1 here.
   if (kSpread && !kLucas && (uint64_t)count * kRestBases <= nthreads) {
     // Few survivors: one (survivor, base) pair per thread, so a short queue
     // takes the time of one exponentiation instead of six in a row.
@@ -119,7 +120,11 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
     const uint32_t j = valid ? q64b[i] : 0u;
     const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
     const bool prime = kLucas ? lucas_warp<kImpl>(n, valid) : rest64_is_prime_warp<kImpl>(n, valid, tab, ld);
-    if (valid && !prime) out[qidx[j]] = 0;
+    if (kSpread) {
+      if (valid && !prime) out[qidx[j]] = 0;
+    } else if (prime) {
+      out[qidx[j]] = 1;
+    }
   }
 }
 
@@ -145,27 +150,28 @@ static unsigned resident_grid(const void* fn, unsigned block, size_t smem, int s
 
 template <int kImpl, int kRest>
 static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
-                             uint32_t compact_min, int sm_count, cudaStream_t s) {
+                             uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s) {
   const size_t smem = (size_t)16 * block * sizeof(uint64_t);
   const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, true, kRest>);
   grid = resident_grid(fn, block, smem, sm_count, grid);
   mr64_base2_kernel<kImpl, true, kRest><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.counters,
-                                                                  q.q64b, out, compact_min);
+                                                                  q.q64b, out, compact_min, mark);
 }
 
 template <int kImpl>
 static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int window,
-                         int lucas, uint32_t compact_min, int sm_count, cudaStream_t s) {
+                         int lucas, uint32_t compact_min, uint32_t mark, int sm_count,
+                         cudaStream_t s) {
   if (window) {
     if (compact_min > 32)
-      launch_base2_win<kImpl, 0>(q, out, grid, block, compact_min, sm_count, s);
+      launch_base2_win<kImpl, 0>(q, out, grid, block, compact_min, mark, sm_count, s);
     else if (lucas == 1)
-      launch_base2_win<kImpl, 2>(q, out, grid, block, compact_min, sm_count, s);
+      launch_base2_win<kImpl, 2>(q, out, grid, block, compact_min, mark, sm_count, s);
     else
-      launch_base2_win<kImpl, 1>(q, out, grid, block, compact_min, sm_count, s);
+      launch_base2_win<kImpl, 1>(q, out, grid, block, compact_min, mark, sm_count, s);
   } else {
     mr64_base2_kernel<kImpl, false, 0><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.counters,
-                                                              q.q64b, out, 33u);
+                                                              q.q64b, out, 33u, mark);
   }
 }
 
@@ -195,14 +201,18 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
   TimedLaunch tl;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
   const uint32_t cm = compact_min;
+  // the spread rest kernel clears survivors that a later base rejects, so the
+  // base-2 kernel marks its survivors prime first
+  const uint32_t mark = (spread_grid != 0 && lucas != 1) ? 1u : 0u;
+  if (lucas == 1) spread_grid = 0;
   switch (impl_b2) {
-    case 1: launch_base2<1>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
-    case 2: launch_base2<2>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
-    case 3: launch_base2<3>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
-    case 4: launch_base2<4>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
-    case 5: launch_base2<5>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
-    case 6: launch_base2<6>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
-    default: launch_base2<0>(q, out, grid, block, window, lucas, cm, sm_count, s); break;
+    case 1: launch_base2<1>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    case 2: launch_base2<2>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    case 3: launch_base2<3>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    case 4: launch_base2<4>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    case 5: launch_base2<5>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    case 6: launch_base2<6>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    default: launch_base2<0>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
   }
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
