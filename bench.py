@@ -511,7 +511,7 @@ def run_served(args, world, rank, local):
             "serve": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                       "max_ms": st["max_ms"], "batches": st["batches"], "span_s": st["span_s"],
                       "short_requests": st["short_requests"],
-                      "short_max_elements": ctx.tuning.small_max,
+                      "short_max_elements": ctx.tuning.serve_short_max,
                       "p50_short_ms": st["p50_short_ms"], "p99_short_ms": st["p99_short_ms"],
                       "p50_long_ms": st["p50_long_ms"], "p99_long_ms": st["p99_long_ms"],
                       "offered_tests_per_s": float(sizes.sum() / arrivals[-1]), "wall_s": wall},

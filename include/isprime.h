@@ -85,6 +85,9 @@ typedef struct {
   uint32_t sieve_cutover_log2; /* sieve / Miller-Rabin cutover of the array paths: the resident
                               sieve answers n < min(S, 2^k); values from there up to 2^32 take
                               trial division and the 32-bit Miller-Rabin test (0..32) */
+  uint32_t serve_short_max;/* a server created on the context batches requests of at most this
+                              many elements apart from longer ones, as one-launch warp batches
+                              on high-priority streams (0..2^20) */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -45,7 +45,7 @@ class Tuning(ctypes.Structure):
                 ("batch_tile_log2", ctypes.c_uint32), ("batch_blocks_per_sm", ctypes.c_uint32),
                 ("base2_window", ctypes.c_uint32), ("rest_test", ctypes.c_uint32),
                 ("small_max", ctypes.c_uint32), ("compact_min", ctypes.c_uint32),
-                ("sieve_cutover_log2", ctypes.c_uint32)]
+                ("sieve_cutover_log2", ctypes.c_uint32), ("serve_short_max", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -85,9 +85,10 @@ static isprime_tuning default_tuning() {
   t.batch_blocks_per_sm = 0;
   t.base2_window = 4;
   t.rest_test = 0;
-  t.small_max = 16384;
+  t.small_max = 8192;
   t.compact_min = 33;
   t.sieve_cutover_log2 = 32;
+  t.serve_short_max = 32768;
   return t;
 }
 
@@ -108,6 +109,7 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.small_max > (1u << 20)) return set_error(ISPRIME_EINVAL, "small_max must be in [0, 2^20]");
   if (t.compact_min > 33) return set_error(ISPRIME_EINVAL, "compact_min must be in [0, 33]");
   if (t.sieve_cutover_log2 > 32) return set_error(ISPRIME_EINVAL, "sieve_cutover_log2 must be in [0, 32]");
+  if (t.serve_short_max > (1u << 20)) return set_error(ISPRIME_EINVAL, "serve_short_max must be in [0, 2^20]");
   return ISPRIME_OK;
 }
 
@@ -437,7 +439,7 @@ int isprime_u64_batched(isprime_ctx* ctx, const isprime_array* arrays, size_t n_
   DeviceGuard g(ctx->device);
   int st = order_before(ctx, s);
   if (st) return st;
-  if ((st = batched_run(ctx, &ctx->batch, arrays, n_arrays, s))) return st;
+  if ((st = batched_run(ctx, &ctx->batch, arrays, n_arrays, ctx->tune.small_max, s))) return st;
   if ((st = order_after(ctx, s))) return st;
   ctx->stats.calls++;
   return ISPRIME_OK;

@@ -65,15 +65,16 @@ std::string cache_key(int device, size_t n, int mode) {
 const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_primes", "chunk_log2",
                          "mont_impl", "mont_impl_base2", "batch_block", "batch_tile_log2",
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
-                         "compact_min", "sieve_cutover_log2"};
+                         "compact_min", "sieve_cutover_log2", "serve_short_max"};
 uint32_t isprime_tuning::*kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
     &isprime_tuning::mont_impl_base2, &isprime_tuning::batch_block,
     &isprime_tuning::batch_tile_log2, &isprime_tuning::batch_blocks_per_sm,
     &isprime_tuning::base2_window, &isprime_tuning::rest_test, &isprime_tuning::small_max,
-    &isprime_tuning::compact_min, &isprime_tuning::sieve_cutover_log2};
-constexpr int kNumFields = 15;
+    &isprime_tuning::compact_min, &isprime_tuning::sieve_cutover_log2,
+    &isprime_tuning::serve_short_max};
+constexpr int kNumFields = 16;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

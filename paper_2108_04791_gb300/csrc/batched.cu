@@ -222,14 +222,14 @@ void batch_state_free(BatchState* b) {
 }
 
 int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, size_t n_arrays,
-                cudaStream_t s) {
+                uint64_t warp_max, cudaStream_t s) {
   const uint32_t block = ctx->tune.batch_block;
   uint64_t elems = 0;
   for (size_t i = 0; i < n_arrays; ++i) elems += arrays[i].n;
   if (elems == 0) return ISPRIME_OK;
-  // A batch of at most small_max elements in all takes the one-launch warp
+  // A batch of at most warp_max elements in all takes the one-launch warp
   // path (lowest latency); its descriptors carry element prefix sums.
-  const bool warp_form = elems <= ctx->tune.small_max && n_arrays < (1ull << 32);
+  const bool warp_form = elems <= warp_max && n_arrays < (1ull << 32);
   const uint32_t tile = warp_form ? 1u : 1u << ctx->tune.batch_tile_log2;
   // Host-side descriptors: tile prefix sums (arrays with n == 0 get no tiles).
   std::vector<BatchDesc> descs(n_arrays);

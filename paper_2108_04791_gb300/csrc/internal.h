@@ -183,8 +183,9 @@ int inline_run(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n,
 // batched.cu
 size_t batched_smem_bytes(uint32_t block, uint32_t tile);
 // Runs one batch with the given launch-site state on stream s (no context
-// ordering; the caller orders uses of `bs`).
+// ordering; the caller orders uses of `bs`).  A batch of at most warp_max
+// elements in all runs as one warp-per-element launch.
 int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, size_t n_arrays,
-                cudaStream_t s);
+                uint64_t warp_max, cudaStream_t s);
 
 }  // namespace ip

@@ -6,7 +6,7 @@
 // fixed arena of the given budget) and one of several stream slots become
 // free, and runs each batch as: copy-in, one batched launch (batched.cu)
 // over all its arrays, copy-out, event.  Short requests (at most the
-// context's small_max elements) are batched apart from long ones and keep a
+// context's serve_short_max elements) are batched apart from long ones and keep a
 // slot of their own, so their latency is that of a one-launch warp batch on a
 // high-priority stream; when their buffers are pinned host memory the kernel
 // reads and writes them in place, with no copies.  Batches on different slots overlap
@@ -146,9 +146,10 @@ void fail_batch(Slot& sl, int st) {
   }
 }
 
-// Size classes.  A request of at most small_cut elements is "short": short
-// requests are batched only with each other, up to small_cut elements per
-// batch (so the batch takes the one-launch warp path), and the last slot
+// Size classes.  A request of at most small_cut elements (the context's
+// serve_short_max) is "short": short requests are batched only with each
+// other, up to small_cut elements per batch, which run as one-launch warp
+// batches; the last slot
 // never takes a batch of long requests, so a short request never waits for a
 // long batch to finish.  Within a class requests keep their arrival order.
 bool is_short(const isprime_server* S, const Request& r) { return r.n <= S->small_cut; }
@@ -252,7 +253,9 @@ void dispatcher_loop(isprime_server* S) {
     }
     if (!st) {
       std::lock_guard<std::mutex> cl(S->ctx->mu);  // host-side bookkeeping of the context
-      st = batched_run(S->ctx, &sl.bs, arrays.data(), arrays.size(), stream);
+      // short batches (at most small_cut elements) run in the warp form
+      st = batched_run(S->ctx, &sl.bs, arrays.data(), arrays.size(), cls == 1 ? S->small_cut : 0,
+                       stream);
     }
     for (size_t i = 0; i < batch.size() && !st; ++i) {
       if (batch[i]->direct) continue;
@@ -349,7 +352,7 @@ int isprime_server_create(isprime_ctx* ctx, size_t mem_budget_bytes, int n_slots
   S->budget = mem_budget_bytes & ~(size_t)255;
   {
     std::lock_guard<std::mutex> lock(ctx->mu);
-    S->small_cut = ctx->tune.small_max;
+    S->small_cut = ctx->tune.serve_short_max;
   }
   int prev = 0;
   IP_CUDA(cudaGetDevice(&prev));

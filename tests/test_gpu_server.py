@@ -29,7 +29,7 @@ def _requests(n_req, max_size, seed):
 @pytest.mark.parametrize("n_slots,small_max", [(3, None), (1, None), (2, 1 << 12), (3, 0)])
 def test_mixed_concurrent_requests_equal_results_alone(n_slots, small_max):
     """Short and long requests from four client threads; short ones (at most
-    small_max elements) are batched apart and keep the last slot."""
+    serve_short_max elements) are batched apart and keep the last slot."""
     reqs = _requests(240, 1 << 15, seed=91) + [np.zeros(0, np.uint64),
                                                np.array([2**64 - 59, 1, 2], np.uint64)]
     ctx = ipg.Context.default(0)
@@ -39,7 +39,7 @@ def test_mixed_concurrent_requests_equal_results_alone(n_slots, small_max):
         alone.append(ctx.isprime(t).cpu().numpy() if r.size else np.zeros(0, np.uint8))
     sctx = ipg.Context(0) if small_max is not None else ctx
     if small_max is not None:
-        sctx.set_tuning(small_max=small_max)
+        sctx.set_tuning(serve_short_max=small_max)
     with ipg.Server(sctx, mem_budget_bytes=64 << 20, n_slots=n_slots) as srv:
         results = [None] * len(reqs)
 
@@ -80,7 +80,7 @@ def test_pinned_short_requests_are_served_in_place():
         a += r.size
         o += r.size + 8
     ctx = ipg.Context(0)
-    ctx.set_tuning(small_max=1 << 12)
+    ctx.set_tuning(serve_short_max=1 << 12)
     with ipg.Server(ctx, mem_budget_bytes=32 << 20, n_slots=2) as srv:
         tickets = [srv.submit(v, out=w) for v, w in zip(views, ov)]
         got = [srv.wait(t) for t in tickets]
