@@ -123,19 +123,26 @@ __device__ __forceinline__ bool rest64_is_prime_warp(uint64_t n, bool valid, uin
   return valid && prime;
 }
 
-// One base of Eq. 4 (index b >= 1) for an odd n >= 2^32 that passed base 2,
-// warp-synchronous like rest64_is_prime_warp (all 32 lanes call it, any mix
-// of n and b; the exponentiation runs the warp's largest nibble count).
+// The bases of Eq. 4 with indices first .. first + cnt - 1 (first >= 1) for
+// an odd n >= 2^32 that passed base 2: true when all pass.  Warp-synchronous
+// like rest64_is_prime_warp (all 32 lanes call it with the same cnt, any mix
+// of n and first; every exponentiation runs the warp's largest nibble count).
 template <int kImpl>
-__device__ __forceinline__ bool base_passes_warp(uint64_t n, int b, uint64_t* tab, int ld) {
+__device__ __forceinline__ bool bases_pass_warp(uint64_t n, int first, int cnt, uint64_t* tab,
+                                                int ld) {
   const Mont64 M = mont64_setup(n);
   const uint64_t r2 = mont64_r2<kImpl>(M);
   uint64_t d = n - 1;
   const int s = ctz64(d);
   d >>= s;
   const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)((64 - clz64(d) + kWin - 1) / kWin));
-  const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b], r2, M);
-  return sprp_tail64<kImpl>(M, mont_pow_win4<kImpl>(M, aR, d, tab, ld, nib), s);
+  bool pass = true;
+#pragma unroll 1
+  for (int k = 0; k < cnt; ++k) {
+    const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[first + k], r2, M);
+    pass = pass && sprp_tail64<kImpl>(M, mont_pow_win4<kImpl>(M, aR, d, tab, ld, nib), s);
+  }
+  return pass;
 }
 
 // Base 2 with 4-bit windows: T[w] = 2^w R mod n for w < 16 by doublings,

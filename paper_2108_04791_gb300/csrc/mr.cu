@@ -97,22 +97,30 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   const uint32_t nthreads = gridDim.x * blockDim.x;
   const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
   constexpr uint32_t kRestBases = kNumBases64 - 1;
-  // kSpread: the base-2 kernel wrote 1 for every survivor and a failing base
-  // writes 0; otherwise a survivor found prime gets its 1 here.
-  if (kSpread && !kLucas && (uint64_t)count * kRestBases <= nthreads) {
-    // Few survivors: one (survivor, base) pair per thread, so a short queue
-    // takes the time of one exponentiation instead of six in a row.
-    const uint32_t pairs = count * kRestBases;
-    for (uint32_t wbase = first; wbase < pairs; wbase += nthreads) {
-      const uint32_t g = wbase + lane;
-      const bool valid = g < pairs;
-      const uint32_t e = valid ? g / kRestBases : 0u;
-      const uint32_t j = valid ? q64b[e] : 0u;
-      const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
-      const bool pass = base_passes_warp<kImpl>(n, 1 + (int)(g - e * kRestBases), tab, ld);
-      if (valid && !pass) out[qidx[j]] = 0;
+  // kSpread: a queue shorter than the grid is spread over f = 6, 3 or 2
+  // threads per survivor (6 / f bases each), so it takes the time of 6 / f
+  // exponentiations instead of six; the base-2 kernel wrote 1 for every
+  // survivor and a failing base writes 0.  Otherwise one survivor per thread,
+  // and a survivor found prime gets its 1 here.
+  if (kSpread && !kLucas) {
+    uint32_t f = 1;
+    if ((uint64_t)count * kRestBases <= nthreads) f = kRestBases;
+    else if ((uint64_t)count * 3 <= nthreads) f = 3;
+    else if ((uint64_t)count * 2 <= nthreads) f = 2;
+    if (f > 1) {
+      const int per = (int)(kRestBases / f);
+      const uint32_t pairs = count * f;
+      for (uint32_t wbase = first; wbase < pairs; wbase += nthreads) {
+        const uint32_t g = wbase + lane;
+        const bool valid = g < pairs;
+        const uint32_t e = valid ? g / f : 0u;
+        const uint32_t j = valid ? q64b[e] : 0u;
+        const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
+        const bool pass = bases_pass_warp<kImpl>(n, 1 + (int)(g - e * f) * per, per, tab, ld);
+        if (valid && !pass) out[qidx[j]] = 0;
+      }
+      return;
     }
-    return;
   }
   for (uint32_t wbase = first; wbase < count; wbase += nthreads) {
     const uint32_t i = wbase + lane;
