@@ -59,9 +59,7 @@ size_t batched_smem_bytes(uint32_t block, uint32_t tile) {
   return (size_t)(tile + block) * 16 + (size_t)(2 * block) * 16 + (size_t)kTab * block * 8;
 }
 
-// Arithmetic: the base-2 test squares with the general 128-bit-form
-// multiplication (MontOps<5>), the six-base test uses the one-cross-product
-// squaring (MontOps<0>); the better choice for each stage on this GPU.
+// Arithmetic: Montgomery formulation 6 (32-bit words in PTX) in both stages.
 constexpr int kImplB2 = 6, kImplRest = 6;
 
 template <int kNtd, bool kLucas>
@@ -93,14 +91,13 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
     }
     __syncthreads();
     if (tid == 0) s_n1 = n1 - cnt;
-    bool pass = false;
-    if (mine) {
-      if (v < (1ull << 32)) {
-        if (mr32_is_prime((uint32_t)v)) *reinterpret_cast<uint8_t*>(a) = 1;
-      } else {
-        pass = base2_passes<kImplB2>(v);
-      }
-    }
+    if (mine && v < (1ull << 32) && mr32_is_prime((uint32_t)v)) *reinterpret_cast<uint8_t*>(a) = 1;
+    // base 2 with 4-bit windows, every lane of the warp taking part with the
+    // warp's largest nibble count (lanes without a 64-bit value test a prime)
+    const bool b2 = mine && v >= (1ull << 32);
+    const uint64_t nb = b2 ? v : 0xFFFFFFFFFFFFFFC5ull;
+    const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(nb));
+    const bool pass = base2_passes_win<kImplB2>(nb, tab, (int)B, nib) && b2;
     smem_push(pass, v, a, q2v, q2a, &s_n2);
     __syncthreads();
   };
