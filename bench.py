@@ -329,12 +329,19 @@ def run_mine(args, world, rank, local):
             achieved = per_launch / (dom_ms / dom_launches / 1e3)
             traffic = (NCU_TRAFFIC.get(dom) if NCU_TRAFFIC["sources"] == kernel_sources_hash()
                        else None)
+            per_kernel = {k: slots[k] * n / (ktimes[k][0] / ktimes[k][1] / 1e3) / peak_ops
+                          for k in slots if ktimes.get(k, (0, 0))[1]}
+            step_slots = sum(slots.values())
             roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                     "unit": "T int-mul slots/s", "frac": achieved / peak_ops, "traffic": traffic,
                     "kernel": dom, "kernel_ms_per_launch": dom_ms / dom_launches,
                     "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived; the probe measures "
                                    "64 mad.lo.u32 lanes/clk/SM)",
-                    "algorithmic_slots_per_element": slots[dom]}
+                    "algorithmic_slots_per_element": slots[dom],
+                    "frac_by_kernel": per_kernel,
+                    "step": {"slots_per_element": step_slots,
+                             "roofline_tests_per_s": peak_ops / step_slots,
+                             "frac": (n * world * args.steps / total_s) / world / (peak_ops / step_slots)}}
     kernels = {k: {"ms_per_step": v[0] / max(args.steps, 1), "launches": v[1]}
                for k, v in ktimes.items() if v[1]}
 
