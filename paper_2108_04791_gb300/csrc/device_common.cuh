@@ -4,8 +4,11 @@
 // Sec. 6.1.2-6.1.3): n < 2, even, sieve lookup below S, trial division by the
 // odd primes 3..p_k without division, and the routing of survivors to the
 // 32- or 64-bit Miller-Rabin test.
-// rest64_is_prime: the six bases 325 ... 1795265022 of Eq. 4 for an n >= 2^32
-// that passed base 2.  mr32_is_prime: bases {2, 7, 61} for n < 2^32.
+// rest64_is_prime_warp / bases_pass_warp: the six bases 325 ... 1795265022 of
+// Eq. 4 (all, or a subset) for an n >= 2^32 that passed base 2, warp-
+// synchronous.  base2_passes_win / base2_passes: the base-2 strong test.
+// lucas_warp: the strong Lucas test of the Baillie-PSW option.
+// mr32_is_prime: bases {2, 7, 61} for n < 2^32.
 #pragma once
 #include "arith.cuh"
 #include "tables.cuh"
@@ -84,27 +87,11 @@ __device__ __forceinline__ uint64_t mont_pow_win4(const Mont64& M, uint64_t aR, 
   return x;
 }
 
-// The six bases after base 2 (Eq. 4) for odd n >= 2^32 (no base is 0 mod n).
-template <int kImpl>
-__device__ __forceinline__ bool rest64_is_prime(uint64_t n, uint64_t* tab, int ld) {
-  const Mont64 M = mont64_setup(n);
-  const uint64_t r2 = mont64_r2<kImpl>(M);
-  uint64_t d = n - 1;
-  const int s = ctz64(d);
-  d >>= s;
-#pragma unroll 1
-  for (int b = 1; b < kNumBases64; ++b) {
-    const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b], r2, M);
-    const uint64_t x = mont_pow_win4<kImpl>(M, aR, d, tab, ld);
-    if (!sprp_tail64<kImpl>(M, x, s)) return false;
-  }
-  return true;
-}
-
-// Warp-synchronous form of rest64_is_prime: all 32 lanes call it; the six
-// exponentiations run the warp's largest nibble count and every base runs
-// (the inputs are almost all primes, which need all six anyway), so the warp
-// never splits.  Lanes with valid == false pass any odd n >= 2^32.
+// The six bases after base 2 (Eq. 4) for odd n >= 2^32 (no base is 0 mod n),
+// warp-synchronous: all 32 lanes call it; the six exponentiations run the
+// warp's largest nibble count and every base runs (the inputs are almost all
+// primes, which need all six anyway), so the warp never splits.  Lanes with
+// valid == false pass any odd n >= 2^32.
 template <int kImpl>
 __device__ __forceinline__ bool rest64_is_prime_warp(uint64_t n, bool valid, uint64_t* tab, int ld) {
   const Mont64 M = mont64_setup(n);

@@ -7,23 +7,25 @@
 //
 // Kernels (each a grid-stride loop over a queue whose length is read on the
 // device, so no host synchronisation separates the stages):
-//   mr64_base2_kernel  base 2 for every 64-bit survivor of trial division;
-//                      "multiply by 2" is a modular doubling.  Passing
-//                      elements (the primes and rare strong pseudoprimes) are
-//                      compacted with warp ballots into a second queue, so
-//                      the next kernel runs on dense warps of likely primes
-//                      instead of idling behind early-exiting composites.
-//                      With the compaction threshold compact_min <= 32, a warp
-//                      left with at least that many survivors finishes them
-//                      itself (few idle lanes, no queue round trip).
+//   mr64_base2_kernel  base 2 for every 64-bit survivor of trial division, by
+//                      4-bit windows over the table 2^w R (or, with
+//                      base2_window 0, binary with a modular doubling for
+//                      "multiply by 2").  Passing elements (the primes and rare
+//                      strong pseudoprimes) are compacted with warp ballots
+//                      into a second queue, so the next kernel runs on dense
+//                      warps of likely primes instead of idling behind
+//                      early-exiting composites.  With the compaction threshold
+//                      compact_min <= 32, a warp left with at least that many
+//                      survivors finishes them itself.
 //   mr64_rest_kernel   the six remaining bases, 4-bit fixed-window
 //                      exponentiation with the per-thread window table in
-//                      shared memory; the base-2 kernel wrote 1 for each
-//                      survivor, and a failing base writes 0.  A queue too
-//                      short to fill the grid six times over is spread one
-//                      (survivor, base) pair per thread.
+//                      shared memory.  On chunks of at most 2^22 elements a
+//                      queue shorter than the grid is spread over 6, 3 or 2
+//                      threads per survivor (the base-2 kernel then marks its
+//                      survivors prime and a failing base clears the byte);
+//                      otherwise one survivor per thread, writing 1 for primes.
 //   mr32_kernel        bases 2, 7, 61 in 32-bit Montgomery arithmetic for
-//                      survivors in [S, 2^32) (only when S < 2^32).
+//                      survivors between the sieve cutover and 2^32.
 // All arithmetic is in arith.cuh (ModExp / ModMultiply / ModAdd of
 // Sec. 2.2-2.4 as Montgomery multiplication and doubling).
 #include "device_common.cuh"
