@@ -321,8 +321,10 @@ typedef struct {
    * [4] multiply, 128-bit product with a word-level REDC in PTX carry chains
    * [5] squaring as a general multiply of [0]
    * [6] multiply, fused product-scanning form (wide multiply-adds carry all carries)
-   * [7] squaring, fused form */
-  double mont_variant[8];
+   * [7] squaring, fused form
+   * [8] multiply, 32-bit-word PTX form without the m0 n0 product (formulation 6)
+   * [9] squaring, the same form */
+  double mont_variant[10];
   double sm_clock_mhz;
 } isprime_int_rates;
 int isprime_measure_int_rates(int device, isprime_int_rates *out);

@@ -77,7 +77,7 @@ class _KTime(ctypes.Structure):
 
 class _IntRates(ctypes.Structure):
     _fields_ = [("mad_lo_u32", ctypes.c_double), ("mad_hi_u32", ctypes.c_double),
-                ("mad_wide_u32", ctypes.c_double), ("mont_variant", ctypes.c_double * 8),
+                ("mad_wide_u32", ctypes.c_double), ("mont_variant", ctypes.c_double * 10),
                 ("sm_clock_mhz", ctypes.c_double)]
 
 
@@ -423,7 +423,7 @@ def int_rates(device: int = 0) -> dict:
     _check(lib().isprime_measure_int_rates(device, ctypes.byref(r)))
     out = {k: getattr(r, k) for k, _ in r._fields_ if k != "mont_variant"}
     names = ["mul_128", "mul_word", "sqr_word", "sqr_128", "mul_128_ptxredc", "sqr_as_mul_128",
-             "mul_fused", "sqr_fused"]
+             "mul_fused", "sqr_fused", "mul_words_ptx", "sqr_words_ptx"]
     for i, nm in enumerate(names):
         out["mont_" + nm] = r.mont_variant[i]
     return out

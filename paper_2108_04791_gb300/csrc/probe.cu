@@ -9,7 +9,7 @@
 namespace ip {
 
 constexpr int kChains = 8;
-constexpr int kMontVariants = 8;
+constexpr int kMontVariants = 10;
 constexpr int kIters = 1024;
 
 template <int kOp>
@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t* sink, uint32_t 
 // wide multiply-adds; 2: the word-level dedicated squaring; 3: squaring in
 // the 128-bit form with one cross product; 4: 128-bit product with a PTX
 // word-level REDC; 5: mont_mul(a, a); 6: fused product-scanning
-// multiplication; 7: fused squaring.
+// multiplication; 7: fused squaring; 8 and 9: multiplication and squaring
+// of the 32-bit-word PTX form (mont_mul_c / mont_sqr_c).
 template <int kVar>
 __global__ void __launch_bounds__(256) mont_rate_kernel(uint64_t* sink, uint64_t seed) {
   uint64_t x[kChains];
@@ -81,6 +82,8 @@ __global__ void __launch_bounds__(256) mont_rate_kernel(uint64_t* sink, uint64_t
       if (kVar == 5) x[k] = mont_mul(x[k], x[k], n, ninv);
       if (kVar == 6) x[k] = mont_mul_f(x[k], x[(k + 1) & (kChains - 1)], n, q);
       if (kVar == 7) x[k] = mont_sqr_f(x[k], n, q);
+      if (kVar == 8) x[k] = mont_mul_c(x[k], x[(k + 1) & (kChains - 1)], n, ninv);
+      if (kVar == 9) x[k] = mont_sqr_c(x[k], n, ninv);
     }
   }
   uint64_t acc = 0;
@@ -148,6 +151,8 @@ int measure_int_rates(int device, isprime_int_rates* out) {
       if (var == 5) mont_rate_kernel<5><<<grid, 256>>>(s64, seed);
       if (var == 6) mont_rate_kernel<6><<<grid, 256>>>(s64, seed);
       if (var == 7) mont_rate_kernel<7><<<grid, 256>>>(s64, seed);
+      if (var == 8) mont_rate_kernel<8><<<grid, 256>>>(s64, seed);
+      if (var == 9) mont_rate_kernel<9><<<grid, 256>>>(s64, seed);
       IP_CUDA(cudaGetLastError());
       IP_CUDA(cudaEventRecord(e1));
       IP_CUDA(cudaEventSynchronize(e1));
