@@ -503,6 +503,15 @@ def _spsp_near_2p63(count, seed):
     return out
 
 
+@pytest.mark.parametrize("log2n", [20, 21, 22])
+def test_rest_queue_spread_factors(log2n):
+    """2^20, 2^21 and 2^22 large values give base-2 survivor queues of about
+    36K, 73K and 145K entries: the rest kernel's grid of 311K threads takes
+    them with 6, 3 and 2 threads per survivor."""
+    v = plain_large(1 << log2n, seed=110 + log2n)
+    _assert_same(v, _gpu(v), oracle.isprime_u64(v))
+
+
 @pytest.mark.parametrize("n", [1, 7, 64, 1000, 5000, 40000])
 def test_short_queues_spread_over_bases(n, ctx_small_sieve):
     """Chunks short enough for one (survivor, base) pair per thread: primes near
