@@ -185,9 +185,11 @@ int isprime_autotune(isprime_ctx *ctx, const uint64_t *d_sample, uint8_t *d_scra
 int isprime_tuning_format(const isprime_tuning *t, char *buf, size_t cap);
 
 /* End-to-end form for host buffers: copies h_in to the device in chunks
- * (through the context's pinned staging buffers), classifies, copies the
- * bytes back into h_out and synchronises `stream` before returning.  h_in and
- * h_out may be pageable or pinned. */
+ * (through the context's staging buffers), classifies each chunk on the
+ * context's own streams while the next one is copied, copies the bytes back
+ * into h_out and returns when h_out holds every result.  `stream` carries only
+ * calls of at most ISPRIME_HOST_INLINE_MAX values.  h_in and h_out may be
+ * pageable or pinned (pinned memory gives asynchronous copies). */
 int isprime_u64_host(isprime_ctx *ctx, const uint64_t *h_in, uint8_t *h_out, size_t n,
                      isprime_stream stream);
 

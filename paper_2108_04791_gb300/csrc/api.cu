@@ -123,10 +123,7 @@ static void free_queues(Queues& q) {
   q = Queues{};
 }
 
-static int ensure_queues(isprime_ctx* ctx, size_t cap) {
-  if (ctx->q.capacity >= cap) return ISPRIME_OK;
-  if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
-  free_queues(ctx->q);
+static int alloc_queues(Queues* out, size_t cap) {
   Queues q;
   IP_CUDA(cudaMalloc(&q.q64_n, cap * sizeof(uint64_t)));
   IP_CUDA(cudaMalloc(&q.q64_idx, cap * sizeof(uint32_t)));
@@ -135,12 +132,21 @@ static int ensure_queues(isprime_ctx* ctx, size_t cap) {
   IP_CUDA(cudaMalloc(&q.q32_idx, cap * sizeof(uint32_t)));
   IP_CUDA(cudaMalloc(&q.counters, 4 * sizeof(uint32_t)));
   q.capacity = cap;
-  ctx->q = q;
+  *out = q;
   return ISPRIME_OK;
 }
 
+static int ensure_queues(isprime_ctx* ctx, size_t cap) {
+  if (ctx->q.capacity >= cap) return ISPRIME_OK;
+  if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
+  free_queues(ctx->q);
+  return alloc_queues(&ctx->q, cap);
+}
+
 static size_t scratch_bytes(const isprime_ctx* ctx) {
-  return ctx->sieve_limit / 16 + ctx->q.capacity * 24 + ctx->stage_elems * 9;
+  return ctx->sieve_limit / 16 +
+         (ctx->q.capacity + ctx->host_q[0].capacity + ctx->host_q[1].capacity) * 24 +
+         ctx->stage_elems * 9;
 }
 
 struct DeviceGuard {
@@ -220,6 +226,35 @@ static int check_array_args(const void* d_in, const void* d_out, size_t n, size_
   return ISPRIME_OK;
 }
 
+// One chunk (len <= q.capacity) through the queue path: classify, then the
+// Miller-Rabin stages on the queues q, all on stream s.  The caller holds
+// ctx->mu and orders the uses of q.
+template <bool kF64>
+static int run_chunk(isprime_ctx* ctx, const Queues& q, const void* in, uint8_t* out, size_t len,
+                     unsigned long long* d_invalid, cudaStream_t s) {
+  IP_CUDA(cudaMemsetAsync(q.counters, 0, 4 * sizeof(uint32_t), s));
+  ClassifyArgs a;
+  a.in = in;
+  a.out = out;
+  a.n = len;
+  a.sieve = ctx->d_sieve;
+  a.sieve_limit = sieve_cut(ctx);
+  a.ntd = ctx->tune.td_primes;
+  a.td_square = td_square_for(ctx->tune.td_primes);
+  a.q64_n = q.q64_n;
+  a.q64_idx = q.q64_idx;
+  a.q32_n = q.q32_n;
+  a.q32_idx = q.q32_idx;
+  a.counters = q.counters;
+  a.invalid = d_invalid;
+  a.head = ((uintptr_t)a.in % 16) ? 1u : 0u;
+  if (a.head > len) a.head = (uint32_t)len;
+  a.pair_store = (((uintptr_t)(a.out + a.head)) % 2 == 0) ? 1u : 0u;
+  int st = kF64 ? launch_classify_f64(ctx, a, s) : launch_classify_u64(ctx, a, s);
+  if (st) return st;
+  return launch_mr(ctx, q, a.out, len, s);
+}
+
 template <bool kF64>
 static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t n,
                      unsigned long long* d_invalid, cudaStream_t s) {
@@ -245,27 +280,9 @@ static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t 
   const size_t step = std::min(chunk, ctx->q.capacity);
   for (size_t off = 0; off < n; off += step) {
     const size_t len = std::min(step, n - off);
-    IP_CUDA(cudaMemsetAsync(ctx->q.counters, 0, 4 * sizeof(uint32_t), s));
-    ClassifyArgs a;
-    a.in = static_cast<const char*>(d_in) + off * esz;
-    a.out = d_out + off;
-    a.n = len;
-    a.sieve = ctx->d_sieve;
-    a.sieve_limit = sieve_cut(ctx);
-    a.ntd = ctx->tune.td_primes;
-    a.td_square = td_square_for(ctx->tune.td_primes);
-    a.q64_n = ctx->q.q64_n;
-    a.q64_idx = ctx->q.q64_idx;
-    a.q32_n = ctx->q.q32_n;
-    a.q32_idx = ctx->q.q32_idx;
-    a.counters = ctx->q.counters;
-    a.invalid = d_invalid;
-    a.head = ((uintptr_t)a.in % 16) ? 1u : 0u;
-    if (a.head > len) a.head = (uint32_t)len;
-    a.pair_store = (((uintptr_t)(a.out + a.head)) % 2 == 0) ? 1u : 0u;
-    st = kF64 ? launch_classify_f64(ctx, a, s) : launch_classify_u64(ctx, a, s);
+    st = run_chunk<kF64>(ctx, ctx->q, static_cast<const char*>(d_in) + off * esz, d_out + off, len,
+                         d_invalid, s);
     if (st) return st;
-    if ((st = launch_mr(ctx, a.out, len, s))) return st;
   }
   if ((st = order_after(ctx, s))) return st;
   ctx->stats.calls++;
@@ -326,6 +343,9 @@ int isprime_ctx_destroy(isprime_ctx* ctx) {
     if (ctx->host_last) cudaEventDestroy(ctx->host_last);
     if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
     if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+    for (auto& hs : ctx->host_s)
+      if (hs) cudaStreamDestroy(hs);
+    for (auto& hq : ctx->host_q) free_queues(hq);
     if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
     if (ctx->scalar_s) cudaStreamSynchronize(ctx->scalar_s), cudaStreamDestroy(ctx->scalar_s);
     if (ctx->h_inline_out) cudaFreeHost(ctx->h_inline_out);
@@ -465,9 +485,11 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
   DeviceGuard g(ctx->device);
   if (n <= (size_t)kInlineMax) return inline_run(ctx, h_in, h_out, n, s);
   std::lock_guard<std::mutex> host_lock(ctx->host_mu);
-  // Pipeline: chunk k is copied in on copy_in, classified on `stream`, and
-  // copied out on copy_out, through staging slot k % 2, so the copy-in of
-  // chunk k+1 and the copy-out of chunk k-1 overlap the kernels of chunk k.
+  // Pipeline: chunk k is copied in on copy_in, classified on the compute
+  // stream of staging slot k % 2 with that slot's own queues, and copied out
+  // on copy_out, so the copy-in of chunk k+1 and the copy-out of chunk k-1
+  // overlap the kernels of chunk k, and the kernels of consecutive chunks
+  // overlap each other's tails.
   const size_t step_max = std::min((size_t)1 << ctx->tune.chunk_log2, (size_t)1 << 22);
   const size_t stage = std::min(step_max, n);
   {
@@ -475,9 +497,16 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
     if (!ctx->copy_in) {
       IP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
       IP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
+      for (auto& hs : ctx->host_s) IP_CUDA(cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking));
       for (auto& e : ctx->stage_ev) IP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       IP_CUDA(cudaEventCreateWithFlags(&ctx->host_last, cudaEventDisableTiming));
     }
+    // Earlier host-path calls have finished (each one waits before returning).
+    for (auto& hq : ctx->host_q)
+      if (hq.capacity < stage) {
+        free_queues(hq);
+        if ((st = alloc_queues(&hq, stage))) return st;
+      }
     if (ctx->stage_elems < stage) {
       if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
       cudaFree(ctx->d_stage_in);
@@ -514,17 +543,29 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
     if (k >= 2) IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, comp_done[slot], 0));
     IP_CUDA(cudaMemcpyAsync(din, h_in + off, len * 8, cudaMemcpyHostToDevice, ctx->copy_in));
     IP_CUDA(cudaEventRecord(in_ready[slot], ctx->copy_in));
-    IP_CUDA(cudaStreamWaitEvent(s, in_ready[slot], 0));
-    if (k >= 2) IP_CUDA(cudaStreamWaitEvent(s, out_done[slot], 0));
-    if ((st = run_array<false>(ctx, din, dout, len, nullptr, s))) return st;
-    IP_CUDA(cudaEventRecord(comp_done[slot], s));
+    const cudaStream_t cs = ctx->host_s[slot];
+    IP_CUDA(cudaStreamWaitEvent(cs, in_ready[slot], 0));
+    if (k >= 2) IP_CUDA(cudaStreamWaitEvent(cs, out_done[slot], 0));
+    {
+      std::lock_guard<std::mutex> lock(ctx->mu);
+      st = len <= ctx->tune.small_max
+               ? launch_small_u64(ctx, din, dout, len, cs)
+               : run_chunk<false>(ctx, ctx->host_q[slot], din, dout, len, nullptr, cs);
+    }
+    if (st) return st;
+    IP_CUDA(cudaEventRecord(comp_done[slot], cs));
     IP_CUDA(cudaStreamWaitEvent(ctx->copy_out, comp_done[slot], 0));
     IP_CUDA(cudaMemcpyAsync(h_out + off, dout, len, cudaMemcpyDeviceToHost, ctx->copy_out));
     IP_CUDA(cudaEventRecord(out_done[slot], ctx->copy_out));
   }
   IP_CUDA(cudaEventRecord(ctx->host_last, ctx->copy_out));
+  // copy_out waited for every chunk's kernels, so this is the end of the call
   IP_CUDA(cudaStreamSynchronize(ctx->copy_out));
-  IP_CUDA(cudaStreamSynchronize(s));
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->stats.calls++;
+    ctx->stats.elements += n;
+  }
   return ISPRIME_OK;
 }
 

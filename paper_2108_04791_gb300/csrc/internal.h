@@ -102,6 +102,8 @@ struct isprime_ctx {
   cudaEvent_t stage_ev[6] = {};      // per staging slot: copied in, computed, copied out
   cudaEvent_t host_last = nullptr;   // end of the previous host-path call
   ip::BatchState batch;              // batched path of the context's own calls
+  ip::Queues host_q[2];              // host path: one queue set per staging slot
+  cudaStream_t host_s[2] = {};       // host path: one compute stream per staging slot
   // latency path (small.cu): results of inline calls land in mapped host memory
   std::mutex inline_mu;
   uint8_t* h_inline_out = nullptr;   // pinned, mapped, ISPRIME_HOST_INLINE_MAX bytes
@@ -154,7 +156,7 @@ int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s)
 
 // mr.cu
 // len: elements of the chunk just classified (bounds the queue lengths).
-int launch_mr(isprime_ctx* ctx, uint8_t* out, uint64_t len, cudaStream_t s);
+int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cudaStream_t s);
 
 // Context-free launchers (explicit launch shape), used by noalloc.cu.
 int launch_classify_u64_raw(const ClassifyArgs& a, unsigned grid, unsigned block, cudaStream_t s);

@@ -239,7 +239,7 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
   return st;
 }
 
-int launch_mr(isprime_ctx* ctx, uint8_t* out, uint64_t len, cudaStream_t s) {
+int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cudaStream_t s) {
   const uint32_t block = ctx->tune.mr_block;
   // The queues hold at most `len` elements (one per thread and pass), so a
   // short chunk gets a short grid.
@@ -257,10 +257,10 @@ int launch_mr(isprime_ctx* ctx, uint8_t* out, uint64_t len, cudaStream_t s) {
   int st;
   if (sieve_cut(ctx) < (1ull << 32)) {
     if ((st = launch_begin(ctx, ISPRIME_K_MR32, s, &tl))) return st;
-    mr32_kernel<<<grid, block, 0, s>>>(ctx->q.q32_n, ctx->q.q32_idx, ctx->q.counters, out);
+    mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
-  return launch_mr64(ctx->q, out, grid, block, (int)ctx->tune.mont_impl,
+  return launch_mr64(q, out, grid, block, (int)ctx->tune.mont_impl,
                      (int)ctx->tune.mont_impl_base2, (int)ctx->tune.base2_window,
                      (int)ctx->tune.rest_test, ctx->tune.compact_min, ctx->sm_count, spread_grid,
                      s, ctx);

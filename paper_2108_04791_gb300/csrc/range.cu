@@ -256,7 +256,7 @@ int range_run(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out, cud
     a.q64_idx = ctx->q.q64_idx;
     a.counters = ctx->q.counters;
     if ((st = launch_range_sieve(ctx, a, s))) return st;
-    if ((st = launch_mr(ctx, d_out + done, c_n, s))) return st;
+    if ((st = launch_mr(ctx, ctx->q, d_out + done, c_n, s))) return st;
     done += c_n;
   }
   return ISPRIME_OK;
