@@ -10,7 +10,9 @@
  * are answered by a device-resident sieve (Sec. 6.1.3), the rest by trial
  * division by small primes (Sec. 6.1.2) and deterministic Miller-Rabin with
  * the seven bases of Eq. 4 (Sec. 2.1) in 64-bit Montgomery arithmetic, or the
- * bases {2, 7, 61} below 2^32.
+ * bases {2, 7, 61} below 2^32 (optionally base 2 and a strong Lucas test,
+ * the Baillie-PSW test of Sec. 10.1).  Short arrays and single values take a
+ * one-launch path with one warp per value.
  *
  * Conventions for every entry point:
  *   - Return value: ISPRIME_OK (0) or a negative isprime_status.  The text of
@@ -55,8 +57,8 @@ typedef struct CUstream_st *isprime_stream; /* same type as cudaStream_t */
 /* Launch and algorithm parameters of a context.  Results never depend on
  * them; only speed does. */
 typedef struct {
-  uint32_t classify_block; /* threads per block of the classify kernel (64..1024, multiple of 32) */
-  uint32_t mr_block;       /* threads per block of the Miller-Rabin kernels (64..1024, multiple of 32) */
+  uint32_t classify_block; /* threads per block of the classify kernel (32..1024, multiple of 32) */
+  uint32_t mr_block;       /* threads per block of the Miller-Rabin kernels (32..256, multiple of 32) */
   uint32_t blocks_per_sm;  /* grid = SMs x blocks_per_sm for grid-stride kernels (1..32) */
   uint32_t td_primes;      /* odd primes 3, 5, 7, ... used for trial division (0..53) */
   uint32_t chunk_log2;     /* elements per internal chunk = 2^chunk_log2 (16..28) */
@@ -67,7 +69,8 @@ typedef struct {
                               squaring as a general multiply, 6 128-bit form in 32-bit words
                               (PTX, wide products and carry chains, no m0 n0 product; default) */
   uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..6) */
-  uint32_t batch_block;    /* threads per block of the batched kernel (64..256, multiple of 32) */
+  uint32_t batch_block;    /* threads per block of the batched kernel (32..256, multiple of 32; the
+                              shared memory of batch_block and batch_tile_log2 must fit a block) */
   uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */
   uint32_t batch_blocks_per_sm; /* cap on resident batched blocks per SM (0 = occupancy limit) */
   uint32_t base2_window;   /* base-2 exponentiation: 0 binary with doublings, 4 4-bit windows */
@@ -92,7 +95,7 @@ typedef struct {
 
 /* Per-context counters since creation (or the last reset). */
 typedef struct {
-  uint64_t calls;          /* completed API calls that launched work */
+  uint64_t calls;          /* API calls that launched work */
   uint64_t elements;       /* elements classified */
   uint64_t kernel_launches;/* kernels launched by the library */
   uint64_t sieve_limit;    /* S: values below S are answered by the sieve */
@@ -102,8 +105,8 @@ typedef struct {
 /* ---------------------------------------------------------------- contexts */
 
 /* Creates a context on `device`: builds the odd-only sieve bitmap for
- * [0, sieve_limit) on the GPU (S/16 bytes; Sec. 6.1.3's "calculate all primes
- * up to N" kept resident) and allocates the work queues.  sieve_limit must be
+ * [0, sieve_limit) on the GPU (S/16 bytes; Sec. 6.1.3's sieve up to the array
+ * maximum, kept resident) and allocates the work queues.  sieve_limit must be
  * 0 (no sieve) or a multiple of 2^20 no larger than 2^32; ISPRIME_SIEVE_DEFAULT
  * selects 2^32.  Blocks until the sieve is built.  *out receives the
  * context; the caller destroys it with isprime_ctx_destroy. */

@@ -1,8 +1,8 @@
 // sieve.cu -- device-resident odd-only sieve of Eratosthenes.
 //
 // The paper's long-array path computes every prime up to the array maximum
-// and then looks elements up (Sec. 6.1.3, "Minimizing the number of
-// divisions"); the sieve itself is described in Sec. 1.  Here the sieve is
+// and then looks elements up (Sec. 6.1.3, which minimises the number of
+// divisions); the sieve itself is described in Sec. 1.  Here the sieve is
 // built once per context on the GPU for [0, S) and kept resident, so a
 // lookup is one bit read.
 //

@@ -1,8 +1,8 @@
 // tables.cuh -- compile-time constants for the primality kernels.
 //
-// Trial division by small primes (the paper's "shrinking the input array",
-// Sec. 6.1.2, and division minimising, Sec. 6.1.3) is done without any
-// division: for odd p and any n < 2^64,
+// Trial division by small primes (removing multiples of small primes before
+// the expensive test, Sec. 6.1.2, and keeping divisions few, Sec. 6.1.3) is
+// done without any division: for odd p and any n < 2^64,
 //     p | n  <=>  n * p^-1 mod 2^64 <= floor((2^64 - 1) / p)
 // (Granlund and Montgomery, PLDI 1994, Sec. 9).  The inverses and limits are
 // generated at compile time by constexpr Newton iterations.
