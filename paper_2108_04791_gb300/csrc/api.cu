@@ -74,7 +74,7 @@ static int collect_timing(isprime_ctx* ctx) {
 static isprime_tuning default_tuning() {
   isprime_tuning t{};
   t.classify_block = 256;
-  t.mr_block = 128;
+  t.mr_block = 256;
   t.blocks_per_sm = 16;
   t.td_primes = 15;  // 3..53
   t.chunk_log2 = 24;
