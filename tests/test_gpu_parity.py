@@ -503,13 +503,23 @@ def _spsp_near_2p63(count, seed):
     return out
 
 
+@pytest.fixture(scope="module")
+def ctx_mr128():
+    with ipg.Context(0) as c:
+        c.set_tuning(mr_block=128)
+        yield c
+
+
 @pytest.mark.parametrize("log2n", [20, 21, 22])
-def test_rest_queue_spread_factors(log2n):
+def test_rest_queue_spread_factors(log2n, ctx_mr128):
     """2^20, 2^21 and 2^22 large values give base-2 survivor queues of about
-    36K, 73K and 145K entries: the rest kernel's grid of 311K threads takes
-    them with 6, 3 and 2 threads per survivor."""
+    36K, 73K and 145K entries: with 128-thread blocks the rest kernel's grid of
+    2432 blocks (311K threads) takes them with 6, 3 and 2 threads per
+    survivor; with the default 256-thread blocks, 6, 6 and 3."""
     v = plain_large(1 << log2n, seed=110 + log2n)
-    _assert_same(v, _gpu(v), oracle.isprime_u64(v))
+    want = oracle.isprime_u64(v)
+    _assert_same(v, _gpu(v, ctx_mr128), want)
+    _assert_same(v, _gpu(v), want)
 
 
 @pytest.mark.parametrize("n", [1, 7, 64, 1000, 5000, 40000])
