@@ -271,8 +271,9 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
 int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, unsigned block,
                   cudaStream_t s) {
   if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
-  // binary base-2 schedule (no shared memory), as this launcher always used
-  launch_mr64(q, out, grid, block, 0, 5, /*window=*/0, /*lucas=*/0, /*compact_min=*/33,
+  // Montgomery formulation 6; base 2 by the binary schedule (its launch needs
+  // no occupancy query, so no SM count)
+  launch_mr64(q, out, grid, block, 6, 6, /*window=*/0, /*lucas=*/0, /*compact_min=*/33,
               /*sm_count=*/0, /*spread_grid=*/0, s, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
