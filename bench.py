@@ -66,18 +66,29 @@ SM_MAX_MHZ = 2070.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of this workload (profiles/*__plain_large_2p24.md); they hold for
-# the kernel sources whose hash is recorded and are reported as null otherwise.
-NCU_TRAFFIC = {"sources": "cadf4558fea4227c", "mr64_base2": 27.42e6, "mr64_rest": 45.44e6,
-               "classify_u64": 148.39e6}
+# the kernel sources whose hash is recorded and the tuning of the capture, and
+# are reported as null otherwise.
+NCU_TRAFFIC = {
+    "sources": "985f4cd9dc451ea7",
+    "tuning": {"classify_block": 256, "mr_block": 256, "blocks_per_sm": 16, "td_primes": 15,
+               "chunk_log2": 24, "mont_impl": 6, "mont_impl_base2": 6, "batch_block": 128,
+               "batch_tile_log2": 10, "batch_blocks_per_sm": 0, "base2_window": 4, "rest_test": 0,
+               "small_max": 8192, "compact_min": 33, "sieve_cutover_log2": 32,
+               "serve_short_max": 32768},
+    "mr64_base2": 27.42e6, "mr64_rest": 45.50e6, "classify_u64": 148.54e6}
+
+
+# The sources of the kernels whose DRAM traffic NCU_TRAFFIC records (device
+# code and the launchers that size their grids).
+KERNEL_SOURCES = ("arith.cuh", "tables.cuh", "device_common.cuh", "classify.cu", "mr.cu")
 
 
 def kernel_sources_hash() -> str:
-    import glob
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2108_04791_gb300", "csrc", "*"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_2108_04791_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -327,8 +338,9 @@ def run_mine(args, world, rank, local):
         if dom in slots:
             per_launch = slots[dom] * n
             achieved = per_launch / (dom_ms / dom_launches / 1e3)
-            traffic = (NCU_TRAFFIC.get(dom) if NCU_TRAFFIC["sources"] == kernel_sources_hash()
-                       else None)
+            same = (NCU_TRAFFIC["sources"] == kernel_sources_hash()
+                    and NCU_TRAFFIC["tuning"] == ctx.tuning.as_dict())
+            traffic = NCU_TRAFFIC.get(dom) if same else None
             per_kernel = {k: slots[k] * n / (ktimes[k][0] / ktimes[k][1] / 1e3) / peak_ops
                           for k in slots if ktimes.get(k, (0, 0))[1]}
             step_slots = sum(slots.values())

@@ -525,17 +525,18 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
   cudaEvent_t* out_done = &ctx->stage_ev[4];   // [2] copy-out of a slot finished
   // The slots may still be in use by a previous call's last chunks.
   IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->host_last, 0));
-  // The first chunks are a quarter and a half of a full one, so that the
-  // kernels start after a short first copy and the pipeline fills sooner
-  // (measured: 13.6 against 13.1 G tests/s on 2^24 values; an eighth first
-  // was slower again); the rest of the array is cut into equal chunks of at
+  // Arrays of at least four full chunks start with a quarter and a half of a
+  // full chunk, so that the kernels start after a short first copy and the
+  // pipeline fills sooner (measured: 13.6 against 13.1 G tests/s on 2^24
+  // values; an eighth first was slower again); shorter arrays would only pay
+  // the extra launches.  The rest of the array is cut into equal chunks of at
   // most a full one, so no short chunk is left at the end.
-  const size_t ramp = std::max(step / 4, (size_t)1) + std::max(step / 2, (size_t)1);
-  const size_t rest_chunks = n > ramp ? (n - ramp + step - 1) / step : 0;
-  const size_t even = rest_chunks ? (n - ramp + rest_chunks - 1) / rest_chunks : step;
+  const bool ramp_up = n >= 4 * step;
+  const size_t ramp = ramp_up ? step / 4 + step / 2 : 0;
+  const size_t rest_chunks = (n - ramp + step - 1) / step;
+  const size_t even = (n - ramp + rest_chunks - 1) / rest_chunks;
   for (size_t off = 0, k = 0, len = 0; off < n; off += len, ++k) {
-    const size_t want = k == 0 ? std::max(step / 4, (size_t)1)
-                      : k == 1 ? std::max(step / 2, (size_t)1) : even;
+    const size_t want = ramp_up && k == 0 ? step / 4 : ramp_up && k == 1 ? step / 2 : even;
     len = std::min(want, n - off);
     const int slot = (int)(k & 1);
     uint64_t* din = ctx->d_stage_in + slot * step;
