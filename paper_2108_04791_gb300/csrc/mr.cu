@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
                                                         const uint32_t* __restrict__ qidx,
                                                         const uint32_t* __restrict__ q64b,
                                                         const uint32_t* __restrict__ counters,
-                                                        uint8_t* __restrict__ out) {
+                                                        uint8_t* __restrict__ out,
+                                                        uint32_t spread_threads) {
   extern __shared__ uint64_t s_tab[];  // kTab x blockDim
   uint64_t* tab = s_tab + threadIdx.x;
   const int ld = blockDim.x;
@@ -105,10 +106,13 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   // survivor and a failing base writes 0.  Otherwise one survivor per thread,
   // and a survivor found prime gets its 1 here.
   if (kSpread && !kLucas) {
+    // f from the threads the chunk could use (spread_threads, six per element
+    // of the chunk up to the grid cap); the launch itself is capped at the
+    // blocks that can be resident and strides over the pairs
     uint32_t f = 1;
-    if ((uint64_t)count * kRestBases <= nthreads) f = kRestBases;
-    else if ((uint64_t)count * 3 <= nthreads) f = 3;
-    else if ((uint64_t)count * 2 <= nthreads) f = 2;
+    if ((uint64_t)count * kRestBases <= spread_threads) f = kRestBases;
+    else if ((uint64_t)count * 3 <= spread_threads) f = 3;
+    else if ((uint64_t)count * 2 <= spread_threads) f = 2;
     if (f > 1) {
       const int per = (int)(kRestBases / f);
       const uint32_t pairs = count * f;
@@ -189,16 +193,22 @@ static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned 
 // over the threads whenever the queue is at most a sixth of its threads.
 template <int kImpl>
 static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int lucas,
-                        unsigned spread_grid, cudaStream_t s) {
+                        unsigned spread_grid, int sm_count, cudaStream_t s) {
   const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
   if (lucas) {
-    mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters, out);
+    mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
+                                                                out, 0u);
   } else if (spread_grid) {
-    mr64_rest_kernel<kImpl, false, true><<<spread_grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
-                                                                         q.counters, out);
+    // at most the blocks that can be resident: more would only queue up (and
+    // cost their launch when the queue is empty)
+    const uint32_t spread_threads = spread_grid * block;
+    const void* fn = reinterpret_cast<const void*>(&mr64_rest_kernel<kImpl, false, true>);
+    const unsigned g = resident_grid(fn, block, smem, sm_count, spread_grid);
+    mr64_rest_kernel<kImpl, false, true><<<g, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
+                                                                out, spread_threads);
   } else {
     mr64_rest_kernel<kImpl, false, false><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
-                                                                   q.counters, out);
+                                                                   q.counters, out, 0u);
   }
 }
 
@@ -227,13 +237,13 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
   switch (impl) {
-    case 1: launch_rest<1>(q, out, grid, block, lucas, spread_grid, s); break;
-    case 2: launch_rest<2>(q, out, grid, block, lucas, spread_grid, s); break;
-    case 3: launch_rest<3>(q, out, grid, block, lucas, spread_grid, s); break;
-    case 4: launch_rest<4>(q, out, grid, block, lucas, spread_grid, s); break;
-    case 5: launch_rest<5>(q, out, grid, block, lucas, spread_grid, s); break;
-    case 6: launch_rest<6>(q, out, grid, block, lucas, spread_grid, s); break;
-    default: launch_rest<0>(q, out, grid, block, lucas, spread_grid, s); break;
+    case 1: launch_rest<1>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    case 2: launch_rest<2>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    case 3: launch_rest<3>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    case 4: launch_rest<4>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    case 5: launch_rest<5>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    case 6: launch_rest<6>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    default: launch_rest<0>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
   }
   if (ctx) st = launch_end(ctx, s, &tl, "mr64_rest_kernel");
   return st;
