@@ -116,21 +116,40 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
   const uint64_t ntiles = (npairs + tile_pairs - 1) / tile_pairs;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     uint64_t v[2 * kPairsPerThread];
-    int d[2 * kPairsPerThread];
-    uint32_t n64 = 0, n32 = 0, nbad = 0;
+    uint32_t dm = 0;     // the eight decisions, two bits each (element j at bits 2j, 2j+1)
+    uint32_t sneed = 0;  // elements whose answer is a sieve bit (bit j), looked up below
+    uint32_t nbad = 0;
 #pragma unroll
     for (int k = 0; k < kPairsPerThread; ++k) {
       const uint64_t p = tile * tile_pairs + (uint64_t)k * blockDim.x + threadIdx.x;
-      d[2 * k] = d[2 * k + 1] = kComposite;
       v[2 * k] = v[2 * k + 1] = 0;
       if (p < npairs) {
-        const uint64_t i0 = head + 2 * p;
         bool ok0, ok1;
-        Loader<T>::pair(a.in, i0, &v[2 * k], &v[2 * k + 1], &ok0, &ok1);
-        d[2 * k] = ok0 ? classify_value<kNtd>(v[2 * k], a) : kComposite;
-        d[2 * k + 1] = ok1 ? classify_value<kNtd>(v[2 * k + 1], a) : kComposite;
+        Loader<T>::pair(a.in, head + 2 * p, &v[2 * k], &v[2 * k + 1], &ok0, &ok1);
+        const int d0 = ok0 ? classify_value<kNtd, ClassifyArgs, true>(v[2 * k], a) : kComposite;
+        const int d1 = ok1 ? classify_value<kNtd, ClassifyArgs, true>(v[2 * k + 1], a) : kComposite;
         nbad += (uint32_t)!ok0 + (uint32_t)!ok1;
-        const uint8_t o0 = (uint8_t)(d[2 * k] == kPrime), o1 = (uint8_t)(d[2 * k + 1] == kPrime);
+        sneed |= ((uint32_t)(d0 == kSieveLookup) << (2 * k)) |
+                 ((uint32_t)(d1 == kSieveLookup) << (2 * k + 1));
+        dm |= ((uint32_t)(d0 & 3) << (4 * k)) | ((uint32_t)(d1 & 3) << (4 * k + 2));
+      }
+    }
+    // The sieve lookups of the tile's elements, all in flight together
+    // (kSieveLookup & 3 == kComposite, so a set bit turns the code to kPrime).
+    static_assert((kSieveLookup & 3) == kComposite, "deferred lookups start as composite");
+    if (sneed) {
+#pragma unroll
+      for (int e = 0; e < 2 * kPairsPerThread; ++e)
+        if ((sneed >> e) & 1u)
+          dm |= ((__ldg(a.sieve + (v[e] >> 6)) >> ((uint32_t)(v[e] >> 1) & 31u)) & 1u) << (2 * e);
+    }
+#pragma unroll
+    for (int k = 0; k < kPairsPerThread; ++k) {
+      const uint64_t p = tile * tile_pairs + (uint64_t)k * blockDim.x + threadIdx.x;
+      if (p < npairs) {
+        const uint64_t i0 = head + 2 * p;
+        const uint8_t o0 = (uint8_t)(((dm >> (4 * k)) & 3u) == kPrime);
+        const uint8_t o1 = (uint8_t)(((dm >> (4 * k + 2)) & 3u) == kPrime);
         if (a.pair_store)
           *reinterpret_cast<uint16_t*>(a.out + i0) = (uint16_t)(o0 | (o1 << 8));
         else {
@@ -139,11 +158,10 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
         }
       }
     }
-#pragma unroll
-    for (int j = 0; j < 2 * kPairsPerThread; ++j) {
-      n64 += (uint32_t)(d[j] == kMR64);
-      n32 += (uint32_t)(d[j] == kMR32);
-    }
+    // kMR64 = 0b10, kMR32 = 0b11: count the codes by their two bits
+    static_assert(kComposite == 0 && kPrime == 1 && kMR64 == 2 && kMR32 == 3, "2-bit decision codes");
+    const uint32_t dhi = (dm >> 1) & 0x5555u, dlo = dm & 0x5555u;
+    const uint32_t n64 = __popc(dhi & ~dlo), n32 = __popc(dhi & dlo);
     // counts fit in 16 bits each (<= 8 per thread, <= 8192 per block)
     uint32_t total;
     const uint32_t pre = block_exclusive_scan(n64 | (n32 << 16), s_scan, &total);
@@ -165,11 +183,12 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int j = 2 * k + h;
-        if (d[j] == kMR64) {
+        const int dj = (int)((dm >> (2 * j)) & 3u);
+        if (dj == kMR64) {
           a.q64_n[pos64] = v[j];
           a.q64_idx[pos64] = i0 + h;
           ++pos64;
-        } else if (d[j] == kMR32) {
+        } else if (dj == kMR32) {
           a.q32_n[pos32] = (uint32_t)v[j];
           a.q32_idx[pos32] = i0 + h;
           ++pos32;

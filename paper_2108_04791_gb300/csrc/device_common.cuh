@@ -19,7 +19,7 @@ namespace ip {
 static __constant__ TdTable c_td = make_td_table();
 static __constant__ BaseTable c_bases = make_base_table();
 
-enum : int { kComposite = 0, kPrime = 1, kMR64 = 2, kMR32 = 3 };
+enum : int { kComposite = 0, kPrime = 1, kMR64 = 2, kMR32 = 3, kSieveLookup = 4 };
 
 // Double input: finite, >= 0, integral and <= 2^53 (Sec. 8.1) converts
 // exactly; anything else is invalid (output 0, counted).
@@ -35,12 +35,16 @@ constexpr int kTab = 1 << kWin;
 // kNtd >= 0: the trial-division count is a compile-time constant, the loops
 // unroll and the inverses and limits become constant operands of the
 // multiply and compare instructions.  kNtd < 0: runtime count a.ntd.
-template <int kNtd, typename P>
+// kDefer: an odd n below the sieve limit returns kSieveLookup instead of its
+// sieve bit, so that the caller can issue the lookups of several values
+// together.
+template <int kNtd, typename P, bool kDefer = false>
 __device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
   if (n < 2) return kComposite;
   if ((n & 1) == 0) return n == 2 ? kPrime : kComposite;
   if (n < a.sieve_limit)
-    return (int)((__ldg(a.sieve + (n >> 6)) >> ((uint32_t)(n >> 1) & 31u)) & 1u);
+    return kDefer ? kSieveLookup
+                  : (int)((__ldg(a.sieve + (n >> 6)) >> ((uint32_t)(n >> 1) & 31u)) & 1u);
   bool hit = false, equal = false;
   const uint32_t ntd = kNtd >= 0 ? (uint32_t)kNtd : a.ntd;
   if (n < (1ull << 32)) {
