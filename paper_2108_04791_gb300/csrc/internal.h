@@ -29,7 +29,7 @@ struct Queues {
   uint32_t* q64b = nullptr;     // positions in q64 that passed the base-2 test
   uint32_t* q32_n = nullptr;    // values in [S, 2^32) that survived trial division
   uint32_t* q32_idx = nullptr;
-  uint32_t* counters = nullptr; // [0] q64 size, [1] q32 size, [2] q64b size, [3] unused
+  uint32_t* counters = nullptr; // [0] q64 size, [1] q32 size, [2] q64b size, [3] base-2 task counter
   size_t capacity = 0;
 };
 
