@@ -69,13 +69,13 @@ SM_MAX_MHZ = 2070.0
 # the kernel sources whose hash is recorded and the tuning of the capture, and
 # are reported as null otherwise.
 NCU_TRAFFIC = {
-    "sources": "e7f77e8fc7c85e30",
+    "sources": "1c13260fc0300556",
     "tuning": {"classify_block": 256, "mr_block": 256, "blocks_per_sm": 16, "td_primes": 15,
                "chunk_log2": 24, "mont_impl": 6, "mont_impl_base2": 6, "batch_block": 128,
-               "batch_tile_log2": 10, "batch_blocks_per_sm": 0, "base2_window": 4, "rest_test": 0,
+               "batch_tile_log2": 10, "batch_blocks_per_sm": 0, "base2_window": 1, "rest_test": 0,
                "small_max": 8192, "compact_min": 33, "sieve_cutover_log2": 32,
                "serve_short_max": 32768},
-    "mr64_base2": 27.42e6, "mr64_rest": 45.38e6, "classify_u64": 145.37e6}
+    "mr64_base2": 27.42e6, "mr64_rest": 45.49e6, "classify_u64": 145.05e6}
 
 
 # The sources of the kernels whose DRAM traffic NCU_TRAFFIC records (device

@@ -73,7 +73,11 @@ typedef struct {
                               shared memory of batch_block and batch_tile_log2 must fit a block) */
   uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */
   uint32_t batch_blocks_per_sm; /* cap on resident batched blocks per SM (0 = occupancy limit) */
-  uint32_t base2_window;   /* base-2 exponentiation: 0 binary with doublings, 4 4-bit windows */
+  uint32_t base2_window;   /* base-2 exponentiation: 0 binary with a doubling per set bit;
+                              1 4-bit windows, x 2^w mod n as x 2^w - q n with q estimated
+                              from a single-precision reciprocal of n (default); 4 4-bit
+                              windows, x 2^w R mod n by a Montgomery product with a table of
+                              2^w R in shared memory */
   uint32_t rest_test;      /* after base 2: 0 the six remaining bases of Eq. 4 (default), 1 the
                               strong Lucas test with Selfridge's parameters (Baillie-PSW).
                               Both are exact below 2^64; 1 rests on the published search
@@ -84,7 +88,7 @@ typedef struct {
                               compact_min survivors finishes them in place (the rest_test
                               stage run by the same warp) instead of appending them to the
                               survivor queue; 0..33, 33 = always compact.  In-place finishing
-                              needs base2_window 4 (with 0 the survivors are always compacted) */
+                              needs base2_window 1 or 4 (with 0 the survivors are always compacted) */
   uint32_t sieve_cutover_log2; /* sieve / Miller-Rabin cutover of the array paths: the resident
                               sieve answers n < min(S, 2^k); values from there up to 2^32 take
                               trial division and the 32-bit Miller-Rabin test (0..32) */

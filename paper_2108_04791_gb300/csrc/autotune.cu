@@ -40,7 +40,7 @@ std::vector<Param> params() {
       {"blocks_per_sm", &isprime_tuning::blocks_per_sm, {4, 8, 16}, P},
       {"mont_impl", &isprime_tuning::mont_impl, {6, 0, 5}, P},
       {"mont_impl_base2", &isprime_tuning::mont_impl_base2, {6, 0, 5}, P},
-      {"base2_window", &isprime_tuning::base2_window, {0, 4}, P},
+      {"base2_window", &isprime_tuning::base2_window, {0, 1, 4}, P},
       {"compact_min", &isprime_tuning::compact_min, {33, 28, 24, 16}, P},
       {"sieve_cutover_log2", &isprime_tuning::sieve_cutover_log2, {32, 28, 24, 20}, P | B},
       {"batch_block", &isprime_tuning::batch_block, {64, 128, 256}, B},

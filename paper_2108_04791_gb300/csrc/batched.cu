@@ -92,12 +92,13 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
     __syncthreads();
     if (tid == 0) s_n1 = n1 - cnt;
     if (mine && v < (1ull << 32) && mr32_is_prime((uint32_t)v)) *reinterpret_cast<uint8_t*>(a) = 1;
-    // base 2 with 4-bit windows, every lane of the warp taking part with the
-    // warp's largest nibble count (lanes without a 64-bit value test a prime)
+    // base 2 with 4-bit windows (x 2^w mod n by a quotient estimate), every
+    // lane of the warp taking part with the warp's largest nibble count
+    // (lanes without a 64-bit value test a prime)
     const bool b2 = mine && v >= (1ull << 32);
     const uint64_t nb = b2 ? v : 0xFFFFFFFFFFFFFFC5ull;
     const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(nb));
-    const bool pass = base2_passes_win<kImplB2>(nb, tab, (int)B, nib) && b2;
+    const bool pass = base2_passes_shift<kImplB2>(nb, nib) && b2;
     smem_push(pass, v, a, q2v, q2a, &s_n2);
     __syncthreads();
   };

@@ -167,6 +167,80 @@ __device__ __forceinline__ bool base2_passes_win(uint64_t n, uint64_t* tab, int 
   return sprp_tail64<kImpl>(M, x, s);
 }
 
+// x 2^w mod n for x < n, 0 <= w <= 15 and odd n >= 2^32, without a
+// Montgomery product: x 2^w - q n with the quotient q = floor(x 2^w / n)
+// estimated in single precision.  n is normalised (N = n << clz(n), top word
+// nt >= 2^31) and x shifted alike (top word xt); then |x/n - xt/nt| < 2^-31,
+// the float quotient adds at most 2^-22 (four roundings of a value <= 1), and
+// after the exact scaling by 2^w one FMA subtracts 1/32 with an error below
+// 2^-9.  So v lies within 2^-6 of t - 1/32 (t = x 2^w / n < 2^15): floor(v) is
+// floor(t) or floor(t) - 1, and v < 0 only when floor(t) = 0 (clamped).  The
+// remainder x 2^w - q n is then in [0, 2n) and one conditional subtraction of
+// n finishes it.  Multiplication by a plain power of two commutes with the
+// Montgomery map, so x may be a Montgomery residue.
+struct Pow2Red {
+  uint32_t sh;  // clz(n) (at most 31)
+  float inv;    // 1 / float(top word of n << sh)
+};
+
+__device__ __forceinline__ Pow2Red pow2red_setup(uint64_t n) {
+  Pow2Red P;
+  P.sh = (uint32_t)__clzll((long long)n);
+  const uint32_t nt = __funnelshift_l((uint32_t)n, (uint32_t)(n >> 32), P.sh);
+  P.inv = __frcp_rn(__uint2float_rn(nt));
+  return P;
+}
+
+__device__ __forceinline__ uint64_t mul_pow2_mod(uint64_t x, uint32_t w, uint64_t n,
+                                                 const Pow2Red& P) {
+  const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+  const uint32_t xt = __funnelshift_l(x0, x1, P.sh);
+  const float p2w = __uint_as_float((127u + w) << 23);  // 2^w, exact
+  const float v = fmaxf(__fmaf_rn(__fmul_rn(__uint2float_rn(xt), P.inv), p2w, -0.03125f), 0.0f);
+  const uint32_t q = __float2uint_rz(v);
+  const uint32_t y0 = x0 << w, y1 = __funnelshift_l(x0, x1, w), y2 = __funnelshift_l(x1, 0u, w);
+  uint32_t r0, r1, d0, d1, d2;
+  asm("{\n\t.reg .u32 pl, ph, sl, sh, r2;\n\t.reg .u64 p, s;\n\t"
+      "mul.wide.u32 p, %5, %6;\n\t"
+      "mul.wide.u32 s, %5, %7;\n\t"
+      "mov.b64 {pl, ph}, p;\n\t"
+      "mov.b64 {sl, sh}, s;\n\t"
+      "add.cc.u32 ph, ph, sl;\n\t"  // q n = (sh : ph : pl)
+      "addc.u32 sh, sh, 0;\n\t"
+      "sub.cc.u32 %0, %8, pl;\n\t"  // r = y - q n, in [0, 2n)
+      "subc.cc.u32 %1, %9, ph;\n\t"
+      "subc.u32 r2, %10, sh;\n\t"
+      "sub.cc.u32 %2, %0, %6;\n\t"  // d = r - n
+      "subc.cc.u32 %3, %1, %7;\n\t"
+      "subc.u32 %4, r2, 0;\n\t"
+      "}"
+      : "=r"(r0), "=r"(r1), "=r"(d0), "=r"(d1), "=r"(d2)
+      : "r"(q), "r"((uint32_t)n), "r"((uint32_t)(n >> 32)), "r"(y0), "r"(y1), "r"(y2));
+  return (int32_t)d2 < 0 ? (((uint64_t)r1 << 32) | r0) : (((uint64_t)d1 << 32) | d0);
+}
+
+// Base 2 with 4-bit windows and no table: per nibble w of d four squarings
+// and x 2^w mod n by mul_pow2_mod.  Same warp-uniform schedule as
+// base2_passes_win (leading zero nibbles square the Montgomery 1).  n >= 2^32.
+template <int kImpl>
+__device__ __forceinline__ bool base2_passes_shift(uint64_t n, int nib_warp) {
+  using Ops = MontOps<kImpl>;
+  const Mont64 M = mont64_setup(n);
+  const Pow2Red P = pow2red_setup(n);
+  uint64_t d = n - 1;
+  const int s = ctz64(d);
+  d >>= s;
+  uint64_t e = nib_warp >= 16 ? d : d << (64 - 4 * nib_warp);  // left-aligned exponent
+  uint64_t x = mul_pow2_mod(M.one, (uint32_t)(e >> 60), n, P);
+  for (int k = 1; k < nib_warp; ++k) {
+    e <<= 4;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) x = Ops::sqr(x, M);
+    x = mul_pow2_mod(x, (uint32_t)(e >> 60), n, P);
+  }
+  return sprp_tail64<kImpl>(M, x, s);
+}
+
 // Number of 4-bit nibbles of the odd part of n - 1.
 __device__ __forceinline__ int base2_nibbles(uint64_t n) {
   uint64_t d = n - 1;

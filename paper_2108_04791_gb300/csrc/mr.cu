@@ -8,9 +8,10 @@
 // Kernels (each a grid-stride loop over a queue whose length is read on the
 // device, so no host synchronisation separates the stages):
 //   mr64_base2_kernel  base 2 for every 64-bit survivor of trial division, by
-//                      4-bit windows over the table 2^w R (or, with
-//                      base2_window 0, binary with a modular doubling for
-//                      "multiply by 2").  Passing elements (the primes and rare
+//                      4-bit windows where "multiply by 2^w" is x 2^w - q n
+//                      with an estimated quotient (base2_window 1), or a
+//                      Montgomery product with the table 2^w R (4), or
+//                      binary with a modular doubling per set bit (0).  Passing elements (the primes and rare
 //                      strong pseudoprimes) are compacted with warp ballots
 //                      into a second queue, so the next kernel runs on dense
 //                      warps of likely primes instead of idling behind
@@ -33,17 +34,20 @@
 
 namespace ip {
 
-// kRest (needs kWindow): 0 compact every survivor into q64b; 1 or 2 a warp
+// kMode: the base-2 schedule (the tuning field base2_window): 0 binary with
+// a modular doubling per set bit, 1 4-bit windows with x 2^w mod n by a
+// quotient estimate, 4 4-bit windows with the table 2^w R in shared memory.
+// kRest (modes 1 and 4): 0 compact every survivor into q64b; 1 or 2 a warp
 // with at least compact_min survivors finishes them itself, with the six
 // remaining bases (1) or the strong Lucas test (2), and compacts nothing.
-template <int kImpl, bool kWindow, int kRest>
+template <int kImpl, int kMode, int kRest>
 __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restrict__ qn,
                                                          const uint32_t* __restrict__ qidx,
                                                          uint32_t* __restrict__ counters,
                                                          uint32_t* __restrict__ q64b,
                                                          uint8_t* __restrict__ out,
                                                          uint32_t compact_min, uint32_t mark) {
-  extern __shared__ uint64_t s_tab[];  // kWindow: 16 x blockDim
+  extern __shared__ uint64_t s_tab[];  // mode 4 or kRest 1: 16 x blockDim
   const uint32_t count = *(volatile uint32_t*)&counters[0];
   const int lane = threadIdx.x & 31;
   // 32-survivor tasks: a warp's first task is fixed (global warp w takes
@@ -63,9 +67,12 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
     uint64_t n = 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 (prime) for lanes past the end
     if (i < count) {
       n = qn[i];
-      if (kWindow) {
+      if (kMode == 4) {
         const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
         pass = base2_passes_win<kImpl>(n, s_tab + threadIdx.x, (int)blockDim.x, nib);
+      } else if (kMode == 1) {
+        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
+        pass = base2_passes_shift<kImpl>(n, nib);
       } else {
         pass = base2_passes<kImpl>(n);
       }
@@ -172,30 +179,42 @@ static unsigned resident_grid(const void* fn, unsigned block, size_t smem, int s
   return want < cap ? want : cap;
 }
 
-template <int kImpl, int kRest>
+// Modes 1 and 4 run one wave of resident blocks (the kernel balances the
+// warps itself); the table of mode 4 and the finishing of kRest 1 take
+// 16 x block words of shared memory.
+template <int kImpl, int kMode, int kRest>
 static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
                              uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s) {
-  const size_t smem = (size_t)16 * block * sizeof(uint64_t);
-  const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, true, kRest>);
+  const size_t smem = (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t) : 0;
+  const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, kMode, kRest>);
   grid = resident_grid(fn, block, smem, sm_count, grid);
-  mr64_base2_kernel<kImpl, true, kRest><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.counters,
-                                                                  q.q64b, out, compact_min, mark);
+  mr64_base2_kernel<kImpl, kMode, kRest><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.counters,
+                                                                   q.q64b, out, compact_min, mark);
+}
+
+template <int kImpl, int kMode>
+static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+                              int lucas, uint32_t compact_min, uint32_t mark, int sm_count,
+                              cudaStream_t s) {
+  if (compact_min > 32)
+    launch_base2_win<kImpl, kMode, 0>(q, out, grid, block, compact_min, mark, sm_count, s);
+  else if (lucas == 1)
+    launch_base2_win<kImpl, kMode, 2>(q, out, grid, block, compact_min, mark, sm_count, s);
+  else
+    launch_base2_win<kImpl, kMode, 1>(q, out, grid, block, compact_min, mark, sm_count, s);
 }
 
 template <int kImpl>
 static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int window,
                          int lucas, uint32_t compact_min, uint32_t mark, int sm_count,
                          cudaStream_t s) {
-  if (window) {
-    if (compact_min > 32)
-      launch_base2_win<kImpl, 0>(q, out, grid, block, compact_min, mark, sm_count, s);
-    else if (lucas == 1)
-      launch_base2_win<kImpl, 2>(q, out, grid, block, compact_min, mark, sm_count, s);
-    else
-      launch_base2_win<kImpl, 1>(q, out, grid, block, compact_min, mark, sm_count, s);
+  if (window == 4) {
+    launch_base2_mode<kImpl, 4>(q, out, grid, block, lucas, compact_min, mark, sm_count, s);
+  } else if (window == 1) {
+    launch_base2_mode<kImpl, 1>(q, out, grid, block, lucas, compact_min, mark, sm_count, s);
   } else {
-    mr64_base2_kernel<kImpl, false, 0><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.counters,
-                                                              q.q64b, out, 33u, mark);
+    mr64_base2_kernel<kImpl, 0, 0><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.counters,
+                                                          q.q64b, out, 33u, mark);
   }
 }
 

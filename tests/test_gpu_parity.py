@@ -218,6 +218,9 @@ def test_tuning_does_not_change_results():
                    dict(mont_impl_base2=3), dict(mont_impl_base2=4), dict(mont_impl_base2=5),
                    dict(td_primes=7), dict(td_primes=11), dict(td_primes=23), dict(td_primes=31),
                    dict(td_primes=40), dict(base2_window=0), dict(base2_window=4, mont_impl_base2=0),
+                   dict(base2_window=4), dict(base2_window=1, mont_impl_base2=0),
+                   dict(base2_window=4, compact_min=8), dict(base2_window=1, compact_min=8),
+                   dict(base2_window=1, compact_min=4, rest_test=1),
                    dict(rest_test=1), dict(rest_test=1, mont_impl=5), dict(rest_test=0),
                    dict(mont_impl=0, td_primes=15), dict(mont_impl=6), dict(mont_impl_base2=6),
                    dict(mont_impl=6, mont_impl_base2=6, base2_window=0),
