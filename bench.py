@@ -215,8 +215,20 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle
 
-def _oracle_rate(vals: np.ndarray, target_s: float = 10.0) -> dict:
-    """Times the CPU oracle (all host cores) on a bounded sample."""
+def _cpu_model() -> str:
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _oracle_rate(vals: np.ndarray, target_s: float = 10.0, single_s: float = 2.0) -> dict:
+    """Times the CPU oracle on bounded samples: all host cores, then one thread."""
     import oracle
     cores = os.cpu_count() or 1
     oracle.isprime_u64(vals[:4096], threads=cores)
@@ -229,9 +241,20 @@ def _oracle_rate(vals: np.ndarray, target_s: float = 10.0) -> dict:
     t0 = time.perf_counter()
     oracle.isprime_u64(sample, threads=cores)
     dt = time.perf_counter() - t0
+    # one thread, on a prefix sized to about single_s seconds
+    t0 = time.perf_counter()
+    oracle.isprime_u64(vals[: 1 << 14], threads=1)
+    rate1 = (1 << 14) / max(time.perf_counter() - t0, 1e-9)
+    n1 = int(min(vals.size, max(1 << 14, rate1 * single_s)))
+    t0 = time.perf_counter()
+    oracle.isprime_u64(vals[:n1], threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {n} elements of the workload, one pass, {cores} threads",
-            "seconds": dt}
+            "seconds": dt, "cpu_model": _cpu_model(),
+            "single_thread": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"first {n1} elements of the workload, one pass",
+                              "seconds": dt1}}
 
 
 def run_reference(args, world, rank):
