@@ -506,6 +506,30 @@ def _spsp_near_2p63(count, seed):
     return out
 
 
+@pytest.mark.parametrize("window", [0, 1, 4])
+def test_base2_schedules_on_every_bit_size(window):
+    """The three base-2 schedules (binary with doublings; 4-bit windows whose
+    step x 2^w mod n uses an estimated quotient; 4-bit windows over a table)
+    on the queue path: random odd values of every size from 33 to 64 bits
+    (normalising shifts 31 down to 0), the primes among them and their odd
+    neighbours, the odd values just above 2^32 and just below 2^64, and
+    base-2 strong pseudoprimes p (2p - 1) near 2^63, which must reach the
+    other bases."""
+    rng = np.random.default_rng(131)
+    cand = np.concatenate([rng.integers(1 << (b - 1), (1 << b) - 1, size=2000, dtype=np.uint64,
+                                        endpoint=True) | np.uint64(1) for b in range(33, 65)])
+    primes = cand[oracle.isprime_u64(cand).astype(bool)]
+    near = primes[primes < np.uint64(2**64 - 2)] + np.uint64(2)
+    edges = np.array(list(range(2**32 + 1, 2**32 + 400, 2)) + list(range(2**64 - 399, 2**64, 2))
+                     + _spsp_near_2p63(16, seed=131), dtype=np.uint64)
+    v = np.concatenate([cand, near, primes - np.uint64(2), edges])
+    want = oracle.isprime_u64(v)
+    assert want.sum() > 2000
+    with ipg.Context(0, sieve_limit=1 << 24) as c:
+        c.set_tuning(base2_window=window, small_max=0)
+        _assert_same(v, _gpu(v, c), want)
+
+
 @pytest.fixture(scope="module")
 def ctx_mr128():
     with ipg.Context(0) as c:
