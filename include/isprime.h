@@ -215,7 +215,7 @@ int isprime_u64_scalar(isprime_ctx *ctx, uint64_t value, uint8_t *result);
 /* Allocation-free variant of isprime_u64 (the paper has no counterpart;
  * this exists for callers that cannot allocate device memory when they need
  * the test -- e.g. code running under an allocator that owns all device
- * memory, or a hook that must not take the driver's allocation lock).
+ * memory, or a hook that must not take the CUDA driver's allocation lock).
  * Same inputs, outputs and results as isprime_u64, but the work queues live
  * in one fixed array of ISPRIME_NOALLOC_SCRATCH_BYTES of device memory that
  * is part of the library image (every GPU that loads the library holds it

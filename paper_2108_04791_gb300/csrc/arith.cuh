@@ -272,7 +272,7 @@ __device__ __forceinline__ uint64_t mont_sqr_c(uint64_t a, uint64_t n, uint64_t 
 // m n + m' n 2^32 keeps it below 2n 2^64, so one extra bit (t4) suffices.
 IP_HD uint64_t mont_reduce_w(uint32_t t0, uint32_t t1, uint64_t H, uint64_t n, uint32_t q) {
   const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
-  // round 1: cancel t0
+  // step 1: cancel t0
   uint32_t m = t0 * q;
   uint64_t acc = (uint64_t)m * n0 + t0;
   acc = (uint64_t)m * n1 + t1 + (acc >> 32);
@@ -280,7 +280,7 @@ IP_HD uint64_t mont_reduce_w(uint32_t t0, uint32_t t1, uint64_t H, uint64_t n, u
   const uint64_t c = acc >> 32;
   H += c;
   uint32_t t4 = H < c;
-  // round 2: cancel t1
+  // step 2: cancel t1
   m = t1 * q;
   acc = (uint64_t)m * n0 + t1;
   acc = (uint64_t)m * n1 + (uint32_t)H + (acc >> 32);

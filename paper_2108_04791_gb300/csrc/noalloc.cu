@@ -3,7 +3,7 @@
 // Some callers cannot allocate device memory at the moment they need a
 // primality test: code running under an allocator that forbids cudaMalloc
 // (a memory pool that owns the whole device), a callback or hook that must
-// not block on the driver's allocation lock, or a process whose device
+// not block on the CUDA driver's allocation lock, or a process whose device
 // memory is fully handed out in advance.  isprime_u64_noalloc serves them:
 // it runs the same kernels as isprime_u64 but keeps its work queues in one
 // fixed array of device memory that is part of the library image (every GPU
