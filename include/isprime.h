@@ -67,8 +67,11 @@ typedef struct {
                               product with PTX word-level reduction, 3 fused product scanning,
                               4 128-bit multiply with fused squaring, 5 128-bit product with
                               squaring as a general multiply, 6 128-bit form in 32-bit words
-                              (PTX, wide products and carry chains, no m0 n0 product; default) */
-  uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..6) */
+                              (PTX, wide products and carry chains, no m0 n0 product; default),
+                              7 formulation 6 with the partial sums carried in the wide
+                              products' 64-bit addends, 8 formulation 7 with squaring as a
+                              general multiply */
+  uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..8) */
   uint32_t batch_block;    /* threads per block of the batched kernel (32..256, multiple of 32; the
                               shared memory of batch_block and batch_tile_log2 must fit a block) */
   uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */

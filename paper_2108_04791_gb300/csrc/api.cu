@@ -99,8 +99,8 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.blocks_per_sm < 1 || t.blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "blocks_per_sm must be in [1, 32]");
   if (t.td_primes > 53) return set_error(ISPRIME_EINVAL, "td_primes must be in [0, 53]");
   if (t.chunk_log2 < 16 || t.chunk_log2 > 28) return set_error(ISPRIME_EINVAL, "chunk_log2 must be in [16, 28]");
-  if (t.mont_impl > 6) return set_error(ISPRIME_EINVAL, "mont_impl must be in [0, 6]");
-  if (t.mont_impl_base2 > 6) return set_error(ISPRIME_EINVAL, "mont_impl_base2 must be in [0, 6]");
+  if (t.mont_impl > 8) return set_error(ISPRIME_EINVAL, "mont_impl must be in [0, 8]");
+  if (t.mont_impl_base2 > 8) return set_error(ISPRIME_EINVAL, "mont_impl_base2 must be in [0, 8]");
   if (bad_block(t.batch_block, 256)) return set_error(ISPRIME_EINVAL, "batch_block must be a multiple of 32 in [32, 256]");
   if (t.batch_tile_log2 < 8 || t.batch_tile_log2 > 14) return set_error(ISPRIME_EINVAL, "batch_tile_log2 must be in [8, 14]");
   if (t.batch_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "batch_blocks_per_sm must be in [0, 32]");

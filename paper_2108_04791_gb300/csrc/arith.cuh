@@ -260,6 +260,102 @@ __device__ __forceinline__ uint64_t mont_sqr_c(uint64_t a, uint64_t n, uint64_t 
 #undef IP_MONT_C_REGS
 #undef IP_MONT_C_TAIL
 #undef IP_MONT_C_OPERANDS
+
+// Formulations 7 and 8: the same product and reduction, with the partial sums
+// folded into the wide products through their 64-bit addend (mad.wide.u32),
+// since every such sum stays below 2^64:
+//   U  = a0 b1 + hi(a0 b0)            V  = a1 b0 + lo(U)
+//   T  = a1 b1 + hi(U) + hi(V)        a b = T 2^64 + lo(V) 2^32 + lo(a0 b0)
+//   V2 = m1 n0 + lo(m0 n1)            W2 = m1 n1 + hi(m0 n1) + hi(V2)
+//   hi64(m n) = W2 + c, c = [lo(V2) > bits 32..63 of a b] (m0 n0 is not formed)
+//   r = T - W2 - c, plus n when negative.
+// Squaring (formulation 7): U = c + hi(a0^2), V = c + lo(U) with c = a0 a1
+// formed once; formulation 8 squares with the multiplication.
+#define IP_MONT_D_REDUCE                                                        \
+  /* m = (t1:t0) n^-1 mod 2^64 */                                               \
+  "mul.wide.u32 w, t0, %8;\n\t"                                                \
+  "mov.b64 {m0, m1}, w;\n\t"                                                   \
+  "mad.lo.u32 m1, t0, %9, m1;\n\t"                                             \
+  "mad.lo.u32 m1, t1, %8, m1;\n\t"                                             \
+  /* V2 = m1 n0 + lo(m0 n1); W2 = m1 n1 + hi(m0 n1) + hi(V2) */                 \
+  "mul.wide.u32 w, m0, %7;\n\t"                                                \
+  "mov.b64 {ql, qh}, w;\n\t"                                                   \
+  "cvt.u64.u32 v2, ql;\n\t"                                                    \
+  "mad.wide.u32 v2, m1, %6, v2;\n\t"                                           \
+  "mov.b64 {v2l, v2h}, v2;\n\t"                                                \
+  "add.cc.u32 sl, qh, v2h;\n\t"                                                \
+  "addc.u32 sh, 0, 0;\n\t"                                                     \
+  "mov.b64 w, {sl, sh};\n\t"                                                   \
+  "mad.wide.u32 w, m1, %7, w;\n\t"                                             \
+  "mov.b64 {x, y}, w;\n\t"                                                     \
+  /* r = T - W2 - c, c the borrow of t1 - lo(V2); + n if negative */            \
+  "mov.b64 {t2, t3}, tt;\n\t"                                                  \
+  "sub.cc.u32 bo, t1, v2l;\n\t"                                                \
+  "subc.cc.u32 %0, t2, x;\n\t"                                                 \
+  "subc.cc.u32 %1, t3, y;\n\t"                                                 \
+  "subc.u32 bo, 0, 0;\n\t"                                                     \
+  "and.b32 x, bo, %6;\n\t"                                                     \
+  "and.b32 y, bo, %7;\n\t"                                                     \
+  "add.cc.u32 %0, %0, x;\n\t"                                                  \
+  "addc.u32 %1, %1, y;\n\t"
+#define IP_MONT_D_REGS                                                          \
+  ".reg .u32 t0, t1, t2, t3, h, ul, uh, vh, m0, m1, ql, qh, v2l, v2h;\n\t"      \
+  ".reg .u32 sl, sh, x, y, bo;\n\t"                                            \
+  ".reg .u64 w, u, v, v2, tt;\n\t"
+
+// Operands as formulation 6: %0 %1 result words; %2 %3 a; %4 %5 b; %6 %7 n;
+// %8 %9 n^-1.
+__device__ __forceinline__ uint64_t mont_mul_d(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+  const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  const uint32_t i0 = (uint32_t)ninv, i1 = (uint32_t)(ninv >> 32);
+  uint32_t r0, r1;
+  asm("{\n\t" IP_MONT_D_REGS
+      "mul.wide.u32 w, %2, %4;\n\t"
+      "mov.b64 {t0, h}, w;\n\t"
+      "cvt.u64.u32 u, h;\n\t"
+      "mad.wide.u32 u, %2, %5, u;\n\t"          // U = a0 b1 + hi(a0 b0)
+      "mov.b64 {ul, uh}, u;\n\t"
+      "cvt.u64.u32 v, ul;\n\t"
+      "mad.wide.u32 v, %3, %4, v;\n\t"          // V = a1 b0 + lo(U)
+      "mov.b64 {t1, vh}, v;\n\t"
+      "add.cc.u32 sl, uh, vh;\n\t"
+      "addc.u32 sh, 0, 0;\n\t"
+      "mov.b64 tt, {sl, sh};\n\t"
+      "mad.wide.u32 tt, %3, %5, tt;\n\t"        // T = a1 b1 + hi(U) + hi(V)
+      IP_MONT_D_REDUCE "}"
+      : "=r"(r0), "=r"(r1)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1), "r"(n0), "r"(n1), "r"(i0), "r"(i1));
+  return ((uint64_t)r1 << 32) | r0;
+}
+
+__device__ __forceinline__ uint64_t mont_sqr_d(uint64_t a, uint64_t n, uint64_t ninv) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  const uint32_t i0 = (uint32_t)ninv, i1 = (uint32_t)(ninv >> 32);
+  uint32_t r0, r1;
+  asm("{\n\t" IP_MONT_D_REGS
+      ".reg .u32 cl, ch;\n\t"
+      "mul.wide.u32 w, %2, %2;\n\t"
+      "mov.b64 {t0, h}, w;\n\t"
+      "mul.wide.u32 w, %2, %3;\n\t"             // c = a0 a1
+      "mov.b64 {cl, ch}, w;\n\t"
+      "add.cc.u32 ul, cl, h;\n\t"               // U = c + hi(a0^2)
+      "addc.u32 uh, ch, 0;\n\t"
+      "add.cc.u32 t1, cl, ul;\n\t"              // V = c + lo(U)
+      "addc.u32 vh, ch, 0;\n\t"
+      "add.cc.u32 sl, uh, vh;\n\t"
+      "addc.u32 sh, 0, 0;\n\t"
+      "mov.b64 tt, {sl, sh};\n\t"
+      "mad.wide.u32 tt, %3, %3, tt;\n\t"        // T = a1^2 + hi(U) + hi(V)
+      IP_MONT_D_REDUCE "}"
+      : "=r"(r0), "=r"(r1)
+      : "r"(a0), "r"(a1), "r"(a0), "r"(a1), "r"(n0), "r"(n1), "r"(i0), "r"(i1));
+  return ((uint64_t)r1 << 32) | r0;
+}
+#undef IP_MONT_D_REDUCE
+#undef IP_MONT_D_REGS
 #endif
 
 // Word-level Montgomery multiplication (Montgomery 1985, two 32-bit words
@@ -418,6 +514,8 @@ IP_HD Mont64 mont64_setup(uint64_t n) {
 //   4: 128-bit multiplication with the fused squaring
 //   5: 128-bit multiplication, squaring as a general multiplication
 //   6: 128-bit form in 32-bit words as PTX, no m0 n0 product (device)
+//   7: formulation 6 with the partial sums in the wide products' addends
+//   8: formulation 7, squaring as a general multiplication
 template <int kImpl>
 struct MontOps;
 
@@ -462,6 +560,26 @@ struct MontOps<6> {
   }
   static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
     return mont_sqr_c(a, M.n, M.ninv);
+  }
+};
+
+template <>
+struct MontOps<7> {
+  static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
+    return mont_mul_d(a, b, M.n, M.ninv);
+  }
+  static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
+    return mont_sqr_d(a, M.n, M.ninv);
+  }
+};
+
+template <>
+struct MontOps<8> {
+  static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
+    return mont_mul_d(a, b, M.n, M.ninv);
+  }
+  static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
+    return mont_mul_d(a, a, M.n, M.ninv);
   }
 };
 

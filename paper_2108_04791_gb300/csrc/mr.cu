@@ -261,6 +261,8 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
     case 4: launch_base2<4>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
     case 5: launch_base2<5>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
     case 6: launch_base2<6>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    case 7: launch_base2<7>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+    case 8: launch_base2<8>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
     default: launch_base2<0>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
   }
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
@@ -272,6 +274,8 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
     case 4: launch_rest<4>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
     case 5: launch_rest<5>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
     case 6: launch_rest<6>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    case 7: launch_rest<7>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+    case 8: launch_rest<8>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
     default: launch_rest<0>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
   }
   if (ctx) st = launch_end(ctx, s, &tl, "mr64_rest_kernel");
