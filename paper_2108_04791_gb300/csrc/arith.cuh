@@ -18,6 +18,13 @@
 #define IP_HD inline
 #include <math.h>
 #endif
+// Loop unrolling hint for functions compiled for both sides: the device pass
+// takes it, the host compiler does not see it.
+#if defined(__CUDA_ARCH__)
+#define IP_UNROLL _Pragma("unroll")
+#else
+#define IP_UNROLL
+#endif
 
 namespace ip {
 
@@ -139,27 +146,28 @@ __device__ __forceinline__ uint64_t mont_mul_p(uint64_t a, uint64_t b, uint64_t 
   const uint64_t lo = a * b;
   const uint64_t hi = __umul64hi(a, b);
   uint32_t t0 = (uint32_t)lo, t1 = (uint32_t)(lo >> 32), t2 = (uint32_t)hi, t3 = (uint32_t)(hi >> 32);
-  uint32_t t4, m;
+  uint32_t t4;
   const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
-  asm("mul.lo.u32      %5, %0, %8;\n\t"
-      "mad.lo.cc.u32   %0, %5, %6, %0;\n\t"
-      "madc.lo.cc.u32  %1, %5, %7, %1;\n\t"
+  asm("{\n\t.reg .u32 mm;\n\t"
+      "mul.lo.u32      mm, %0, %7;\n\t"
+      "mad.lo.cc.u32   %0, mm, %5, %0;\n\t"
+      "madc.lo.cc.u32  %1, mm, %6, %1;\n\t"
       "addc.cc.u32     %2, %2, 0;\n\t"
       "addc.cc.u32     %3, %3, 0;\n\t"
       "addc.u32        %4, 0, 0;\n\t"
-      "mad.hi.cc.u32   %1, %5, %6, %1;\n\t"
-      "madc.hi.cc.u32  %2, %5, %7, %2;\n\t"
+      "mad.hi.cc.u32   %1, mm, %5, %1;\n\t"
+      "madc.hi.cc.u32  %2, mm, %6, %2;\n\t"
       "addc.cc.u32     %3, %3, 0;\n\t"
       "addc.u32        %4, %4, 0;\n\t"
-      "mul.lo.u32      %5, %1, %8;\n\t"
-      "mad.lo.cc.u32   %1, %5, %6, %1;\n\t"
-      "madc.lo.cc.u32  %2, %5, %7, %2;\n\t"
+      "mul.lo.u32      mm, %1, %7;\n\t"
+      "mad.lo.cc.u32   %1, mm, %5, %1;\n\t"
+      "madc.lo.cc.u32  %2, mm, %6, %2;\n\t"
       "addc.cc.u32     %3, %3, 0;\n\t"
       "addc.u32        %4, %4, 0;\n\t"
-      "mad.hi.cc.u32   %2, %5, %6, %2;\n\t"
-      "madc.hi.cc.u32  %3, %5, %7, %3;\n\t"
-      "addc.u32        %4, %4, 0;"
-      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "=r"(t4), "=r"(m)
+      "mad.hi.cc.u32   %2, mm, %5, %2;\n\t"
+      "madc.hi.cc.u32  %3, mm, %6, %3;\n\t"
+      "addc.u32        %4, %4, 0;\n\t}"
+      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "=r"(t4)
       : "r"(n0), "r"(n1), "r"(q));
   const uint64_t r = ((uint64_t)t3 << 32) | t2;
   return (t4 != 0 || r >= n) ? r - n : r;
@@ -599,7 +607,7 @@ struct MontOps<2> {
 template <int kImpl = 0>
 IP_HD uint64_t mont64_r2(const Mont64& M) {
   uint64_t x = M.one;
-#pragma unroll
+  IP_UNROLL
   for (int i = 0; i < 8; ++i) x = mod_dbl(x, M.n);
   x = MontOps<kImpl>::sqr(x, M);
   x = MontOps<kImpl>::sqr(x, M);
@@ -619,7 +627,7 @@ IP_HD bool sprp2_64(const Mont64& M, uint64_t d, int s) {
   uint64_t e = d << (64 - 4 * nib);          // exponent bits left-aligned
   uint64_t x = M.one;
   for (int k = 0; k < nib; ++k) {
-#pragma unroll
+    IP_UNROLL
     for (int j = 0; j < 4; ++j) {
       x = MontOps<kImpl>::sqr(x, M);
       const uint64_t y = mod_dbl(x, n);

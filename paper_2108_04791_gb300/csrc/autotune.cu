@@ -24,9 +24,11 @@ namespace ip {
 
 namespace {
 
+using FieldPtr = uint32_t isprime_tuning::*;
+
 struct Param {
   const char* name;
-  uint32_t isprime_tuning::*field;
+  FieldPtr field;
   std::vector<uint32_t> values;
   int modes;  // bit ISPRIME_TUNE_PLAIN and/or ISPRIME_TUNE_BATCHED
 };
@@ -66,7 +68,7 @@ const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_prim
                          "mont_impl", "mont_impl_base2", "batch_block", "batch_tile_log2",
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
                          "compact_min", "sieve_cutover_log2", "serve_short_max"};
-uint32_t isprime_tuning::*kFieldPtr[] = {
+FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
     &isprime_tuning::mont_impl_base2, &isprime_tuning::batch_block,

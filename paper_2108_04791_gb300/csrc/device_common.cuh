@@ -47,17 +47,19 @@ __device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
                   : (int)((__ldg(a.sieve + (n >> 6)) >> ((uint32_t)(n >> 1) & 31u)) & 1u);
   bool hit = false, equal = false;
   const uint32_t ntd = kNtd >= 0 ? (uint32_t)kNtd : a.ntd;
-  if (n < (1ull << 32)) {
-    const uint32_t v = (uint32_t)n;
+  if constexpr (kNtd != 0) {
+    if (n < (1ull << 32)) {
+      const uint32_t v = (uint32_t)n;
 #pragma unroll
-    for (uint32_t i = 0; i < (kNtd >= 0 ? (uint32_t)kNtd : ntd); ++i) {
-      hit |= v * c_td.inv32[i] <= c_td.lim32[i];
-      equal |= v == c_td.p[i];
+      for (uint32_t i = 0; i < (kNtd >= 0 ? (uint32_t)kNtd : ntd); ++i) {
+        hit |= v * c_td.inv32[i] <= c_td.lim32[i];
+        equal |= v == c_td.p[i];
+      }
+    } else {
+#pragma unroll
+      for (uint32_t i = 0; i < (kNtd >= 0 ? (uint32_t)kNtd : ntd); ++i)
+        hit |= n * c_td.inv64[i] <= c_td.lim64[i];
     }
-  } else {
-#pragma unroll
-    for (uint32_t i = 0; i < (kNtd >= 0 ? (uint32_t)kNtd : ntd); ++i)
-      hit |= n * c_td.inv64[i] <= c_td.lim64[i];
   }
   if (equal) return kPrime;
   if (hit) return kComposite;
