@@ -69,7 +69,7 @@ SM_MAX_MHZ = 2070.0
 # the kernel sources whose hash is recorded and the tuning of the capture, and
 # are reported as null otherwise.
 NCU_TRAFFIC = {
-    "sources": "52e68c1cbfb871a0",
+    "sources": "0f5699efa3b82eb3",
     "tuning": {"classify_block": 256, "mr_block": 256, "blocks_per_sm": 16, "td_primes": 15,
                "chunk_log2": 24, "mont_impl": 6, "mont_impl_base2": 6, "batch_block": 128,
                "batch_tile_log2": 10, "batch_blocks_per_sm": 0, "base2_window": 1, "rest_test": 0,

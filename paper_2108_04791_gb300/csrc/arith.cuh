@@ -118,10 +118,6 @@ IP_HD uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) {
   return (hi < mh) ? r + n : r;
 }
 
-IP_HD uint64_t mont_sqr(uint64_t a, uint64_t n, uint64_t ninv) {
-  return mont_mul(a, a, n, ninv);
-}
-
 // Squaring in the same 128-bit form with the cross product computed once:
 // a^2 = a0^2 + 2 a0 a1 2^32 + a1^2 2^64 (three wide products instead of
 // four); the REDC is the one of mont_mul.
