@@ -236,6 +236,38 @@ int isprime_u64_noalloc(const uint64_t *d_in, uint8_t *d_out, size_t n, isprime_
  * from the resident bitmap (pi(S); 0 when S == 0).  Synchronous. */
 int isprime_sieve_count(isprime_ctx *ctx, uint64_t *out);
 
+/* ------------------------------------------- sharding a job across devices */
+/* Every element is independent (Sec. 1: element i of the result depends on
+ * N[i] alone), so one job splits across devices with no exchange of data
+ * between them.  These helpers decide which device takes which part; each
+ * device then runs the plain, batched or served entry points on its part with
+ * its own context.  Host only: no device is touched, no context is needed. */
+
+/* Contiguous split of n elements into n_shards ranges whose sizes differ by
+ * at most one (the first n mod n_shards ranges take one more): shard s takes
+ * [begin[s], begin[s+1]).  begin: caller-owned, n_shards + 1 entries.
+ * n_shards == 0 or begin == NULL: ISPRIME_EINVAL. */
+int isprime_plan_contiguous(uint64_t n, uint32_t n_shards, uint64_t *begin);
+
+/* Whole arrays of a batch, sizes[i] elements each, to n_shards by
+ * longest-processing-time first: arrays in decreasing size (equal sizes in
+ * index order), each to the shard with the least total so far (ties to the
+ * lower shard index).  Every shard's total is at most the mean total plus the
+ * largest array, and the largest total at most 4/3 of the best possible.
+ * owner[i] receives the shard of array i; load[s] (nullable, n_shards
+ * entries) the elements of shard s.  Caller-owned arrays.  n_arrays == 0
+ * only fills load with zeros.  NULL sizes or owner with n_arrays > 0, or
+ * n_shards == 0: ISPRIME_EINVAL. */
+int isprime_plan_batched(const uint64_t *sizes, size_t n_arrays, uint32_t n_shards,
+                         uint32_t *owner, uint64_t *load);
+
+/* Served requests across devices: *device receives the index of the device
+ * with the least outstanding work (outstanding[d]: elements admitted to
+ * device d and not yet finished), ties to the lower index.  n_devices == 0 or
+ * a NULL pointer: ISPRIME_EINVAL. */
+int isprime_route_least_loaded(const uint64_t *outstanding, uint32_t n_devices,
+                               uint32_t *device);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A continuous-batching server on one context.  Requests (host arrays) are

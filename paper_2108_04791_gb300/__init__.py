@@ -20,7 +20,8 @@ import numpy as np
 from . import _build
 
 __all__ = ["build", "lib", "isprime", "isprime_host", "isprime_scalar", "Context", "Server", "Tuning",
-           "IsPrimeError", "int_rates", "KERNEL_NAMES"]
+           "IsPrimeError", "int_rates", "KERNEL_NAMES", "plan_contiguous", "plan_batched",
+           "route_least_loaded"]
 
 _lock = threading.Lock()
 _lib = None
@@ -125,6 +126,10 @@ def lib():
                 "isprime_timing_read": ([vp, ctypes.POINTER(_KTime), i32], i32),
                 "isprime_timing_reset": ([vp], i32),
                 "isprime_measure_int_rates": ([i32, ctypes.POINTER(_IntRates)], i32),
+                "isprime_plan_contiguous": ([u64, ctypes.c_uint32, vp], i32),
+                "isprime_plan_batched": ([vp, sz, ctypes.c_uint32, vp, vp], i32),
+                "isprime_route_least_loaded": ([vp, ctypes.c_uint32,
+                                                ctypes.POINTER(ctypes.c_uint32)], i32),
                 "isprime_strerror": ([i32], ctypes.c_char_p),
                 "isprime_last_error": ([], ctypes.c_char_p),
                 "isprime_version": ([], i32),
@@ -427,3 +432,35 @@ def int_rates(device: int = 0) -> dict:
     for i, nm in enumerate(names):
         out["mont_" + nm] = r.mont_variant[i]
     return out
+
+
+# ------------------------------------------------ sharding a job across devices
+# Host-only planning (no device is touched): which device takes which part.
+
+def plan_contiguous(n: int, n_shards: int) -> np.ndarray:
+    """Boundaries of n_shards contiguous ranges of n elements (sizes differ by
+    at most one): shard s takes [begin[s], begin[s+1])."""
+    begin = np.zeros(n_shards + 1 if n_shards > 0 else 1, dtype=np.uint64)
+    _check(lib().isprime_plan_contiguous(n, n_shards, begin.ctypes.data))
+    return begin
+
+
+def plan_batched(sizes, n_shards: int) -> tuple[np.ndarray, np.ndarray]:
+    """Whole arrays to n_shards, longest first to the least-loaded shard.
+    Returns (owner per array, elements per shard)."""
+    sizes = np.ascontiguousarray(sizes, dtype=np.uint64)
+    owner = np.zeros(sizes.size, dtype=np.uint32)
+    load = np.zeros(max(n_shards, 1), dtype=np.uint64)
+    _check(lib().isprime_plan_batched(sizes.ctypes.data if sizes.size else None, sizes.size,
+                                      n_shards, owner.ctypes.data if sizes.size else None,
+                                      load.ctypes.data))
+    return owner, load
+
+
+def route_least_loaded(outstanding) -> int:
+    """The device with the least outstanding work (ties to the lower index)."""
+    o = np.ascontiguousarray(outstanding, dtype=np.uint64)
+    d = ctypes.c_uint32(0)
+    _check(lib().isprime_route_least_loaded(o.ctypes.data if o.size else None, o.size,
+                                            ctypes.byref(d)))
+    return int(d.value)
