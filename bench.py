@@ -64,10 +64,10 @@ IMAD_PER_SM_PER_CLK = 64                           # 32-bit IMAD issue rate per 
 SM_COUNT_GB300 = 152
 SM_MAX_MHZ = 2070.0
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of this workload (profiles/*__plain_large_2p24.md); they hold for
-# the kernel sources whose hash is recorded and the tuning of the capture, and
-# are reported as null otherwise.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu capture of this workload whose kernel-source hash and tuning are
+# recorded here; they hold for that build only and are reported as null for
+# any other.
 NCU_TRAFFIC = {
     "sources": "0f5699efa3b82eb3",
     "tuning": {"classify_block": 256, "mr_block": 256, "blocks_per_sm": 16, "td_primes": 15,
@@ -105,6 +105,8 @@ def _parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-probe", action="store_true", help="skip the integer-rate probe")
+    p.add_argument("--no-sub", action="store_true",
+                   help="skip the batched and served sub-records of the default run")
     p.add_argument("--tune", default="", help="tuning overrides, e.g. mont_impl=1,td_primes=24")
     return p.parse_args()
 
@@ -127,6 +129,15 @@ def _workload(name: str, rank: int) -> tuple[np.ndarray, str]:
     n = 1 << 26
     return wg.plain_mixed(n, seed=2, offset=rank * n), \
         "2^26 uint64, bit length uniform in 2..64, seed 2"
+
+
+def _config(workload: str, n: int, desc: str, world: int) -> dict:
+    """The workload's config: the same dict in both arms of the benchmark."""
+    l2 = ("input 128 MiB > L2 (126 MB); the GPU arm also writes a 256 MiB buffer "
+          "between steps to flush L2" if workload == "plain_large" else
+          "the GPU arm writes a 256 MiB buffer between steps to flush L2")
+    return {"workload": workload, "elements": n, "description": desc, "l2": l2,
+            "parallelism": f"dp{world} (independent shards)"}
 
 
 # ---------------------------------------------------------------- distributed
@@ -286,8 +297,8 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "elements_per_step": per_step,
-                       "description": desc},
+            "config": _config(args.workload, int(vals.size), desc, world),
+            "sample_elements_per_step": per_step,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} consecutive elements of the workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -342,7 +353,7 @@ def run_mine(args, world, rank, local):
     value = n * world * args.steps / total_s
     ktimes = ctx.timing_read()
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline: the whole step, and the dominant kernel
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     dom_ms, dom_launches = ktimes[dom]
     roof = None
@@ -358,25 +369,33 @@ def run_mine(args, world, rank, local):
             "mr64_rest": w["rest_squarings"] * IMAD_SLOTS_PER_SQUARING
             + w["rest_multiplies"] * IMAD_SLOTS_PER_MULMOD,
         }
+        same = (NCU_TRAFFIC["sources"] == kernel_sources_hash()
+                and NCU_TRAFFIC["tuning"] == ctx.tuning.as_dict())
+        per_kernel = {k: slots[k] * n / (ktimes[k][0] / ktimes[k][1] / 1e3) / peak_ops
+                      for k in slots if ktimes.get(k, (0, 0))[1]}
+        step_slots = sum(slots.values())
+        step_achieved = (n * world * args.steps / total_s) / world * step_slots
+        dom_roof = None
         if dom in slots:
-            per_launch = slots[dom] * n
-            achieved = per_launch / (dom_ms / dom_launches / 1e3)
-            same = (NCU_TRAFFIC["sources"] == kernel_sources_hash()
-                    and NCU_TRAFFIC["tuning"] == ctx.tuning.as_dict())
-            traffic = NCU_TRAFFIC.get(dom) if same else None
-            per_kernel = {k: slots[k] * n / (ktimes[k][0] / ktimes[k][1] / 1e3) / peak_ops
-                          for k in slots if ktimes.get(k, (0, 0))[1]}
-            step_slots = sum(slots.values())
-            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                    "unit": "T int-mul slots/s", "frac": achieved / peak_ops, "traffic": traffic,
-                    "kernel": dom, "kernel_ms_per_launch": dom_ms / dom_launches,
-                    "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived; the probe measures "
-                                   "64 mad.lo.u32 lanes/clk/SM)",
-                    "algorithmic_slots_per_element": slots[dom],
-                    "frac_by_kernel": per_kernel,
-                    "step": {"slots_per_element": step_slots,
-                             "roofline_tests_per_s": peak_ops / step_slots,
-                             "frac": (n * world * args.steps / total_s) / world / (peak_ops / step_slots)}}
+            dom_achieved = slots[dom] * n / (dom_ms / dom_launches / 1e3)
+            dom_roof = {"kernel": dom, "achieved": dom_achieved / 1e12, "frac": dom_achieved / peak_ops,
+                        "ms_per_launch": dom_ms / dom_launches,
+                        "algorithmic_slots_per_element": slots[dom],
+                        "traffic": NCU_TRAFFIC.get(dom) if same else None}
+        traffic = (sum(NCU_TRAFFIC[k] for k in slots) if same else None)
+        roof = {"bound": "alu", "achieved": step_achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "T int-mul slots/s", "frac": step_achieved / peak_ops, "traffic": traffic,
+                "kernel": "whole step: classify_u64 + mr64_base2 + mr64_rest (one launch each)",
+                "frac_dominant_kernel": dom_roof["frac"] if dom_roof else None,
+                "dominant_kernel": dom_roof,
+                "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived; the probe measures "
+                               "64 mad.lo.u32 lanes/clk/SM)",
+                "algorithmic_slots_per_element": step_slots,
+                "roofline_tests_per_s": peak_ops / step_slots,
+                "frac_by_kernel": per_kernel,
+                "traffic_note": "DRAM bytes per step (sum of the three kernels) from the ncu "
+                                "capture whose source hash and tuning match this build; "
+                                "null otherwise"}
     kernels = {k: {"ms_per_step": v[0] / max(args.steps, 1), "launches": v[1]}
                for k, v in ktimes.items() if v[1]}
 
@@ -404,44 +423,83 @@ def run_mine(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = _oracle_rate(vals)
 
+    # ---- the batched and served forms on this GPU (bounded sub-records)
+    subs = {}
+    if args.workload == "plain_large" and world == 1 and not args.no_sub:
+        with_cpu = rank == 0 and not args.no_cpu_baseline
+        subs["batched"] = batched_record(ctx, dev, max(3, min(args.steps, 10)), 3, world, with_cpu)
+        subs["served"] = served_record(ctx, dev, 3, world, rank, with_cpu)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "elements": n, "description": desc,
-                       "l2": "input 128 MiB > L2, plus a 256 MiB L2 flush between steps",
-                       "parallelism": f"dp{world} (independent shards)"},
+            "config": _config(args.workload, n, desc, world),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "kernels": kernels,
             "tuning": ctx.tuning.as_dict(),
-            "wall_s_timed_region": wall, "int_rates": imad_rate,
+            "wall_s_timed_region": wall, "int_rates": imad_rate, **subs,
         }
         print(json.dumps(line), flush=True)
 
 
-def run_batched(args, world, rank, local):
-    """4096 ragged arrays (log-uniform sizes 1..2^20, 25% primes near 2^64,
-    10% semiprimes) classified by one batched launch per step, against the
-    same arrays through one plain call each."""
-    import torch
-    import paper_2108_04791_gb300 as ipg
+def _golden_work(name: str) -> dict:
+    """Per-element algorithmic work of a workload, counted once by the CPU
+    oracle's work counter (tests/golden/make_work_counts.py wrote the file)."""
+    with open(os.path.join(ROOT, "tests", "golden", "work_counts.json")) as f:
+        return json.load(f)[name]
 
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
+
+def _slots_per_element(w: dict) -> float:
+    """Integer-pipe slots per element of the canonical schedule: trial
+    division, base-2 squarings, and the six bases' squarings and products."""
+    return (w["trial_tests"] * IMAD_SLOTS_PER_TRIAL_TEST
+            + (w["base2_squarings"] + w["rest_squarings"]) * IMAD_SLOTS_PER_SQUARING
+            + w["rest_multiplies"] * IMAD_SLOTS_PER_MULMOD)
+
+
+def _alu_roofline(tests_per_s: float, work_name: str, note: str) -> dict:
+    peak_ops = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6
+    g = _golden_work(work_name)
+    slots = _slots_per_element(g["per_element"])
+    achieved = tests_per_s * slots
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+            "unit": "T int-mul slots/s", "frac": achieved / peak_ops, "traffic": None,
+            "algorithmic_slots_per_element": slots, "roofline_tests_per_s": peak_ops / slots,
+            "work_source": f"oracle work counter over {g['elements']} elements ({work_name})",
+            "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived)", "note": note}
+
+
+def _cpu_rate_on(vals: np.ndarray, target_s: float, what: str) -> dict:
+    """The CPU oracle on all host cores over a bounded prefix of `vals`."""
+    import oracle
+    cores = os.cpu_count() or 1
+    cal = vals[: 1 << 16]
+    t0 = time.perf_counter()
+    oracle.isprime_u64(cal, threads=cores)
+    rate = cal.size / max(time.perf_counter() - t0, 1e-9)
+    n = int(min(vals.size, max(1 << 16, rate * target_s)))
+    t0 = time.perf_counter()
+    oracle.isprime_u64(vals[:n], threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} values of {what}, one pass, {cores} threads", "seconds": dt}
+
+
+def batched_record(ctx, dev, steps: int, warm: int, world: int, with_cpu: bool) -> dict:
+    """The batched workload (4096 ragged arrays, log-uniform sizes 1..2^20,
+    25% primes near 2^64, 10% semiprimes) through one batched launch per step,
+    against the same arrays through one plain call each."""
+    import torch
     from workloads import torch_gen
-    d_all, offs = torch_gen.batched_arrays(n_arrays=4096, max_size=1 << 20, seed=3 + 1000 * rank,
-                                           device=dev)
+    d_all, offs = torch_gen.batched_arrays(n_arrays=4096, max_size=1 << 20, seed=3, device=dev)
     n = d_all.numel()
     out_all = torch.empty(n, dtype=torch.uint8, device=dev)
     ins = [d_all[offs[i]:offs[i + 1]] for i in range(len(offs) - 1)]
     outs = [out_all[offs[i]:offs[i + 1]] for i in range(len(offs) - 1)]
-    ctx = ipg.Context.default(local)
-    if args.tune:
-        ctx.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
     stream = torch.cuda.current_stream(dev)
-    steps, warm = max(args.steps, 1), max(args.warmup, 3)
 
     def timed(fn, k):
         for _ in range(warm):
@@ -460,48 +518,53 @@ def run_batched(args, world, rank, local):
     launches0 = ctx.stats()["kernel_launches"]
     ctx.timing_reset()
     ctx.timing(True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     t_batch = timed(lambda: ctx.isprime_batched(ins, outs), steps)
     clk = clocks.stop()
     ctx.timing(False)
     launches = ctx.stats()["kernel_launches"] - launches0
     kt = ctx.timing_read()
-    k_plain = max(1, min(steps, 3))
+    k_plain = max(1, min(steps, 2))
     t_plain = timed(lambda: [ctx.isprime(x, out=o) for x, o in zip(ins, outs)], k_plain)
     value = n * world * steps / t_batch
     plain_value = n * world * k_plain / t_plain
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
-            "warmup": warm, "ms_per_step": 1e3 * t_batch / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "batched", "arrays": len(ins), "elements": int(n),
-                       "description": wg.WORKLOADS["batched"], "launch": "one CUDA-graph replay per step"},
-            "plain_per_call": {"value": plain_value, "unit": UNIT, "steps": k_plain,
-                               "calls_per_step": len(ins)},
-            "speedup_vs_plain_calls": value / plain_value,
-            "gpu_launches": launches, "clocks": clk,
-            "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]} for k, v in kt.items() if v[1]},
-            "tuning": ctx.tuning.as_dict(),
-        }
-        print(json.dumps(line), flush=True)
+    roof = _alu_roofline(value / world, "batched",
+                         "whole launch (the batched kernel runs every stage); per-element work "
+                         "of this exact batch")
+    rec = {"value": value, "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * t_batch / steps,
+           "config": {"workload": "batched", "arrays": len(ins), "elements": int(n),
+                      "description": wg.WORKLOADS["batched"],
+                      "launch": "one CUDA-graph replay per step",
+                      "l2": "2.3 GB of input per step > L2"},
+           "plain_per_call": {"value": plain_value, "unit": UNIT, "steps": k_plain,
+                              "calls_per_step": len(ins)},
+           "speedup_vs_plain_calls": value / plain_value,
+           "roofline": roof, "gpu_launches": launches, "clocks": clk,
+           "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]} for k, v in kt.items()
+                       if v[1]}}
+    if with_cpu:
+        rec["cpu_baseline"] = _cpu_rate_on(d_all[: 1 << 24].cpu().numpy().view(np.uint64), 4.0,
+                                           "the batch (arrays in order)")
+    del d_all, out_all, ins, outs
+    return rec
 
 
-def run_served(args, world, rank, local):
-    """20,000 requests with exponential inter-arrival times (mean 200 us),
-    log-uniform sizes 1..2^22 and values drawn as in the batched workload,
-    submitted at their arrival times to the continuous-batching server
-    (8 GB device budget).  Request inputs are slices of a 2^27-value pool
-    with that distribution, in pinned host memory; outputs go to a pinned
-    ring larger than the server can hold in flight."""
+def served_record(ctx, dev, warm: int, world: int, rank: int, with_cpu: bool,
+                  n_requests: int = 20_000) -> dict:
+    """The served workload: requests with exponential inter-arrival times
+    (mean 200 us), log-uniform sizes 1..2^22, values drawn as in the batched
+    workload, through the continuous-batching server (8 GB device budget).
+    Request inputs are slices of a 2^27-value pool with that distribution in
+    pinned host memory; outputs go to a pinned ring larger than the server can
+    hold in flight.  Three runs over the same request stream: open loop at the
+    arrival times (latency at 5,000 req/s), all requests offered at once
+    (capacity), and one isprime_u64_host call per request, one after another
+    (the per-call plain form)."""
     import torch
     import paper_2108_04791_gb300 as ipg
     from workloads import torch_gen
-
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
-    arrivals, sizes, _ = wg.served_requests(n_requests=20_000, max_size=1 << 22,
+    arrivals, sizes, _ = wg.served_requests(n_requests=n_requests, max_size=1 << 22,
                                             rate_per_s=5000.0, seed=4 + 1000 * rank, values=False)
     pool_n = 1 << 27
     pool = torch_gen.served_values(pool_n, seed=4 + 1000 * rank, device=dev).cpu().pin_memory()
@@ -512,53 +575,118 @@ def run_served(args, world, rank, local):
     np.cumsum(sizes[:-1], out=starts[1:])
     in_off = starts % (pool_n - (1 << 22))
     out_off = starts % (ring_n - (1 << 22))
+    total = int(sizes.sum())
+    srv = ipg.Server(ctx, mem_budget_bytes=8 << 30, n_slots=4)
+    for _ in range(max(warm, 3)):  # graph recording, first touch of the arena
+        srv.wait(srv.submit(pool_np[:1 << 20], out=ring[:1 << 20]))
+
+    def run(paced: bool):
+        srv.reset_stats()
+        _barrier(world)
+        t0 = time.perf_counter()
+        tickets = []
+        for i in range(len(sizes)):
+            if paced:
+                target = t0 + arrivals[i]
+                while True:
+                    now = time.perf_counter()
+                    if now >= target:
+                        break
+                    if target - now > 2e-3:
+                        time.sleep(target - now - 1e-3)
+            a, o, m = int(in_off[i]), int(out_off[i]), int(sizes[i])
+            tickets.append(srv.submit(pool_np[a:a + m], out=ring[o:o + m]))
+        for t in tickets:
+            srv.wait(t)
+        return time.perf_counter() - t0, srv.stats()
+
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    wall_open, st_open = run(paced=True)
+    wall_cap, st_cap = run(paced=False)
+    clk = clocks.stop()
+    srv.close()
+    # per-call plain form on the same stream: one host-buffer call per request
+    L = ipg.lib()
+    s = ipg.ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    for i in range(3):
+        ipg._check(L.isprime_u64_host(ctx.handle, pool_np[:1 << 20].ctypes.data,
+                                      ring[:1 << 20].ctypes.data, 1 << 20, s))
+    _barrier(world)
+    t0 = time.perf_counter()
+    for i in range(len(sizes)):
+        a, o, m = int(in_off[i]), int(out_off[i]), int(sizes[i])
+        ipg._check(L.isprime_u64_host(ctx.handle, pool_np[a:].ctypes.data, ring[o:].ctypes.data,
+                                      m, s))
+    t_plain = _max_over_ranks(time.perf_counter() - t0, world, dev)
+    cap = total / st_cap["span_s"]
+    rec = {"value": cap * world, "unit": UNIT,
+           "config": {"workload": "served", "requests": len(sizes), "elements": total,
+                      "rate_req_per_s": 5000, "budget_bytes": 8 << 30, "slots": 4,
+                      "description": wg.WORKLOADS["served"],
+                      "inputs": "slices of a 2^27-value pool in pinned host memory"},
+           "capacity": {"value": cap * world, "unit": UNIT, "span_s": st_cap["span_s"],
+                        "how": "all requests submitted at once, in arrival order",
+                        "p50_ms": st_cap["p50_ms"], "p99_ms": st_cap["p99_ms"],
+                        "batches": st_cap["batches"]},
+           "open_loop": {"tests_per_s": st_open["tests_per_s"], "p50_ms": st_open["p50_ms"],
+                         "p99_ms": st_open["p99_ms"], "mean_ms": st_open["mean_ms"],
+                         "max_ms": st_open["max_ms"], "batches": st_open["batches"],
+                         "short_requests": st_open["short_requests"],
+                         "p50_short_ms": st_open["p50_short_ms"],
+                         "p99_short_ms": st_open["p99_short_ms"],
+                         "p50_long_ms": st_open["p50_long_ms"], "p99_long_ms": st_open["p99_long_ms"],
+                         "offered_tests_per_s": float(total / arrivals[-1]), "wall_s": wall_open},
+           "plain_per_call": {"value": total * world / t_plain, "unit": UNIT, "seconds": t_plain,
+                              "how": "one isprime_u64_host call per request, in order"},
+           "capacity_vs_plain_calls": cap * world / (total * world / t_plain),
+           "roofline": _alu_roofline(cap, "served_pool",
+                                     "capacity run; per-element work of the 2^27-value pool the "
+                                     "requests are sliced from (the stream covers it about 40 "
+                                     "times); copies in and out are inside the span"),
+           "e2e": {"value": cap * world, "unit": UNIT, "h2d_bytes_per_step": 8 * total,
+                   "d2h_bytes_per_step": total, "step": "the whole request stream"},
+           "clocks": clk}
+    if with_cpu:
+        rec["cpu_baseline"] = _cpu_rate_on(pool_np, 4.0, "the request pool")
+    del pool, ring
+    return rec
+
+
+def run_batched(args, world, rank, local):
+    import torch
+    import paper_2108_04791_gb300 as ipg
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
     ctx = ipg.Context.default(local)
     _apply_tune(ctx, args)
-    srv = ipg.Server(ctx, mem_budget_bytes=8 << 30, n_slots=4)
-    # warm-up requests (graph recording, first-touch of the arena)
-    for i in range(max(args.warmup, 3)):
-        srv.wait(srv.submit(pool_np[:1 << 20], out=ring[:1 << 20]))
-    srv.reset_stats()
-    _barrier(world)
-    clocks = ClockSampler(local)
-    clocks.start()
-    t0 = time.perf_counter()
-    tickets = []
-    for i in range(len(sizes)):
-        target = t0 + arrivals[i]
-        while True:
-            now = time.perf_counter()
-            if now >= target:
-                break
-            if target - now > 2e-3:
-                time.sleep(target - now - 1e-3)
-        a, o, n = int(in_off[i]), int(out_off[i]), int(sizes[i])
-        tickets.append(srv.submit(pool_np[a:a + n], out=ring[o:o + n]))
-    for t in tickets:
-        srv.wait(t)
-    wall = time.perf_counter() - t0
-    clk = clocks.stop()
-    st = srv.stats()
-    srv.close()
-    value = _max_over_ranks(st["tests_per_s"], world, dev) if world == 1 else st["tests_per_s"] * world
+    rec = batched_record(ctx, dev, max(args.steps, 1), max(args.warmup, 3), world,
+                         with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": len(sizes), "warmup": max(args.warmup, 3),
-            "ms_per_step": 1e3 * st["span_s"] / len(sizes), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "served", "requests": len(sizes), "elements": int(sizes.sum()),
-                       "rate_req_per_s": 5000, "budget_bytes": 8 << 30, "slots": 4,
-                       "description": wg.WORKLOADS["served"]},
-            "serve": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-                      "max_ms": st["max_ms"], "batches": st["batches"], "span_s": st["span_s"],
-                      "short_requests": st["short_requests"],
-                      "short_max_elements": ctx.tuning.serve_short_max,
-                      "p50_short_ms": st["p50_short_ms"], "p99_short_ms": st["p99_short_ms"],
-                      "p50_long_ms": st["p50_long_ms"], "p99_long_ms": st["p99_long_ms"],
-                      "offered_tests_per_s": float(sizes.sum() / arrivals[-1]), "wall_s": wall},
-            "clocks": clk,
-        }
+        line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world,
+                "steps": rec["steps"], "warmup": max(args.warmup, 3),
+                "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic", **rec,
+                "tuning": ctx.tuning.as_dict()}
+        print(json.dumps(line), flush=True)
+
+
+def run_served(args, world, rank, local):
+    import torch
+    import paper_2108_04791_gb300 as ipg
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ctx = ipg.Context.default(local)
+    _apply_tune(ctx, args)
+    rec = served_record(ctx, dev, args.warmup, world, rank,
+                        with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+    if rank == 0:
+        n_req = rec["config"]["requests"]
+        line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world,
+                "steps": n_req, "warmup": max(args.warmup, 3),
+                "ms_per_step": 1e3 * rec["capacity"]["span_s"] / n_req, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", **rec,
+                "tuning": ctx.tuning.as_dict()}
         print(json.dumps(line), flush=True)
 
 

@@ -98,6 +98,27 @@ typedef struct {
   uint32_t serve_short_max;/* a server created on the context batches requests of at most this
                               many elements apart from longer ones, as one-launch warp batches
                               on high-priority streams (0..2^20) */
+  uint32_t td_fold;        /* trial division of 64-bit values by the primes 3..53 (td_primes 15):
+                              0 every prime by the 64-bit multiply-by-inverse test; 1 the primes
+                              dividing 2^32-1, 2^24-1 and 2^20-1 (3, 5, 7, 11, 13, 17, 31, 41)
+                              by the 32-bit test on a sum of chunks of n that is congruent to n
+                              modulo that number; 2 also 29 and 43 by 2^28-1 */
+  uint32_t base2_split;    /* 1: 64-bit survivors with n = 3 (mod 4) (s = 1 in n-1 = 2^s d) are
+                              queued apart from the others, so the base-2 kernel's warps of those
+                              run no strong-test tail; 0: one queue */
+  uint32_t base2_ilp;      /* survivors per thread in the base-2 kernel (1 or 2; 2 takes effect
+                              with base2_window 1, mont_impl_base2 6 and compact_min 33) */
+  uint32_t rest_window;    /* window bits of the six-base exponentiations (3 or 4; 3 takes effect
+                              with mont_impl 6) */
+  uint32_t window_ratio16; /* per-call path choice of the uint64 array entry points (Sec. 6.2's
+                              choice between sieving up to max(N) and testing each element):
+                              0 never (default); otherwise a call of at least 2^16 values reads
+                              the array's min and max (one reduction kernel; the call waits for
+                              it) and, when max >= S, W = max - min + 1 <= 2^30 and
+                              16 W <= window_ratio16 * n, classifies every integer of [min, max]
+                              with the range kernels and gathers the array's bytes from that
+                              window instead of running the queue path.  0..4096; the
+                              autotuner measures the crossover on this GPU */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */
@@ -107,6 +128,7 @@ typedef struct {
   uint64_t kernel_launches;/* kernels launched by the library */
   uint64_t sieve_limit;    /* S: values below S are answered by the sieve */
   uint64_t scratch_bytes;  /* device memory held by the context */
+  uint64_t window_calls;   /* calls that took the window path (window_ratio16) */
 } isprime_stats;
 
 /* ---------------------------------------------------------------- contexts */
@@ -144,12 +166,27 @@ int isprime_u64_ctx(isprime_ctx *ctx, const uint64_t *d_in, uint8_t *d_out, size
 /* Double path (Sec. 8.1): element i is valid when it is finite, >= 0,
  * integral and <= 2^53; valid elements are classified as integers, invalid
  * ones give 0.  If d_invalid is not NULL, the number of invalid elements is
- * added to the device counter *d_invalid (the caller zeroes it and reads it
- * after synchronising; a nonzero count is the ISPRIME_EDOMAIN condition). */
+ * also added to the device counter *d_invalid (the caller zeroes it and reads
+ * it after synchronising).  Whether or not d_invalid is given, the count is
+ * added to the context's own counter, which isprime_f64_sync_status reports
+ * as ISPRIME_EDOMAIN.  The double-path calls of one context run one after
+ * another on the GPU (each waits for the previous one's kernels), whatever
+ * streams they are made on.  isprime_f64 uses the current device's default
+ * context (isprime_default_ctx). */
 int isprime_f64(const double *d_in, uint8_t *d_out, size_t n, unsigned long long *d_invalid,
                 isprime_stream stream);
 int isprime_f64_ctx(isprime_ctx *ctx, const double *d_in, uint8_t *d_out, size_t n,
                     unsigned long long *d_invalid, isprime_stream stream);
+
+/* Domain status of the double path (Sec. 8.1 stores integers in doubles only
+ * up to 2^53; the paper does not say what other doubles give, and this
+ * library answers 0 for them and reports them here).  Waits until every
+ * double-path call made on ctx before this call has run, then takes the
+ * context's count of invalid elements since the previous status call (or the
+ * context's creation) and resets it to 0.  *count (nullable) receives it.
+ * Returns ISPRIME_EDOMAIN if it was not 0, else ISPRIME_OK; ISPRIME_EINVAL
+ * for a NULL ctx; ISPRIME_ECUDA if a CUDA call failed.  Synchronous. */
+int isprime_f64_sync_status(isprime_ctx *ctx, unsigned long long *count);
 
 /* Range form: d_out[i] = isprime(lo + i) for i < count, with no input array
  * (the incrementing sequences 1:N of Sec. 6.1.3 / Table 3 and the windows of
@@ -225,9 +262,12 @@ int isprime_u64_scalar(isprime_ctx *ctx, uint64_t value, uint8_t *result);
  * until exit); no sieve is used.  Calls no cudaMalloc, cudaFree or other
  * allocating routine.  n > ISPRIME_NOALLOC_MAX_ELEMS gives ISPRIME_EINVAL.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls on a device share the array: calls whose GPU work
- * overlaps race, so the caller must order them (one stream, or events). */
+ * device, with that device current) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not call
+ * this entry point on a device after cudaDeviceReset (or anything else that
+ * destroys the device's primary context), which invalidates the address.
+ * All calls on a device share the array: calls whose GPU work overlaps race,
+ * so the caller must order them (one stream, or events). */
 #define ISPRIME_NOALLOC_MAX_ELEMS ((size_t)1 << 20)
 #define ISPRIME_NOALLOC_SCRATCH_BYTES ((size_t)24 * ((size_t)1 << 20) + 256)
 int isprime_u64_noalloc(const uint64_t *d_in, uint8_t *d_out, size_t n, isprime_stream stream);
@@ -372,6 +412,30 @@ typedef struct {
   double sm_clock_mhz;
 } isprime_int_rates;
 int isprime_measure_int_rates(int device, isprime_int_rates *out);
+
+/* Executed Montgomery operations of the two 64-bit Miller-Rabin stages, as
+ * issued by the GPU: each pair is [warp-level issues, active lanes summed
+ * over those issues].  A warp issue occupies all 32 lanes of the integer
+ * pipes whatever the number of active lanes, so 32 x issues is the lane work
+ * paid and the active-lane sum the part that carried a value; the canonical
+ * count of the method (binary left-to-right schedule, Sec. 2.4) is smaller
+ * than either by the warp-uniform padding of the schedules and the
+ * window-table products. */
+typedef struct {
+  uint64_t elements;
+  uint64_t base2_squarings[2]; /* base-2 stage: Montgomery squarings */
+  uint64_t base2_products[2];  /* Montgomery products (window table, mode 4) */
+  uint64_t base2_steps[2];     /* x 2^w mod n window steps (mode 1) */
+  uint64_t rest_squarings[2];  /* six-base stage: squarings (incl. R^2 setup) */
+  uint64_t rest_products[2];   /* products (base conversion, tables, windows) */
+} isprime_op_counts;
+/* Runs isprime_u64_ctx's queue path once on d_in (n values; d_out receives
+ * the results) with the Miller-Rabin kernels built to count their
+ * operations (formulation 6 plus counting; slower), synchronously, and
+ * returns the counts.  Measurement only: no other thread may use ctx during
+ * the call.  Argument errors as isprime_u64_ctx. */
+int isprime_count_ops(isprime_ctx *ctx, const uint64_t *d_in, uint8_t *d_out, size_t n,
+                      isprime_op_counts *out);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -46,7 +46,10 @@ class Tuning(ctypes.Structure):
                 ("batch_tile_log2", ctypes.c_uint32), ("batch_blocks_per_sm", ctypes.c_uint32),
                 ("base2_window", ctypes.c_uint32), ("rest_test", ctypes.c_uint32),
                 ("small_max", ctypes.c_uint32), ("compact_min", ctypes.c_uint32),
-                ("sieve_cutover_log2", ctypes.c_uint32), ("serve_short_max", ctypes.c_uint32)]
+                ("sieve_cutover_log2", ctypes.c_uint32), ("serve_short_max", ctypes.c_uint32),
+                ("td_fold", ctypes.c_uint32), ("base2_split", ctypes.c_uint32),
+                ("base2_ilp", ctypes.c_uint32), ("rest_window", ctypes.c_uint32),
+                ("window_ratio16", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +72,13 @@ class _ServerStats(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_uint64), ("elements", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("sieve_limit", ctypes.c_uint64),
-                ("scratch_bytes", ctypes.c_uint64)]
+                ("scratch_bytes", ctypes.c_uint64), ("window_calls", ctypes.c_uint64)]
+
+
+class _OpCounts(ctypes.Structure):
+    _fields_ = [("elements", ctypes.c_uint64), ("base2_squarings", ctypes.c_uint64 * 2),
+                ("base2_products", ctypes.c_uint64 * 2), ("base2_steps", ctypes.c_uint64 * 2),
+                ("rest_squarings", ctypes.c_uint64 * 2), ("rest_products", ctypes.c_uint64 * 2)]
 
 
 class _KTime(ctypes.Structure):
@@ -109,6 +118,7 @@ def lib():
                 "isprime_u64_ctx": ([vp, vp, vp, sz, vp], i32),
                 "isprime_f64": ([vp, vp, sz, vp, vp], i32),
                 "isprime_f64_ctx": ([vp, vp, vp, sz, vp, vp], i32),
+                "isprime_f64_sync_status": ([vp, ctypes.POINTER(ctypes.c_ulonglong)], i32),
                 "isprime_u64_host": ([vp, vp, vp, sz, vp], i32),
                 "isprime_u64_scalar": ([vp, u64, ctypes.POINTER(ctypes.c_uint8)], i32),
                 "isprime_range": ([vp, u64, u64, vp, vp], i32),
@@ -126,6 +136,7 @@ def lib():
                 "isprime_timing_read": ([vp, ctypes.POINTER(_KTime), i32], i32),
                 "isprime_timing_reset": ([vp], i32),
                 "isprime_measure_int_rates": ([i32, ctypes.POINTER(_IntRates)], i32),
+                "isprime_count_ops": ([vp, vp, vp, sz, ctypes.POINTER(_OpCounts)], i32),
                 "isprime_plan_contiguous": ([u64, ctypes.c_uint32, vp], i32),
                 "isprime_plan_batched": ([vp, sz, ctypes.c_uint32, vp, vp], i32),
                 "isprime_route_least_loaded": ([vp, ctypes.c_uint32,
@@ -278,6 +289,34 @@ class Context:
             inv = None if invalid is None else ctypes.c_void_p(invalid.data_ptr())
             _check(L.isprime_f64_ctx(self._h, src.data_ptr(), out.data_ptr(), n, inv, sh))
         return out
+
+    def count_ops(self, t) -> dict:
+        """Executed Montgomery operations of the Miller-Rabin stages on one
+        pass over the CUDA integer tensor t: {name: (warp issues, active
+        lanes)} (see isprime_count_ops)."""
+        torch = _torch()
+        src, kind = _prep(t)
+        if kind != "u64":
+            raise TypeError("count_ops takes an integer tensor")
+        out = torch.empty(src.numel(), dtype=torch.uint8, device=src.device)
+        c = _OpCounts()
+        _check(lib().isprime_count_ops(self._h, src.data_ptr(), out.data_ptr(), src.numel(),
+                                       ctypes.byref(c)))
+        res = {"elements": int(c.elements)}
+        for k, _ in c._fields_[1:]:
+            v = getattr(c, k)
+            res[k] = (int(v[0]), int(v[1]))
+        return res
+
+    def f64_status(self) -> int:
+        """Invalid double inputs (not integers in [0, 2^53]) seen by the
+        context's double-path calls since the last status read; waits for
+        those calls.  0 means ISPRIME_OK, more than 0 ISPRIME_EDOMAIN."""
+        c = ctypes.c_ulonglong(0)
+        st = lib().isprime_f64_sync_status(self._h, ctypes.byref(c))
+        if st not in (OK, EDOMAIN):
+            _check(st)
+        return int(c.value)
 
     def autotune(self, sample, mode: str = "plain", cache_path: str | None = None) -> dict:
         """Times `sample` (a CUDA integer tensor) under candidate tunings and

@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-O2,-Wall", "-I", os.path.join(ROOT, "include")]
 SOURCES = ["api.cu", "sieve.cu", "classify.cu", "mr.cu", "probe.cu", "noalloc.cu", "batched.cu",
-           "autotune.cu", "server.cu", "range.cu", "small.cu", "shard.cu"]
+           "autotune.cu", "server.cu", "range.cu", "small.cu", "shard.cu", "window.cu"]
 
 
 def nvcc() -> str:

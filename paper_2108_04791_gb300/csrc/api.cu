@@ -89,6 +89,11 @@ static isprime_tuning default_tuning() {
   t.compact_min = 33;
   t.sieve_cutover_log2 = 32;
   t.serve_short_max = 32768;
+  t.td_fold = 0;
+  t.base2_split = 0;
+  t.base2_ilp = 1;
+  t.rest_window = 4;
+  t.window_ratio16 = 0;
   return t;
 }
 
@@ -111,6 +116,11 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.compact_min > 33) return set_error(ISPRIME_EINVAL, "compact_min must be in [0, 33]");
   if (t.sieve_cutover_log2 > 32) return set_error(ISPRIME_EINVAL, "sieve_cutover_log2 must be in [0, 32]");
   if (t.serve_short_max > (1u << 20)) return set_error(ISPRIME_EINVAL, "serve_short_max must be in [0, 2^20]");
+  if (t.td_fold > 2) return set_error(ISPRIME_EINVAL, "td_fold must be in [0, 2]");
+  if (t.base2_split > 1) return set_error(ISPRIME_EINVAL, "base2_split must be 0 or 1");
+  if (t.base2_ilp != 1 && t.base2_ilp != 2) return set_error(ISPRIME_EINVAL, "base2_ilp must be 1 or 2");
+  if (t.rest_window != 3 && t.rest_window != 4) return set_error(ISPRIME_EINVAL, "rest_window must be 3 or 4");
+  if (t.window_ratio16 > 4096) return set_error(ISPRIME_EINVAL, "window_ratio16 must be in [0, 4096]");
   return ISPRIME_OK;
 }
 
@@ -131,7 +141,7 @@ static int alloc_queues(Queues* out, size_t cap) {
   IP_CUDA(cudaMalloc(&q.q64b, cap * sizeof(uint32_t)));
   IP_CUDA(cudaMalloc(&q.q32_n, cap * sizeof(uint32_t)));
   IP_CUDA(cudaMalloc(&q.q32_idx, cap * sizeof(uint32_t)));
-  IP_CUDA(cudaMalloc(&q.counters, 4 * sizeof(uint32_t)));
+  IP_CUDA(cudaMalloc(&q.counters, kQueueCounters * sizeof(uint32_t)));
   q.capacity = cap;
   *out = q;
   return ISPRIME_OK;
@@ -147,7 +157,7 @@ static int ensure_queues(isprime_ctx* ctx, size_t cap) {
 static size_t scratch_bytes(const isprime_ctx* ctx) {
   return ctx->sieve_limit / 16 +
          (ctx->q.capacity + ctx->host_q[0].capacity + ctx->host_q[1].capacity) * 24 +
-         ctx->stage_elems * 9;
+         ctx->stage_elems * 9 + 2 * sizeof(unsigned long long) + ctx->window_cap;
 }
 
 struct DeviceGuard {
@@ -180,6 +190,9 @@ static int ctx_create(int device, uint64_t sieve_limit, isprime_ctx** out) {
   ctx->tune = default_tuning();
   ctx->sieve_limit = sieve_limit;
   IP_CUDA(cudaEventCreateWithFlags(&ctx->order_ev, cudaEventDisableTiming));
+  IP_CUDA(cudaEventCreateWithFlags(&ctx->f64_ev, cudaEventDisableTiming));
+  IP_CUDA(cudaMalloc(&ctx->d_status, 2 * sizeof(unsigned long long)));
+  IP_CUDA(cudaMemset(ctx->d_status, 0, 2 * sizeof(unsigned long long)));
   cudaStream_t s;
   IP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   int st = ISPRIME_OK;
@@ -211,6 +224,19 @@ static int order_after(isprime_ctx* ctx, cudaStream_t s) {
   return ISPRIME_OK;
 }
 
+// The double-path calls of a context form one chain (each waits for the
+// previous one's kernels), so that isprime_f64_sync_status, which waits for
+// the chain's last event, sees the counts of every earlier call.
+static int f64_before(isprime_ctx* ctx, cudaStream_t s) {
+  if (ctx->f64_ev_valid) IP_CUDA(cudaStreamWaitEvent(s, ctx->f64_ev, 0));
+  return ISPRIME_OK;
+}
+static int f64_after(isprime_ctx* ctx, cudaStream_t s) {
+  IP_CUDA(cudaEventRecord(ctx->f64_ev, s));
+  ctx->f64_ev_valid = true;
+  return ISPRIME_OK;
+}
+
 static bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t a0 = (uintptr_t)a, a1 = a0 + na, b0 = (uintptr_t)b, b1 = b0 + nb;
   return a0 < b1 && b0 < a1;
@@ -233,7 +259,7 @@ static int check_array_args(const void* d_in, const void* d_out, size_t n, size_
 template <bool kF64>
 static int run_chunk(isprime_ctx* ctx, const Queues& q, const void* in, uint8_t* out, size_t len,
                      unsigned long long* d_invalid, cudaStream_t s) {
-  IP_CUDA(cudaMemsetAsync(q.counters, 0, 4 * sizeof(uint32_t), s));
+  IP_CUDA(cudaMemsetAsync(q.counters, 0, kQueueCounters * sizeof(uint32_t), s));
   ClassifyArgs a;
   a.in = in;
   a.out = out;
@@ -248,9 +274,13 @@ static int run_chunk(isprime_ctx* ctx, const Queues& q, const void* in, uint8_t*
   a.q32_idx = q.q32_idx;
   a.counters = q.counters;
   a.invalid = d_invalid;
+  a.invalid_ctx = kF64 ? ctx->d_status : nullptr;
   a.head = ((uintptr_t)a.in % 16) ? 1u : 0u;
   if (a.head > len) a.head = (uint32_t)len;
   a.pair_store = (((uintptr_t)(a.out + a.head)) % 2 == 0) ? 1u : 0u;
+  a.q64_cap = (uint32_t)q.capacity;
+  a.fold = ctx->tune.td_fold;
+  a.split = ctx->tune.base2_split;
   int st = kF64 ? launch_classify_f64(ctx, a, s) : launch_classify_u64(ctx, a, s);
   if (st) return st;
   return launch_mr(ctx, q, a.out, len, s);
@@ -267,9 +297,12 @@ static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t 
   DeviceGuard g(ctx->device);
   int st;
   if (n <= ctx->tune.small_max) {  // one launch, no queues: no ordering needed
-    st = kF64 ? launch_small_f64(ctx, static_cast<const double*>(d_in), d_out, n, d_invalid, s)
+    if (kF64 && (st = f64_before(ctx, s))) return st;
+    st = kF64 ? launch_small_f64(ctx, static_cast<const double*>(d_in), d_out, n, d_invalid,
+                                 ctx->d_status, s)
               : launch_small_u64(ctx, static_cast<const uint64_t*>(d_in), d_out, n, s);
     if (st) return st;
+    if (kF64 && (st = f64_after(ctx, s))) return st;
     ctx->stats.calls++;
     ctx->stats.elements += n;
     return ISPRIME_OK;
@@ -278,6 +311,17 @@ static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t 
   st = ensure_queues(ctx, std::min(chunk, std::max(n, (size_t)1 << 16)));
   if (st) return st;
   if ((st = order_before(ctx, s))) return st;
+  if (kF64 && (st = f64_before(ctx, s))) return st;
+  if (!kF64) {  // the window path, when the tuning asks for the per-call choice
+    bool taken = false;
+    if ((st = window_try(ctx, static_cast<const uint64_t*>(d_in), d_out, n, s, &taken))) return st;
+    if (taken) {
+      if ((st = order_after(ctx, s))) return st;
+      ctx->stats.calls++;
+      ctx->stats.elements += n;
+      return ISPRIME_OK;
+    }
+  }
   const size_t step = std::min(chunk, ctx->q.capacity);
   for (size_t off = 0; off < n; off += step) {
     const size_t len = std::min(step, n - off);
@@ -285,10 +329,16 @@ static int run_array(isprime_ctx* ctx, const void* d_in, uint8_t* d_out, size_t 
                          d_invalid, s);
     if (st) return st;
   }
+  if (kF64 && (st = f64_after(ctx, s))) return st;
   if ((st = order_after(ctx, s))) return st;
   ctx->stats.calls++;
   ctx->stats.elements += n;
   return ISPRIME_OK;
+}
+
+// Take-and-clear of the context's invalid-element count (one thread).
+__global__ void take_invalid_kernel(unsigned long long* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) status[1] = atomicExch(&status[0], 0ull);
 }
 
 // ---------------------------------------------------------------- defaults
@@ -348,6 +398,12 @@ int isprime_ctx_destroy(isprime_ctx* ctx) {
       if (hs) cudaStreamDestroy(hs);
     for (auto& hq : ctx->host_q) free_queues(hq);
     if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
+    if (ctx->f64_ev) cudaEventDestroy(ctx->f64_ev);
+    if (ctx->status_s) cudaStreamSynchronize(ctx->status_s), cudaStreamDestroy(ctx->status_s);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_mm);
+    if (ctx->h_mm) cudaFreeHost(ctx->h_mm);
+    cudaFree(ctx->d_window);
     if (ctx->scalar_s) cudaStreamSynchronize(ctx->scalar_s), cudaStreamDestroy(ctx->scalar_s);
     if (ctx->h_inline_out) cudaFreeHost(ctx->h_inline_out);
   }
@@ -423,6 +479,24 @@ int isprime_f64(const double* d_in, uint8_t* d_out, size_t n, unsigned long long
   st = current_default(&ctx);
   if (st) return st;
   return run_array<true>(ctx, d_in, d_out, n, d_invalid, (cudaStream_t)stream);
+}
+
+int isprime_f64_sync_status(isprime_ctx* ctx, unsigned long long* count) {
+  if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
+  if (count) *count = 0;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard g(ctx->device);
+  if (!ctx->status_s) IP_CUDA(cudaStreamCreateWithFlags(&ctx->status_s, cudaStreamNonBlocking));
+  if (ctx->f64_ev_valid) IP_CUDA(cudaStreamWaitEvent(ctx->status_s, ctx->f64_ev, 0));
+  take_invalid_kernel<<<1, 32, 0, ctx->status_s>>>(ctx->d_status);
+  IP_CUDA(cudaGetLastError());
+  unsigned long long v = 0;
+  IP_CUDA(cudaMemcpyAsync(&v, ctx->d_status + 1, sizeof v, cudaMemcpyDeviceToHost, ctx->status_s));
+  IP_CUDA(cudaStreamSynchronize(ctx->status_s));
+  if (count) *count = v;
+  if (v == 0) return ISPRIME_OK;
+  return set_error(ISPRIME_EDOMAIN, std::to_string(v) +
+                                        " double input(s) were not integers in [0, 2^53] (output 0)");
 }
 
 int isprime_range(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out,
@@ -626,6 +700,52 @@ int isprime_timing_reset(isprime_ctx* ctx) {
     ctx->kernel_launches[k] = 0;
   }
   return st;
+}
+
+int isprime_count_ops(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
+                      isprime_op_counts* out) {
+  if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
+  memset(out, 0, sizeof *out);
+  int st = check_array_args(d_in, d_out, n, 8);
+  if (st || n == 0) return st;
+  DeviceGuard g(ctx->device);
+  unsigned long long c[2][3][2];
+  isprime_tuning saved;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ctx->order_ev_valid) IP_CUDA(cudaEventSynchronize(ctx->order_ev));
+    if ((st = op_counts_read(c, true))) return st;
+    saved = ctx->tune;
+    ctx->tune.small_max = 0;  // the queue path, whose kernels count
+    ctx->count_ops = true;
+  }
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    st = run_array<false>(ctx, d_in, d_out, n, nullptr, s);
+    e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->count_ops = false;
+    ctx->tune = saved;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "isprime_count_ops stream");
+  if (st) return st;
+  if ((st = op_counts_read(c, true))) return st;
+  out->elements = n;
+  out->base2_squarings[0] = c[0][0][0];
+  out->base2_squarings[1] = c[0][0][1];
+  out->base2_products[0] = c[0][1][0];
+  out->base2_products[1] = c[0][1][1];
+  out->base2_steps[0] = c[0][2][0];
+  out->base2_steps[1] = c[0][2][1];
+  out->rest_squarings[0] = c[1][0][0];
+  out->rest_squarings[1] = c[1][0][1];
+  out->rest_products[0] = c[1][1][0];
+  out->rest_products[1] = c[1][1][1];
+  return ISPRIME_OK;
 }
 
 int isprime_measure_int_rates(int device, isprime_int_rates* out) {

@@ -587,6 +587,52 @@ struct MontOps<8> {
   }
 };
 
+// Formulations 16 and 17: formulation 6 with every operation counted, for
+// the measurement entry point isprime_count_ops (16 in the base-2 kernel, 17
+// in the six-base kernel).  Per operation the warp's first active lane adds
+// one warp-level issue and the number of active lanes to a counter of this
+// translation unit (64 copies, picked by block, to spread the atomics).
+// Kinds: 0 squaring, 1 product, 2 multiplication by 2^w (base-2 window step).
+constexpr int kOpKinds = 3;
+constexpr int kOpSpread = 64;
+static __device__ unsigned long long g_ip_ops[2][kOpKinds][2][kOpSpread];
+
+template <int kImpl>
+__device__ __forceinline__ void op_note(int kind) {
+  if constexpr (kImpl == 16 || kImpl == 17) {
+    const unsigned m = __activemask();
+    if ((int)(threadIdx.x & 31) == __ffs(m) - 1) {
+      unsigned long long* c = g_ip_ops[kImpl - 16][kind][0];
+      atomicAdd(&c[blockIdx.x % kOpSpread], 1ull);
+      atomicAdd(&c[kOpSpread + blockIdx.x % kOpSpread], (unsigned long long)__popc(m));
+    }
+  }
+}
+
+template <>
+struct MontOps<16> {
+  static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
+    op_note<16>(1);
+    return mont_mul_c(a, b, M.n, M.ninv);
+  }
+  static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
+    op_note<16>(0);
+    return mont_sqr_c(a, M.n, M.ninv);
+  }
+};
+
+template <>
+struct MontOps<17> {
+  static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
+    op_note<17>(1);
+    return mont_mul_c(a, b, M.n, M.ninv);
+  }
+  static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
+    op_note<17>(0);
+    return mont_sqr_c(a, M.n, M.ninv);
+  }
+};
+
 template <>
 struct MontOps<2> {
   static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {

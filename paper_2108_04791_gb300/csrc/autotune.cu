@@ -44,6 +44,10 @@ std::vector<Param> params() {
       {"mont_impl_base2", &isprime_tuning::mont_impl_base2, {6, 0, 5}, P},
       {"base2_window", &isprime_tuning::base2_window, {0, 1, 4}, P},
       {"compact_min", &isprime_tuning::compact_min, {33, 28, 24, 16}, P},
+      {"td_fold", &isprime_tuning::td_fold, {0, 1, 2}, P},
+      {"base2_split", &isprime_tuning::base2_split, {0, 1}, P},
+      {"base2_ilp", &isprime_tuning::base2_ilp, {1, 2}, P},
+      {"rest_window", &isprime_tuning::rest_window, {4, 3}, P},
       {"sieve_cutover_log2", &isprime_tuning::sieve_cutover_log2, {32, 28, 24, 20}, P | B},
       {"batch_block", &isprime_tuning::batch_block, {64, 128, 256}, B},
       {"batch_tile_log2", &isprime_tuning::batch_tile_log2, {8, 9, 10, 11, 12}, B},
@@ -67,7 +71,8 @@ std::string cache_key(int device, size_t n, int mode) {
 const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_primes", "chunk_log2",
                          "mont_impl", "mont_impl_base2", "batch_block", "batch_tile_log2",
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
-                         "compact_min", "sieve_cutover_log2", "serve_short_max"};
+                         "compact_min", "sieve_cutover_log2", "serve_short_max", "td_fold",
+                         "base2_split", "base2_ilp", "rest_window", "window_ratio16"};
 FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
@@ -75,8 +80,9 @@ FieldPtr kFieldPtr[] = {
     &isprime_tuning::batch_tile_log2, &isprime_tuning::batch_blocks_per_sm,
     &isprime_tuning::base2_window, &isprime_tuning::rest_test, &isprime_tuning::small_max,
     &isprime_tuning::compact_min, &isprime_tuning::sieve_cutover_log2,
-    &isprime_tuning::serve_short_max};
-constexpr int kNumFields = 16;
+    &isprime_tuning::serve_short_max, &isprime_tuning::td_fold, &isprime_tuning::base2_split,
+    &isprime_tuning::base2_ilp, &isprime_tuning::rest_window, &isprime_tuning::window_ratio16};
+constexpr int kNumFields = 21;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;
@@ -226,6 +232,20 @@ int autotune(isprime_ctx* ctx, const uint64_t* d_sample, uint8_t* d_out, size_t 
       best_small = (uint32_t)m;
     }
     t.small_max = best_small;
+  }
+  // The window path (window.cu): its crossover on this GPU near the sample's
+  // largest value; installed when the sample itself is a window the fitted
+  // rule takes (its values dense in [min, max] above the sieve limit).
+  if (!st && !batched) {
+    isprime_ctx_set_tuning(ctx, &t);
+    uint64_t lo = 0, hi = 0;
+    uint32_t r16 = 0;
+    st = array_minmax(ctx, d_sample, n, s, &lo, &hi);
+    if (!st) st = window_fit(ctx, hi, n, s, &r16);
+    const unsigned __int128 w = (unsigned __int128)(hi - lo) + 1;
+    if (!st && r16 && n >= ((size_t)1 << 16) && hi >= sieve_cut(ctx) &&
+        w <= ((unsigned __int128)1 << 30) && w * 16 <= (unsigned __int128)n * r16)
+      t.window_ratio16 = r16;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

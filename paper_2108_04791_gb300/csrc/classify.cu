@@ -12,6 +12,8 @@
 //   is written 0 here and set to 1 later if they are prime.
 // Loads are 16-byte vector loads (coalesced, eight elements per thread per
 // tile); queue appends are block-aggregated (one atomic per queue and tile).
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -57,6 +59,7 @@ __device__ void classify_single(const ClassifyArgs& a, uint64_t i) {
   const uint64_t v = Loader<T>::one(a.in, i, &ok);
   int d = ok ? classify_value<-1>(v, a) : kComposite;
   if (!ok && a.invalid) atomicAdd(a.invalid, 1ull);
+  if (!ok && a.invalid_ctx) atomicAdd(a.invalid_ctx, 1ull);
   a.out[i] = (uint8_t)(d == kPrime);
   if (d == kMR64) {
     const uint32_t pos = atomicAdd(&a.counters[0], 1u);
@@ -70,25 +73,26 @@ __device__ void classify_single(const ClassifyArgs& a, uint64_t i) {
 }
 
 // Exclusive block-wide prefix sum of v; *total receives the block sum.
-// Every thread of the block must call it (two barriers).
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp,
-                                                         uint32_t* total) {
+// Every thread of the block must call it (two barriers).  V is uint32_t or
+// uint64_t (several small counts packed in bit fields add field by field).
+template <typename V>
+__device__ __forceinline__ V block_exclusive_scan(V v, V* s_warp, V* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
-  uint32_t incl = v;
+  V incl = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    const V t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
     if (lane >= o) incl += t;
   }
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    const uint32_t w = lane < nwarps ? s_warp[lane] : 0u;
-    uint32_t wi = w;
+    const V w = lane < nwarps ? s_warp[lane] : (V)0;
+    V wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      const V t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
       if (lane >= o) wi += t;
     }
     s_warp[lane] = wi - w;
@@ -106,10 +110,17 @@ constexpr int kPairsPerThread = 4;  // 8 elements per thread per tile
 // queues with one atomic per queue for the whole block.  40 registers give
 // six 256-thread blocks per SM (measured: 0.115 ms per 2^24 large values,
 // 0.547 ms per 2^26 mixed values, against 0.117 / 0.596 ms at 45).
-template <typename T, int kNtd>
+// kFold: fold level of the 64-bit trial division (classify_value).
+// kSplit: 64-bit survivors with n = 3 (mod 4) (s = 1 in n - 1 = 2^s d) are
+// appended to q64 from the front, the others (s >= 2) from the back end
+// (position q64_cap - 1 - k), so that the base-2 kernel's warps of the front
+// region share s = 1 and skip the strong-test tail; without kSplit every
+// survivor goes to the front.
+template <typename T, int kNtd, int kFold = 0, bool kSplit = false>
 __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
-  __shared__ uint32_t s_scan[33];
-  __shared__ uint32_t s_base[2];
+  using ScanT = typename std::conditional<kSplit, unsigned long long, uint32_t>::type;
+  __shared__ ScanT s_scan[33];
+  __shared__ uint32_t s_base[3];
   const uint64_t head = a.head;
   const uint64_t npairs = (a.n - head) / 2;
   const uint64_t tile_pairs = (uint64_t)blockDim.x * kPairsPerThread;
@@ -119,6 +130,7 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
     uint32_t dm = 0;     // the eight decisions, two bits each (element j at bits 2j, 2j+1)
     uint32_t sneed = 0;  // elements whose answer is a sieve bit (bit j), looked up below
     uint32_t nbad = 0;
+    uint32_t s1 = 0;     // kSplit: n = 3 (mod 4) marks at the codes' even bit positions (2j)
 #pragma unroll
     for (int k = 0; k < kPairsPerThread; ++k) {
       const uint64_t p = tile * tile_pairs + (uint64_t)k * blockDim.x + threadIdx.x;
@@ -126,8 +138,13 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
       if (p < npairs) {
         bool ok0, ok1;
         Loader<T>::pair(a.in, head + 2 * p, &v[2 * k], &v[2 * k + 1], &ok0, &ok1);
-        const int d0 = ok0 ? classify_value<kNtd, ClassifyArgs, true>(v[2 * k], a) : kComposite;
-        const int d1 = ok1 ? classify_value<kNtd, ClassifyArgs, true>(v[2 * k + 1], a) : kComposite;
+        if (kSplit)
+          s1 |= (((uint32_t)v[2 * k] >> 1) & 1u) << (4 * k) |
+                (((uint32_t)v[2 * k + 1] >> 1) & 1u) << (4 * k + 2);
+        const int d0 =
+            ok0 ? classify_value<kNtd, ClassifyArgs, true, kFold>(v[2 * k], a) : kComposite;
+        const int d1 =
+            ok1 ? classify_value<kNtd, ClassifyArgs, true, kFold>(v[2 * k + 1], a) : kComposite;
         nbad += (uint32_t)!ok0 + (uint32_t)!ok1;
         sneed |= ((uint32_t)(d0 == kSieveLookup) << (2 * k)) |
                  ((uint32_t)(d1 == kSieveLookup) << (2 * k + 1));
@@ -161,21 +178,35 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
     // kMR64 = 0b10, kMR32 = 0b11: count the codes by their two bits
     static_assert(kComposite == 0 && kPrime == 1 && kMR64 == 2 && kMR32 == 3, "2-bit decision codes");
     const uint32_t dhi = (dm >> 1) & 0x5555u, dlo = dm & 0x5555u;
-    const uint32_t n64 = __popc(dhi & ~dlo), n32 = __popc(dhi & dlo);
-    // counts fit in 16 bits each (<= 8 per thread, <= 8192 per block)
-    uint32_t total;
-    const uint32_t pre = block_exclusive_scan(n64 | (n32 << 16), s_scan, &total);
+    const uint32_t m64 = dhi & ~dlo, n32 = __popc(dhi & dlo);
+    const uint32_t n64f = __popc(kSplit ? (m64 & s1) : m64);
+    const uint32_t n64b = kSplit ? __popc(m64 & ~s1) : 0u;
+    // counts fit in 16 bits each (<= 8 per thread, <= 8192 per block); the
+    // split form packs three counts in 21-bit fields of a 64-bit word
+    ScanT total;
+    const ScanT packed = kSplit ? (ScanT)n64f | ((ScanT)n64b << 21) | ((ScanT)n32 << 42)
+                                : (ScanT)n64f | ((ScanT)n32 << 16);
+    const ScanT pre = block_exclusive_scan<ScanT>(packed, s_scan, &total);
+    constexpr int kSh32 = kSplit ? 42 : 16;
+    constexpr ScanT kMask = kSplit ? (ScanT)0x1FFFFF : (ScanT)0xFFFF;
     if (threadIdx.x == 0) {
-      s_base[0] = (total & 0xFFFFu) ? atomicAdd(&a.counters[0], total & 0xFFFFu) : 0u;
-      s_base[1] = (total >> 16) ? atomicAdd(&a.counters[1], total >> 16) : 0u;
+      const uint32_t tf = (uint32_t)(total & kMask), t32 = (uint32_t)(total >> kSh32);
+      const uint32_t tb = kSplit ? (uint32_t)((total >> 21) & kMask) : 0u;
+      s_base[0] = tf ? atomicAdd(&a.counters[0], tf) : 0u;
+      s_base[1] = t32 ? atomicAdd(&a.counters[1], t32) : 0u;
+      s_base[2] = tb ? atomicAdd(&a.counters[4], tb) : 0u;
     }
-    if (a.invalid) {
+    if (a.invalid || a.invalid_ctx) {
       const unsigned bad = __reduce_add_sync(0xFFFFFFFFu, nbad);
-      if ((threadIdx.x & 31) == 0 && bad) atomicAdd(a.invalid, (unsigned long long)bad);
+      if ((threadIdx.x & 31) == 0 && bad) {
+        if (a.invalid) atomicAdd(a.invalid, (unsigned long long)bad);
+        if (a.invalid_ctx) atomicAdd(a.invalid_ctx, (unsigned long long)bad);
+      }
     }
     __syncthreads();
-    uint32_t pos64 = s_base[0] + (pre & 0xFFFFu);
-    uint32_t pos32 = s_base[1] + (pre >> 16);
+    uint32_t pos64 = s_base[0] + (uint32_t)(pre & kMask);
+    uint32_t pos32 = s_base[1] + (uint32_t)(pre >> kSh32);
+    uint32_t posb = kSplit ? s_base[2] + (uint32_t)((pre >> 21) & kMask) : 0u;
 #pragma unroll
     for (int k = 0; k < kPairsPerThread; ++k) {
       const uint64_t p = tile * tile_pairs + (uint64_t)k * blockDim.x + threadIdx.x;
@@ -185,9 +216,16 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
         const int j = 2 * k + h;
         const int dj = (int)((dm >> (2 * j)) & 3u);
         if (dj == kMR64) {
-          a.q64_n[pos64] = v[j];
-          a.q64_idx[pos64] = i0 + h;
-          ++pos64;
+          if (!kSplit || ((s1 >> (2 * j)) & 1u)) {
+            a.q64_n[pos64] = v[j];
+            a.q64_idx[pos64] = i0 + h;
+            ++pos64;
+          } else {
+            const uint32_t pb = a.q64_cap - 1u - posb;
+            a.q64_n[pb] = v[j];
+            a.q64_idx[pb] = i0 + h;
+            ++posb;
+          }
         } else if (dj == kMR32) {
           a.q32_n[pos32] = (uint32_t)v[j];
           a.q32_idx[pos32] = i0 + h;
@@ -206,9 +244,22 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
 
 // Trial-division counts with a compiled specialisation; other counts use
 // the runtime-count kernel.
+// The fold levels and the s-split are compiled for the default count (15,
+// the odd primes 3..53, all of which kFoldOf covers); other counts take the
+// unfolded, unsplit kernel (the results are the same either way).
 template <typename T>
 static void launch_classify_kernel(const ClassifyArgs& a, unsigned grid, unsigned block,
                                    cudaStream_t s) {
+  if (a.ntd == 15 && (a.fold != 0 || a.split != 0)) {
+    const int key = (int)a.fold * 2 + (a.split ? 1 : 0);
+    switch (key) {
+      case 1: classify_kernel<T, 15, 0, true><<<grid, block, 0, s>>>(a); return;
+      case 2: classify_kernel<T, 15, 1, false><<<grid, block, 0, s>>>(a); return;
+      case 3: classify_kernel<T, 15, 1, true><<<grid, block, 0, s>>>(a); return;
+      case 4: classify_kernel<T, 15, 2, false><<<grid, block, 0, s>>>(a); return;
+      default: classify_kernel<T, 15, 2, true><<<grid, block, 0, s>>>(a); return;
+    }
+  }
   switch (a.ntd) {
     case 0: classify_kernel<T, 0><<<grid, block, 0, s>>>(a); break;
     case 7: classify_kernel<T, 7><<<grid, block, 0, s>>>(a); break;

@@ -32,13 +32,31 @@ __device__ __forceinline__ bool f64_to_u64(double x, uint64_t* v) {
 constexpr int kWin = 4;
 constexpr int kTab = 1 << kWin;
 
+// Chunk sums of n = hi 2^32 + lo modulo 2^k - 1 (see kFoldOf in tables.cuh);
+// each result is below 2^32 and congruent to n modulo 2^k - 1.
+__device__ __forceinline__ uint32_t fold_sum32(uint32_t lo, uint32_t hi) {
+  const uint64_t s = (uint64_t)lo + hi;  // < 2^33; the carry wraps around
+  return (uint32_t)s + (uint32_t)(s >> 32);
+}
+__device__ __forceinline__ uint32_t fold_sum24(uint32_t lo, uint32_t hi) {
+  return (lo & 0xFFFFFFu) + (__funnelshift_r(lo, hi, 24) & 0xFFFFFFu) + (hi >> 16);
+}
+__device__ __forceinline__ uint32_t fold_sum20(uint32_t lo, uint32_t hi) {
+  return (lo & 0xFFFFFu) + (__funnelshift_r(lo, hi, 20) & 0xFFFFFu) + ((hi >> 8) & 0xFFFFFu) +
+         (hi >> 28);
+}
+__device__ __forceinline__ uint32_t fold_sum28(uint32_t lo, uint32_t hi) {
+  return (lo & 0xFFFFFFFu) + (__funnelshift_r(lo, hi, 28) & 0xFFFFFFFu) + (hi >> 24);
+}
+
 // kNtd >= 0: the trial-division count is a compile-time constant, the loops
 // unroll and the inverses and limits become constant operands of the
 // multiply and compare instructions.  kNtd < 0: runtime count a.ntd.
 // kDefer: an odd n below the sieve limit returns kSieveLookup instead of its
 // sieve bit, so that the caller can issue the lookups of several values
-// together.
-template <int kNtd, typename P, bool kDefer = false>
+// together.  kFold (compile-time kNtd only): the fold level of the 64-bit
+// trial division, 0 none, 1 or 2 (fold_width in tables.cuh).
+template <int kNtd, typename P, bool kDefer = false, int kFold = 0>
 __device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
   if (n < 2) return kComposite;
   if ((n & 1) == 0) return n == 2 ? kPrime : kComposite;
@@ -55,6 +73,19 @@ __device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
         hit |= v * c_td.inv32[i] <= c_td.lim32[i];
         equal |= v == c_td.p[i];
       }
+    } else if constexpr (kFold > 0 && kNtd > 0) {
+      const uint32_t lo = (uint32_t)n, hi = (uint32_t)(n >> 32);
+      const uint32_t v32 = fold_sum32(lo, hi), v24 = fold_sum24(lo, hi);
+      const uint32_t v20 = fold_sum20(lo, hi), v28 = kFold >= 2 ? fold_sum28(lo, hi) : 0u;
+#pragma unroll
+      for (int i = 0; i < kNtd; ++i) {
+        const int k = fold_width(i, kFold);
+        const uint32_t v = k == 32 ? v32 : k == 24 ? v24 : k == 20 ? v20 : v28;
+        if (k != 0)
+          hit |= v * c_td.inv32[i] <= c_td.lim32[i];
+        else
+          hit |= n * c_td.inv64[i] <= c_td.lim64[i];
+      }
     } else {
 #pragma unroll
       for (uint32_t i = 0; i < (kNtd >= 0 ? (uint32_t)kNtd : ntd); ++i)
@@ -67,30 +98,41 @@ __device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
   return n < (1ull << 32) ? kMR32 : kMR64;
 }
 
-// a^d mod n in Montgomery form by 4-bit fixed windows over the nibbles of d.
-// tab points at this thread's column of the shared table (stride `ld`).
-template <int kImpl>
-__device__ __forceinline__ uint64_t mont_pow_win4(const Mont64& M, uint64_t aR, uint64_t d,
-                                                  uint64_t* tab, int ld, int nib_warp = 0) {
+// a^d mod n in Montgomery form by kW-bit fixed windows over the digits of d
+// (kW = 4: a table of 16 powers, 14 products to build it and one product
+// per four squarings; kW = 3: 8 powers, 6 products, one per three squarings;
+// for a 63-bit d that is 89 against 86 Montgomery operations).  tab points
+// at this thread's column of the shared table (stride `ld`); nib_warp is the
+// warp's largest digit count (leading zero digits select tab[0] = 1).
+template <int kImpl, int kW = kWin>
+__device__ __forceinline__ uint64_t mont_pow_win(const Mont64& M, uint64_t aR, uint64_t d,
+                                                 uint64_t* tab, int ld, int nib_warp = 0) {
   using Ops = MontOps<kImpl>;
+  constexpr int kT = 1 << kW;
   tab[0] = M.one;
   tab[ld] = aR;
   uint64_t t = Ops::sqr(aR, M);
   tab[2 * ld] = t;
 #pragma unroll
-  for (int j = 3; j < kTab; ++j) {
+  for (int j = 3; j < kT; ++j) {
     t = Ops::mul(t, aR, M);
     tab[j * ld] = t;
   }
-  int nib = (64 - clz64(d) + kWin - 1) / kWin;  // nibbles in d (d >= 1)
-  if (nib_warp > nib) nib = nib_warp;  // leading zero nibbles select tab[0] = 1
-  uint64_t x = tab[(int)((d >> (kWin * (nib - 1))) & (kTab - 1)) * ld];
+  int nib = (64 - clz64(d) + kW - 1) / kW;  // digits in d (d >= 1)
+  if (nib_warp > nib) nib = nib_warp;
+  uint64_t x = tab[(int)((d >> (kW * (nib - 1))) & (kT - 1)) * ld];
   for (int k = nib - 2; k >= 0; --k) {
 #pragma unroll
-    for (int r = 0; r < kWin; ++r) x = Ops::sqr(x, M);
-    x = Ops::mul(x, tab[(int)((d >> (kWin * k)) & (kTab - 1)) * ld], M);
+    for (int r = 0; r < kW; ++r) x = Ops::sqr(x, M);
+    x = Ops::mul(x, tab[(int)((d >> (kW * k)) & (kT - 1)) * ld], M);
   }
   return x;
+}
+
+// Digits of kW bits in d >= 1.
+template <int kW>
+__device__ __forceinline__ int win_digits(uint64_t d) {
+  return (64 - clz64(d) + kW - 1) / kW;
 }
 
 // The six bases after base 2 (Eq. 4) for odd n >= 2^32 (no base is 0 mod n),
@@ -98,19 +140,19 @@ __device__ __forceinline__ uint64_t mont_pow_win4(const Mont64& M, uint64_t aR, 
 // warp's largest nibble count and every base runs (the inputs are almost all
 // primes, which need all six anyway), so the warp never splits.  Lanes with
 // valid == false pass any odd n >= 2^32.
-template <int kImpl>
+template <int kImpl, int kW = kWin>
 __device__ __forceinline__ bool rest64_is_prime_warp(uint64_t n, bool valid, uint64_t* tab, int ld) {
   const Mont64 M = mont64_setup(n);
   const uint64_t r2 = mont64_r2<kImpl>(M);
   uint64_t d = n - 1;
   const int s = ctz64(d);
   d >>= s;
-  const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)((64 - clz64(d) + kWin - 1) / kWin));
+  const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)win_digits<kW>(d));
   bool prime = true;
 #pragma unroll 1
   for (int b = 1; b < kNumBases64; ++b) {
     const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b], r2, M);
-    const uint64_t x = mont_pow_win4<kImpl>(M, aR, d, tab, ld, nib);
+    const uint64_t x = mont_pow_win<kImpl, kW>(M, aR, d, tab, ld, nib);
     prime = prime && sprp_tail64<kImpl>(M, x, s);
   }
   return valid && prime;
@@ -120,7 +162,7 @@ __device__ __forceinline__ bool rest64_is_prime_warp(uint64_t n, bool valid, uin
 // an odd n >= 2^32 that passed base 2: true when all pass.  Warp-synchronous
 // like rest64_is_prime_warp (all 32 lanes call it with the same cnt, any mix
 // of n and first; every exponentiation runs the warp's largest nibble count).
-template <int kImpl>
+template <int kImpl, int kW = kWin>
 __device__ __forceinline__ bool bases_pass_warp(uint64_t n, int first, int cnt, uint64_t* tab,
                                                 int ld) {
   const Mont64 M = mont64_setup(n);
@@ -128,12 +170,12 @@ __device__ __forceinline__ bool bases_pass_warp(uint64_t n, int first, int cnt, 
   uint64_t d = n - 1;
   const int s = ctz64(d);
   d >>= s;
-  const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)((64 - clz64(d) + kWin - 1) / kWin));
+  const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)win_digits<kW>(d));
   bool pass = true;
 #pragma unroll 1
   for (int k = 0; k < cnt; ++k) {
     const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[first + k], r2, M);
-    pass = pass && sprp_tail64<kImpl>(M, mont_pow_win4<kImpl>(M, aR, d, tab, ld, nib), s);
+    pass = pass && sprp_tail64<kImpl>(M, mont_pow_win<kImpl, kW>(M, aR, d, tab, ld, nib), s);
   }
   return pass;
 }
@@ -234,13 +276,69 @@ __device__ __forceinline__ bool base2_passes_shift(uint64_t n, int nib_warp) {
   d >>= s;
   uint64_t e = nib_warp >= 16 ? d : d << (64 - 4 * nib_warp);  // left-aligned exponent
   uint64_t x = mul_pow2_mod(M.one, (uint32_t)(e >> 60), n, P);
+  op_note<kImpl>(2);
   for (int k = 1; k < nib_warp; ++k) {
     e <<= 4;
 #pragma unroll
     for (int r = 0; r < 4; ++r) x = Ops::sqr(x, M);
     x = mul_pow2_mod(x, (uint32_t)(e >> 60), n, P);
+    op_note<kImpl>(2);
   }
   return sprp_tail64<kImpl>(M, x, s);
+}
+
+// Base 2 for two values at once (odd na, nb >= 2^32), the schedule of
+// base2_passes_shift run on both in one loop: the two exponentiations are
+// independent, so the multiplies of one overlap the carry chains of the
+// other.  nib_warp covers both values of every lane of the warp.  The
+// strong-test tails run until both values are decided.
+template <int kImpl>
+__device__ __forceinline__ void base2_passes_shift_x2(uint64_t na, uint64_t nb, int nib_warp,
+                                                      bool* pass_a, bool* pass_b) {
+  using Ops = MontOps<kImpl>;
+  const Mont64 Ma = mont64_setup(na), Mb = mont64_setup(nb);
+  const Pow2Red Pa = pow2red_setup(na), Pb = pow2red_setup(nb);
+  uint64_t da = na - 1, db = nb - 1;
+  const int sa = ctz64(da), sb = ctz64(db);
+  da >>= sa;
+  db >>= sb;
+  uint64_t ea = nib_warp >= 16 ? da : da << (64 - 4 * nib_warp);
+  uint64_t eb = nib_warp >= 16 ? db : db << (64 - 4 * nib_warp);
+  uint64_t xa = mul_pow2_mod(Ma.one, (uint32_t)(ea >> 60), na, Pa);
+  op_note<kImpl>(2);
+  uint64_t xb = mul_pow2_mod(Mb.one, (uint32_t)(eb >> 60), nb, Pb);
+  op_note<kImpl>(2);
+  for (int k = 1; k < nib_warp; ++k) {
+    ea <<= 4;
+    eb <<= 4;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      xa = Ops::sqr(xa, Ma);
+      xb = Ops::sqr(xb, Mb);
+    }
+    xa = mul_pow2_mod(xa, (uint32_t)(ea >> 60), na, Pa);
+    op_note<kImpl>(2);
+    xb = mul_pow2_mod(xb, (uint32_t)(eb >> 60), nb, Pb);
+    op_note<kImpl>(2);
+  }
+  // a passes when a^d = +-1, or a^(d 2^r) = -1 for some 1 <= r < s; a value
+  // of 1 after a squaring ends the test (it stays 1)
+  bool pa = xa == Ma.one || xa == Ma.mone, pb = xb == Mb.one || xb == Mb.mone;
+  bool done_a = pa || sa <= 1, done_b = pb || sb <= 1;
+  for (int r = 1; !(done_a && done_b); ++r) {
+    if (!done_a) {
+      xa = Ops::sqr(xa, Ma);
+      pa = xa == Ma.mone;
+      done_a = pa || xa == Ma.one || r + 1 >= sa;
+    }
+    if (!done_b) {
+      xb = Ops::sqr(xb, Mb);
+      pb = xb == Mb.mone;
+      done_b = pb || xb == Mb.one || r + 1 >= sb;
+    }
+  }
+  *pass_a = pa;
+  *pass_b = pb;
 }
 
 // Number of 4-bit nibbles of the odd part of n - 1.

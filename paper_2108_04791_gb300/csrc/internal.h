@@ -21,6 +21,9 @@ int cuda_fail(cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return ::ip::cuda_fail(e_, #call); \
   } while (0)
 
+// Number of 32-bit queue counters (see Queues::counters).
+constexpr int kQueueCounters = 8;
+
 // Queue layout (device, per context).  Capacities are the chunk length, so a
 // queue can hold every element of a chunk and never overflows.
 struct Queues {
@@ -29,7 +32,9 @@ struct Queues {
   uint32_t* q64b = nullptr;     // positions in q64 that passed the base-2 test
   uint32_t* q32_n = nullptr;    // values in [S, 2^32) that survived trial division
   uint32_t* q32_idx = nullptr;
-  uint32_t* counters = nullptr; // [0] q64 size, [1] q32 size, [2] q64b size, [3] base-2 task counter
+  // [0] q64 front size, [1] q32 size, [2] q64b size, [3] base-2 task counter,
+  // [4] q64 back size (entries at capacity - 1, capacity - 2, ...), [5..7] unused
+  uint32_t* counters = nullptr;
   size_t capacity = 0;
 };
 
@@ -86,6 +91,7 @@ struct isprime_ctx {
   std::mutex host_mu;  // serialises isprime_u64_host (staging buffers)
   // measurement
   bool timing = false;
+  bool count_ops = false;            // isprime_count_ops: counting Miller-Rabin kernels
   std::vector<ip::TimedLaunch> pending;
   std::vector<cudaEvent_t> event_pool;
   double kernel_ms[ISPRIME_K_COUNT] = {};
@@ -109,6 +115,20 @@ struct isprime_ctx {
   uint8_t* h_inline_out = nullptr;   // pinned, mapped, ISPRIME_HOST_INLINE_MAX bytes
   uint8_t* d_inline_out = nullptr;   // its device address
   cudaStream_t scalar_s = nullptr;   // stream of isprime_u64_scalar
+  // double-path domain status: every f64 call adds its invalid elements to
+  // d_status[0]; isprime_f64_sync_status takes it (into d_status[1]) after
+  // the last f64 call (f64_ev), on status_s
+  unsigned long long* d_status = nullptr;
+  cudaEvent_t f64_ev = nullptr;
+  bool f64_ev_valid = false;
+  cudaStream_t status_s = nullptr;
+  // window path (window.cu): min/max read-back and the window's bytes
+  unsigned long long* d_mm = nullptr;
+  unsigned long long* h_mm = nullptr;  // pinned
+  uint64_t last_window_lo = 0, last_window_hi = 0;
+  uint32_t fitted_window_ratio16 = 0;  // the autotuner's last crossover fit
+  uint8_t* d_window = nullptr;
+  size_t window_cap = 0;
 };
 
 namespace ip {
@@ -147,9 +167,13 @@ struct ClassifyArgs {
   uint32_t* q32_n;
   uint32_t* q32_idx;
   uint32_t* counters;
-  unsigned long long* invalid;
+  unsigned long long* invalid;      // the caller's counter (nullable)
+  unsigned long long* invalid_ctx;  // the context's own counter (nullable)
   uint32_t head;              // leading elements handled singly (alignment)
   uint32_t pair_store;        // 1 if out+head is 2-byte aligned (16-bit stores)
+  uint32_t q64_cap;           // capacity of q64 (its back region ends there)
+  uint32_t fold;              // fold level of the 64-bit trial division (0..2)
+  uint32_t split;             // 1: 64-bit survivors split by s into q64's two regions
 };
 int launch_classify_u64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s);
 int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s);
@@ -157,11 +181,24 @@ int launch_classify_f64(isprime_ctx* ctx, const ClassifyArgs& a, cudaStream_t s)
 // mr.cu
 // len: elements of the chunk just classified (bounds the queue lengths).
 int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cudaStream_t s);
+// The operation counters of the counting kernels: [stage: base 2, six bases]
+// [kind: squaring, product, 2^w step][warp issues, active lanes].
+int op_counts_read(unsigned long long out[2][3][2], bool reset);
 
 // Context-free launchers (explicit launch shape), used by noalloc.cu.
 int launch_classify_u64_raw(const ClassifyArgs& a, unsigned grid, unsigned block, cudaStream_t s);
 int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, unsigned block,
                   cudaStream_t s);
+
+// window.cu: the per-call choice of the window path for a u64 array of n
+// values; *taken tells whether it ran (otherwise the queue path must).
+int window_try(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n, cudaStream_t s,
+               bool* taken);
+int array_minmax(isprime_ctx* ctx, const uint64_t* d_in, size_t n, cudaStream_t s, uint64_t* lo,
+                 uint64_t* hi);
+// The autotuner's crossover fit of the window path near the value `near`
+// (arrays of up to n values); the context's tuning is unchanged.
+int window_fit(isprime_ctx* ctx, uint64_t near, size_t n, cudaStream_t s, uint32_t* ratio16);
 
 // probe.cu
 int measure_int_rates(int device, isprime_int_rates* out);
@@ -173,7 +210,8 @@ constexpr int kInlineMax = ISPRIME_HOST_INLINE_MAX;
 int launch_small_u64(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
                      cudaStream_t s);
 int launch_small_f64(isprime_ctx* ctx, const double* d_in, uint8_t* d_out, size_t n,
-                     unsigned long long* d_invalid, cudaStream_t s);
+                     unsigned long long* d_invalid, unsigned long long* d_invalid_ctx,
+                     cudaStream_t s);
 // A batch in one-warp-per-element form: d_descs[i].tile_begin holds the
 // element prefix sum of array i (total elements in all arrays).
 int launch_small_batched(isprime_ctx* ctx, const BatchDesc* d_descs, uint32_t n_arrays,

@@ -29,6 +29,8 @@
 //                      survivors between the sieve cutover and 2^32.
 // All arithmetic is in arith.cuh (ModExp / ModMultiply / ModAdd of
 // Sec. 2.2-2.4 as Montgomery multiplication and doubling).
+#include <string.h>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -40,59 +42,101 @@ namespace ip {
 // kRest (modes 1 and 4): 0 compact every survivor into q64b; 1 or 2 a warp
 // with at least compact_min survivors finishes them itself, with the six
 // remaining bases (1) or the strong Lucas test (2), and compacts nothing.
-template <int kImpl, int kMode, int kRest>
+// kIlp (mode 1, kRest 0): survivors per thread, 1 or 2 (two independent
+// exponentiations per thread, base2_passes_shift_x2).
+//
+// The queue q64 has two regions (see classify.cu): [0, counters[0]) from the
+// front and [cap - counters[4], cap) from the back.  When classify splits by
+// s (n - 1 = 2^s d), the front holds s = 1 and the back s >= 2, so the
+// strong-test tail, which a warp runs for its largest s, is empty for the
+// front's warps.  Tasks of 32 * kIlp positions walk the front region (its
+// last task padded) and then the back region.
+template <int kImpl, int kMode, int kRest, int kIlp = 1>
 __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restrict__ qn,
                                                          const uint32_t* __restrict__ qidx,
                                                          uint32_t* __restrict__ counters,
                                                          uint32_t* __restrict__ q64b,
                                                          uint8_t* __restrict__ out,
-                                                         uint32_t compact_min, uint32_t mark) {
+                                                         uint32_t compact_min, uint32_t mark,
+                                                         uint32_t cap) {
   extern __shared__ uint64_t s_tab[];  // mode 4 or kRest 1: 16 x blockDim
-  const uint32_t count = *(volatile uint32_t*)&counters[0];
+  constexpr uint32_t kTask = 32u * kIlp;
+  const uint32_t count_f = *(volatile uint32_t*)&counters[0];
+  const uint32_t count_b = *(volatile uint32_t*)&counters[4];
+  const uint32_t front_pad = (count_f + kTask - 1) / kTask * kTask;
+  const uint32_t vcount = front_pad + count_b;  // virtual positions: front (padded), back
+  const uint32_t back0 = cap - count_b;
   const int lane = threadIdx.x & 31;
-  // 32-survivor tasks: a warp's first task is fixed (global warp w takes
-  // task w), later ones come from counters[3] (zeroed with the queues).  The
-  // launch is one wave of resident blocks, and under a fixed stride the warps
-  // the scheduler favours finish early while the rest run on with the SM
-  // half empty (measured: 27 of 40 warps resident on average).  The next
-  // task's atomic is issued before the current task runs, so its latency is
-  // hidden, and warps without a first task issue none.
-  const uint32_t first_tasks = gridDim.x * (blockDim.x >> 5) * 32u;
-  uint32_t next = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
-  while (next < count) {
-    const uint32_t wbase = next;
-    if (lane == 0) next = first_tasks + atomicAdd(&counters[3], 32u);
-    const uint32_t i = wbase + lane;
-    bool pass = false;
-    uint64_t n = 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 (prime) for lanes past the end
-    if (i < count) {
-      n = qn[i];
-      if (kMode == 4) {
-        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
-        pass = base2_passes_win<kImpl>(n, s_tab + threadIdx.x, (int)blockDim.x, nib);
-      } else if (kMode == 1) {
-        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
-        pass = base2_passes_shift<kImpl>(n, nib);
+  // Tasks: a warp's first task is fixed (global warp w takes task w), later
+  // ones come from counters[3] (zeroed with the queues).  The launch is one
+  // wave of resident blocks, and under a fixed stride the warps the scheduler
+  // favours finish early while the rest run on with the SM half empty
+  // (measured: 27 of 40 warps resident on average).  The next task's atomic
+  // is issued before the current task runs, so its latency is hidden, and
+  // warps without a first task issue none.
+  const uint32_t first_tasks = gridDim.x * (blockDim.x >> 5) * kTask;
+  uint32_t next = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kTask;
+  while (next < vcount) {
+    const uint32_t vbase = next;
+    if (lane == 0) next = first_tasks + atomicAdd(&counters[3], kTask);
+    // queue positions of this lane's values (kIlp of them), valid or not
+    uint32_t pos[kIlp];
+    bool valid[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const uint32_t v = vbase + 32u * u + lane;
+      if (vbase < front_pad) {
+        pos[u] = v;
+        valid[u] = v < count_f;
       } else {
-        pass = base2_passes<kImpl>(n);
+        pos[u] = back0 + (v - front_pad);
+        valid[u] = v < vcount;
       }
     }
-    const unsigned mask = __ballot_sync(0xFFFFFFFFu, pass);
-    if (kRest != 0 && mask && (uint32_t)__popc(mask) >= compact_min) {
-      // dense warp: finishing here costs fewer idle lanes than a queue round trip
-      const uint64_t m = pass ? n : 0xFFFFFFFFFFFFFFC5ull;
-      const bool prime = kRest == 2 ? lucas_warp<kImpl>(m, pass)
-                                    : rest64_is_prime_warp<kImpl>(m, pass, s_tab + threadIdx.x,
-                                                                  (int)blockDim.x);
-      if (prime) out[qidx[i]] = 1;
-    } else if (mask) {
-      const int leader = __ffs(mask) - 1;
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&counters[2], (uint32_t)__popc(mask));
-      base = __shfl_sync(0xFFFFFFFFu, base, leader);
-      if (pass) {
-        q64b[base + __popc(mask & ((1u << lane) - 1u))] = i;
-        if (mark) out[qidx[i]] = 1;  // prime unless a later base clears it (spread rest kernel)
+    bool pass[kIlp];
+    uint64_t n[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      pass[u] = false;
+      n[u] = valid[u] ? qn[pos[u]] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 (prime) when idle
+    }
+    if (kIlp == 2) {
+      const int nib = (int)__reduce_max_sync(
+          0xFFFFFFFFu, (unsigned)max(base2_nibbles(n[0]), base2_nibbles(n[kIlp - 1])));
+      bool p0, p1;
+      base2_passes_shift_x2<kImpl>(n[0], n[kIlp - 1], nib, &p0, &p1);
+      pass[0] = valid[0] && p0;
+      pass[kIlp - 1] = valid[kIlp - 1] && p1;
+    } else if (valid[0]) {
+      if (kMode == 4) {
+        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n[0]));
+        pass[0] = base2_passes_win<kImpl>(n[0], s_tab + threadIdx.x, (int)blockDim.x, nib);
+      } else if (kMode == 1) {
+        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n[0]));
+        pass[0] = base2_passes_shift<kImpl>(n[0], nib);
+      } else {
+        pass[0] = base2_passes<kImpl>(n[0]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const unsigned mask = __ballot_sync(0xFFFFFFFFu, pass[u]);
+      if (kRest != 0 && mask && (uint32_t)__popc(mask) >= compact_min) {
+        // dense warp: finishing here costs fewer idle lanes than a queue round trip
+        const uint64_t m = pass[u] ? n[u] : 0xFFFFFFFFFFFFFFC5ull;
+        const bool prime = kRest == 2 ? lucas_warp<kImpl>(m, pass[u])
+                                      : rest64_is_prime_warp<kImpl>(m, pass[u], s_tab + threadIdx.x,
+                                                                    (int)blockDim.x);
+        if (prime) out[qidx[pos[u]]] = 1;
+      } else if (mask) {
+        const int leader = __ffs(mask) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&counters[2], (uint32_t)__popc(mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (pass[u]) {
+          q64b[base + __popc(mask & ((1u << lane) - 1u))] = pos[u];
+          if (mark) out[qidx[pos[u]]] = 1;  // prime unless a later base clears it (spread rest kernel)
+        }
       }
     }
     next = __shfl_sync(0xFFFFFFFFu, next, 0);
@@ -100,15 +144,16 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
 }
 
 // kLucas: the strong Lucas test (Baillie-PSW with the base-2 stage) instead
-// of the six remaining Miller-Rabin bases.
-template <int kImpl, bool kLucas, bool kSpread>
+// of the six remaining Miller-Rabin bases.  kW: window bits of the six
+// exponentiations (3 or 4; the shared table holds 2^kW values per thread).
+template <int kImpl, bool kLucas, bool kSpread, int kW = kWin>
 __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restrict__ qn,
                                                         const uint32_t* __restrict__ qidx,
                                                         const uint32_t* __restrict__ q64b,
                                                         const uint32_t* __restrict__ counters,
                                                         uint8_t* __restrict__ out,
                                                         uint32_t spread_threads) {
-  extern __shared__ uint64_t s_tab[];  // kTab x blockDim
+  extern __shared__ uint64_t s_tab[];  // 2^kW x blockDim
   uint64_t* tab = s_tab + threadIdx.x;
   const int ld = blockDim.x;
   const uint32_t count = *(volatile const uint32_t*)&counters[2];
@@ -139,7 +184,7 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
         const uint32_t e = valid ? g / f : 0u;
         const uint32_t j = valid ? q64b[e] : 0u;
         const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
-        const bool pass = bases_pass_warp<kImpl>(n, 1 + (int)(g - e * f) * per, per, tab, ld);
+        const bool pass = bases_pass_warp<kImpl, kW>(n, 1 + (int)(g - e * f) * per, per, tab, ld);
         if (valid && !pass) out[qidx[j]] = 0;
       }
       return;
@@ -150,7 +195,8 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
     const bool valid = i < count;
     const uint32_t j = valid ? q64b[i] : 0u;
     const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
-    const bool prime = kLucas ? lucas_warp<kImpl>(n, valid) : rest64_is_prime_warp<kImpl>(n, valid, tab, ld);
+    const bool prime =
+        kLucas ? lucas_warp<kImpl>(n, valid) : rest64_is_prime_warp<kImpl, kW>(n, valid, tab, ld);
     if (kSpread) {
       if (valid && !prime) out[qidx[j]] = 0;
     } else if (prime) {
@@ -179,104 +225,129 @@ static unsigned resident_grid(const void* fn, unsigned block, size_t smem, int s
   return want < cap ? want : cap;
 }
 
+// How the Miller-Rabin stages of one chunk run (from the context's tuning).
+struct MrOpts {
+  int impl = 6;       // Montgomery formulation of the six-base kernel
+  int impl_b2 = 6;    // and of the base-2 kernel
+  int window = 1;     // base-2 schedule (base2_window)
+  int lucas = 0;      // rest_test
+  uint32_t compact_min = 33;
+  int ilp = 1;        // base2_ilp
+  int rest_win = 4;   // rest_window
+};
+
 // Modes 1 and 4 run one wave of resident blocks (the kernel balances the
 // warps itself); the table of mode 4 and the finishing of kRest 1 take
 // 16 x block words of shared memory.
-template <int kImpl, int kMode, int kRest>
+template <int kImpl, int kMode, int kRest, int kIlp>
 static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
                              uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s) {
   const size_t smem = (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t) : 0;
-  const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, kMode, kRest>);
+  const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, kMode, kRest, kIlp>);
   grid = resident_grid(fn, block, smem, sm_count, grid);
-  mr64_base2_kernel<kImpl, kMode, kRest><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.counters,
-                                                                   q.q64b, out, compact_min, mark);
+  mr64_base2_kernel<kImpl, kMode, kRest, kIlp><<<grid, block, smem, s>>>(
+      q.q64_n, q.q64_idx, q.counters, q.q64b, out, compact_min, mark, (uint32_t)q.capacity);
 }
 
 template <int kImpl, int kMode>
 static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
-                              int lucas, uint32_t compact_min, uint32_t mark, int sm_count,
-                              cudaStream_t s) {
-  if (compact_min > 32)
-    launch_base2_win<kImpl, kMode, 0>(q, out, grid, block, compact_min, mark, sm_count, s);
-  else if (lucas == 1)
-    launch_base2_win<kImpl, kMode, 2>(q, out, grid, block, compact_min, mark, sm_count, s);
-  else
-    launch_base2_win<kImpl, kMode, 1>(q, out, grid, block, compact_min, mark, sm_count, s);
+                              const MrOpts& o, uint32_t mark, int sm_count, cudaStream_t s) {
+  if (o.compact_min > 32) {
+    // two survivors per thread: formulation 6, estimated-quotient windows
+    if ((kImpl == 6 || kImpl == 16) && kMode == 1 && o.ilp == 2)
+      launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+    else
+      launch_base2_win<kImpl, kMode, 0, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+  } else if (o.lucas == 1) {
+    launch_base2_win<kImpl, kMode, 2, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+  } else {
+    launch_base2_win<kImpl, kMode, 1, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+  }
 }
 
 template <int kImpl>
-static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int window,
-                         int lucas, uint32_t compact_min, uint32_t mark, int sm_count,
-                         cudaStream_t s) {
-  if (window == 4) {
-    launch_base2_mode<kImpl, 4>(q, out, grid, block, lucas, compact_min, mark, sm_count, s);
-  } else if (window == 1) {
-    launch_base2_mode<kImpl, 1>(q, out, grid, block, lucas, compact_min, mark, sm_count, s);
+static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+                         const MrOpts& o, uint32_t mark, int sm_count, cudaStream_t s) {
+  if (o.window == 4) {
+    launch_base2_mode<kImpl, 4>(q, out, grid, block, o, mark, sm_count, s);
+  } else if (o.window == 1) {
+    launch_base2_mode<kImpl, 1>(q, out, grid, block, o, mark, sm_count, s);
   } else {
-    mr64_base2_kernel<kImpl, 0, 0><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.counters,
-                                                          q.q64b, out, 33u, mark);
+    mr64_base2_kernel<kImpl, 0, 0><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.counters, q.q64b,
+                                                          out, 33u, mark, (uint32_t)q.capacity);
   }
 }
 
 // spread_grid > 0: launch the variant that spreads (survivor, base) pairs
 // over the threads whenever the queue is at most a sixth of its threads.
-template <int kImpl>
-static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int lucas,
-                        unsigned spread_grid, int sm_count, cudaStream_t s) {
-  const size_t smem = (size_t)kTab * block * sizeof(uint64_t);
-  if (lucas) {
-    mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
-                                                                out, 0u);
-  } else if (spread_grid) {
+template <int kImpl, int kW>
+static void launch_rest_w(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+                          unsigned spread_grid, int sm_count, cudaStream_t s) {
+  const size_t smem = ((size_t)1 << kW) * block * sizeof(uint64_t);
+  if (spread_grid) {
     // at most the blocks that can be resident: more would only queue up (and
     // cost their launch when the queue is empty)
     const uint32_t spread_threads = spread_grid * block;
-    const void* fn = reinterpret_cast<const void*>(&mr64_rest_kernel<kImpl, false, true>);
+    const void* fn = reinterpret_cast<const void*>(&mr64_rest_kernel<kImpl, false, true, kW>);
     const unsigned g = resident_grid(fn, block, smem, sm_count, spread_grid);
-    mr64_rest_kernel<kImpl, false, true><<<g, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
-                                                                out, spread_threads);
+    mr64_rest_kernel<kImpl, false, true, kW><<<g, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
+                                                                    q.counters, out, spread_threads);
   } else {
-    mr64_rest_kernel<kImpl, false, false><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
-                                                                   q.counters, out, 0u);
+    mr64_rest_kernel<kImpl, false, false, kW><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
+                                                                       q.counters, out, 0u);
+  }
+}
+
+template <int kImpl>
+static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+                        const MrOpts& o, unsigned spread_grid, int sm_count, cudaStream_t s) {
+  if (o.lucas) {
+    mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
+                                                                out, 0u);
+  } else if ((kImpl == 6 || kImpl == 17) && o.rest_win == 3) {
+    launch_rest_w<kImpl, 3>(q, out, grid, block, spread_grid, sm_count, s);
+  } else {
+    launch_rest_w<kImpl, kWin>(q, out, grid, block, spread_grid, sm_count, s);
   }
 }
 
 // impl_b2 selects the arithmetic of the base-2 kernel, impl that of the
 // six-base kernel (see MontOps).
-static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned block, int impl,
-                       int impl_b2, int window, int lucas, uint32_t compact_min, int sm_count,
-                       unsigned spread_grid, cudaStream_t s, isprime_ctx* ctx) {
+static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
+                       const MrOpts& o, int sm_count, unsigned spread_grid, cudaStream_t s,
+                       isprime_ctx* ctx) {
   int st = ISPRIME_OK;
   TimedLaunch tl;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_BASE2, s, &tl))) return st;
-  const uint32_t cm = compact_min;
   // the spread rest kernel clears survivors that a later base rejects, so the
   // base-2 kernel marks its survivors prime first
-  const uint32_t mark = (spread_grid != 0 && lucas != 1) ? 1u : 0u;
-  if (lucas == 1) spread_grid = 0;
-  switch (impl_b2) {
-    case 1: launch_base2<1>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    case 2: launch_base2<2>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    case 3: launch_base2<3>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    case 4: launch_base2<4>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    case 5: launch_base2<5>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    case 6: launch_base2<6>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    case 7: launch_base2<7>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    case 8: launch_base2<8>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
-    default: launch_base2<0>(q, out, grid, block, window, lucas, cm, mark, sm_count, s); break;
+  const uint32_t mark = (spread_grid != 0 && o.lucas != 1) ? 1u : 0u;
+  if (o.lucas == 1) spread_grid = 0;
+  switch (o.impl_b2) {
+    case 1: launch_base2<1>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 2: launch_base2<2>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 3: launch_base2<3>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 4: launch_base2<4>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 5: launch_base2<5>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 6: launch_base2<6>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 7: launch_base2<7>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 8: launch_base2<8>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 16: launch_base2<16>(q, out, grid, block, o, mark, sm_count, s); break;
+    default: launch_base2<0>(q, out, grid, block, o, mark, sm_count, s); break;
   }
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
-  switch (impl) {
-    case 1: launch_rest<1>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    case 2: launch_rest<2>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    case 3: launch_rest<3>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    case 4: launch_rest<4>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    case 5: launch_rest<5>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    case 6: launch_rest<6>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    case 7: launch_rest<7>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    case 8: launch_rest<8>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
-    default: launch_rest<0>(q, out, grid, block, lucas, spread_grid, sm_count, s); break;
+  switch (o.impl) {
+    case 1: launch_rest<1>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 2: launch_rest<2>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 3: launch_rest<3>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 4: launch_rest<4>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 5: launch_rest<5>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 6: launch_rest<6>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 7: launch_rest<7>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 8: launch_rest<8>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 17: launch_rest<17>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    default: launch_rest<0>(q, out, grid, block, o, spread_grid, sm_count, s); break;
   }
   if (ctx) st = launch_end(ctx, s, &tl, "mr64_rest_kernel");
   return st;
@@ -303,10 +374,19 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
     mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
-  return launch_mr64(q, out, grid, block, (int)ctx->tune.mont_impl,
-                     (int)ctx->tune.mont_impl_base2, (int)ctx->tune.base2_window,
-                     (int)ctx->tune.rest_test, ctx->tune.compact_min, ctx->sm_count, spread_grid,
-                     s, ctx);
+  MrOpts o;
+  o.impl = (int)ctx->tune.mont_impl;
+  o.impl_b2 = (int)ctx->tune.mont_impl_base2;
+  o.window = (int)ctx->tune.base2_window;
+  o.lucas = (int)ctx->tune.rest_test;
+  o.compact_min = ctx->tune.compact_min;
+  o.ilp = (int)ctx->tune.base2_ilp;
+  o.rest_win = (int)ctx->tune.rest_window;
+  if (ctx->count_ops) {  // isprime_count_ops: formulation 6 with its operations counted
+    o.impl_b2 = 16;
+    o.impl = 17;
+  }
+  return launch_mr64(q, out, grid, block, o, ctx->sm_count, spread_grid, s, ctx);
 }
 
 // Launch without a context (explicit grid and block and queue pointers);
@@ -316,10 +396,31 @@ int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, 
   if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
   // Montgomery formulation 6; base 2 by the binary schedule (its launch needs
   // no occupancy query, so no SM count)
-  launch_mr64(q, out, grid, block, 6, 6, /*window=*/0, /*lucas=*/0, /*compact_min=*/33,
-              /*sm_count=*/0, /*spread_grid=*/0, s, nullptr);
+  MrOpts o;
+  o.window = 0;
+  launch_mr64(q, out, grid, block, o, /*sm_count=*/0, /*spread_grid=*/0, s, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
+}
+
+// The operation counters of this translation unit (arith.cuh, g_ip_ops):
+// out receives [stage][kind][warp issues, active lanes] summed over the
+// spread copies; reset clears them.  Synchronous on the current device.
+int op_counts_read(unsigned long long out[2][kOpKinds][2], bool reset) {
+  unsigned long long h[2][kOpKinds][2][kOpSpread];
+  IP_CUDA(cudaMemcpyFromSymbol(h, g_ip_ops, sizeof h));
+  for (int st = 0; st < 2; ++st)
+    for (int k = 0; k < kOpKinds; ++k)
+      for (int j = 0; j < 2; ++j) {
+        unsigned long long t = 0;
+        for (int i = 0; i < kOpSpread; ++i) t += h[st][k][j][i];
+        out[st][k][j] = t;
+      }
+  if (reset) {
+    memset(h, 0, sizeof h);
+    IP_CUDA(cudaMemcpyToSymbol(g_ip_ops, h, sizeof h));
+  }
+  return ISPRIME_OK;
 }
 
 }  // namespace ip

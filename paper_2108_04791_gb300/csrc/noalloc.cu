@@ -5,12 +5,19 @@
 // (a memory pool that owns the whole device), a callback or hook that must
 // not block on the CUDA driver's allocation lock, or a process whose device
 // memory is fully handed out in advance.  isprime_u64_noalloc serves them:
-// it runs the same kernels as isprime_u64 but keeps its work queues in one
-// fixed array of device memory that is part of the library image (every GPU
-// that loads the library holds it until the process exits), and it uses no
-// sieve (values below 2^32 go through trial division and the 32-bit
-// Miller-Rabin bases {2, 7, 61}).  It calls no cudaMalloc, cudaFree or any
-// other allocating routine.
+// it runs the classify and Miller-Rabin code of isprime_u64 (with the binary
+// base-2 schedule, one queue region, and the six-base kernel without the
+// variant that spreads short queues over threads) but keeps its work queues
+// in one fixed array of device memory that is part of the library image
+// (every GPU that loads the library holds it until the process exits), and
+// it uses no sieve (values below 2^32 go through trial division and the
+// 32-bit Miller-Rabin bases {2, 7, 61}).  It calls no cudaMalloc, cudaFree or
+// any other allocating routine.
+//
+// The array's device address is looked up once per device and kept for the
+// life of the process; a cudaDeviceReset (or anything else that destroys the
+// device's primary context) invalidates it, so the entry point must not be
+// used on a device after such a reset.
 //
 // Limits and sharing: at most kNoallocMaxElems elements per call; every
 // call on a device uses the same array, which keeps the last call's
@@ -24,8 +31,8 @@ namespace ip {
 
 constexpr size_t kNoallocMaxElems = (size_t)1 << 20;  // ISPRIME_NOALLOC_MAX_ELEMS
 
-// Queue storage for kNoallocMaxElems elements, 24 bytes each, plus four
-// 32-bit counters at the end: 24 MiB + 256 B.
+// Queue storage for kNoallocMaxElems elements, 24 bytes each, plus the
+// 32-bit queue counters (kQueueCounters of them) at the end: 24 MiB + 256 B.
 constexpr size_t kNoallocQ64N = 0;                                   // u64 values
 constexpr size_t kNoallocQ64Idx = kNoallocQ64N + 8 * kNoallocMaxElems;  // u32 indices
 constexpr size_t kNoallocQ64B = kNoallocQ64Idx + 4 * kNoallocMaxElems;  // u32 positions
@@ -98,7 +105,7 @@ extern "C" int isprime_u64_noalloc(const uint64_t* d_in, uint8_t* d_out, size_t 
   q.counters = reinterpret_cast<uint32_t*>(d.scratch + kNoallocCounters);
   q.capacity = kNoallocMaxElems;
   // The counters keep the previous call's values: start them at zero.
-  e = cudaMemsetAsync(q.counters, 0, 4 * sizeof(uint32_t), s);
+  e = cudaMemsetAsync(q.counters, 0, kQueueCounters * sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
 
   constexpr uint32_t kTdPrimes = 15;  // 3..53, as in the default tuning
@@ -116,8 +123,12 @@ extern "C" int isprime_u64_noalloc(const uint64_t* d_in, uint8_t* d_out, size_t 
   a.q32_idx = q.q32_idx;
   a.counters = q.counters;
   a.invalid = nullptr;
+  a.invalid_ctx = nullptr;
   a.head = ((uintptr_t)d_in % 16) ? 1u : 0u;
   a.pair_store = (((uintptr_t)(d_out + a.head)) % 2 == 0) ? 1u : 0u;
+  a.q64_cap = (uint32_t)q.capacity;
+  a.fold = 0;
+  a.split = 0;
   const unsigned block = 256;
   const uint64_t npairs = (n - a.head) / 2;
   const uint64_t want = (npairs + 4 * block - 1) / (4 * block);  // 4 pairs per thread per tile

@@ -245,7 +245,7 @@ int range_run(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out, cud
   while (done < count) {
     const uint64_t c_lo = lo + done;
     const uint64_t c_n = std::min(count - done, chunk);
-    IP_CUDA(cudaMemsetAsync(ctx->q.counters, 0, 4 * sizeof(uint32_t), s));
+    IP_CUDA(cudaMemsetAsync(ctx->q.counters, 0, kQueueCounters * sizeof(uint32_t), s));
     RangeArgs a{};
     a.lo = c_lo;
     a.count = c_n;

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kSmallBlock) small_kernel(const T* __restrict_
                                                             uint8_t* __restrict__ out, uint64_t n,
                                                             const uint32_t* __restrict__ sieve,
                                                             uint64_t S,
-                                                            unsigned long long* invalid) {
+                                                            unsigned long long* invalid,
+                                                            unsigned long long* invalid_ctx) {
   const int lane = threadIdx.x & 31;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   uint32_t bad = 0;
@@ -111,7 +112,10 @@ __global__ void __launch_bounds__(kSmallBlock) small_kernel(const T* __restrict_
       bad += ok ? 0 : 1;
     }
   }
-  if (invalid && lane == 0 && bad) atomicAdd(invalid, (unsigned long long)bad);
+  if (lane == 0 && bad) {
+    if (invalid) atomicAdd(invalid, (unsigned long long)bad);
+    if (invalid_ctx) atomicAdd(invalid_ctx, (unsigned long long)bad);
+  }
 }
 
 template <int kCap>
@@ -160,17 +164,19 @@ int launch_small_u64(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, siz
   int st = launch_begin(ctx, ISPRIME_K_SMALL, s, &tl);
   if (st) return st;
   small_kernel<uint64_t><<<small_grid(ctx, n), kSmallBlock, 0, s>>>(d_in, d_out, n, ctx->d_sieve,
-                                                                    sieve_cut(ctx), nullptr);
+                                                                    sieve_cut(ctx), nullptr, nullptr);
   return launch_end(ctx, s, &tl, "small_kernel<u64>");
 }
 
 int launch_small_f64(isprime_ctx* ctx, const double* d_in, uint8_t* d_out, size_t n,
-                     unsigned long long* d_invalid, cudaStream_t s) {
+                     unsigned long long* d_invalid, unsigned long long* d_invalid_ctx,
+                     cudaStream_t s) {
   TimedLaunch tl;
   int st = launch_begin(ctx, ISPRIME_K_SMALL, s, &tl);
   if (st) return st;
   small_kernel<double><<<small_grid(ctx, n), kSmallBlock, 0, s>>>(d_in, d_out, n, ctx->d_sieve,
-                                                                  sieve_cut(ctx), d_invalid);
+                                                                  sieve_cut(ctx), d_invalid,
+                                                                  d_invalid_ctx);
   return launch_end(ctx, s, &tl, "small_kernel<f64>");
 }
 

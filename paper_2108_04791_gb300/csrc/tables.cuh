@@ -71,4 +71,25 @@ constexpr TdTable make_td_table() {
 
 constexpr TdTable kTdHost = make_td_table();
 
+// Folded trial division.  For k bits, 2^k = 1 (mod 2^k - 1), so the sum of
+// the k-bit chunks of n is congruent to n modulo 2^k - 1, and modulo every
+// prime p dividing 2^k - 1.  With k = 32, 24, 20 and 28 that sum fits in 32
+// bits, so p | n is decided by the 32-bit multiply-by-inverse test on it (one
+// low multiply) instead of the 64-bit one (a wide and two low multiplies):
+//   2^32 - 1 = 3 * 5 * 17 * 257 * 65537
+//   2^24 - 1 = 3^2 * 5 * 7 * 13 * 17 * 241
+//   2^20 - 1 = 3 * 5^2 * 11 * 31 * 41
+//   2^28 - 1 = 3 * 5 * 29 * 43 * 113 * 127
+// kFoldOf[i] is the k whose chunk sum serves the i-th odd prime at fold level
+// 2 (0: the 64-bit test); level 1 leaves out k = 28.  The shifts, masks and
+// adds of the folds run on the ALU pipe, the tests they replace on the
+// multiply pipe, so the level trades one pipe's work for the other's.
+constexpr int kFoldPrimes = 15;  // 3 .. 53
+constexpr int kFoldOf[kFoldPrimes] = {32, 32, 24, 20, 24, 32, 0, 0, 28, 20, 0, 20, 28, 0, 0};
+constexpr int fold_width(int i, int level) {
+  return (i >= kFoldPrimes || level <= 0) ? 0
+         : (kFoldOf[i] == 28 && level < 2) ? 0
+                                            : kFoldOf[i];
+}
+
 }  // namespace ip

@@ -87,7 +87,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     src.write_text('#include "isprime.h"\n#include <stdio.h>\n'
                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(isprime_tuning),'
                    ' sizeof(isprime_stats), sizeof(isprime_kernel_time), sizeof(isprime_int_rates),'
-                   ' sizeof(isprime_array)); printf("%zu\\n", sizeof(isprime_server_stats)); return 0;}\n')
+                   ' sizeof(isprime_array)); printf("%zu\\n", sizeof(isprime_server_stats));'
+                   ' printf("%zu\\n", sizeof(isprime_op_counts)); return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
                    check=True)
@@ -95,4 +96,4 @@ def test_struct_layouts_match_the_header(tmp_path):
                                             check=True).stdout.split()]
     assert sizes == [ctypes.sizeof(ipg.Tuning), ctypes.sizeof(ipg._Stats), ctypes.sizeof(ipg._KTime),
                      ctypes.sizeof(ipg._IntRates), ctypes.sizeof(ipg.ArrayDesc),
-                     ctypes.sizeof(ipg._ServerStats)]
+                     ctypes.sizeof(ipg._ServerStats), ctypes.sizeof(ipg._OpCounts)]

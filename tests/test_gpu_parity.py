@@ -81,17 +81,6 @@ def test_plain_mixed_2p22():
     _assert_same(v, _gpu(v), oracle.isprime_u64(v))
 
 
-def test_plain_mixed_full_size_sampled():
-    """Full 2^26 elements on the GPU; every 61st element checked by the oracle."""
-    v = plain_mixed()
-    got = _gpu(v)
-    idx = np.arange(0, v.size, 61)
-    _assert_same(v[idx], got[idx], oracle.isprime_u64(v[idx]))
-    # prime density property over the whole array (Mertens-style sanity)
-    frac = got.mean()
-    assert 0.02 < frac < 0.2
-
-
 def test_mixed_doubles():
     x = mixed_doubles(1 << 20)
     t = torch.from_numpy(x).to(_dev())
@@ -120,6 +109,63 @@ def test_f64_domain_and_invalid_count(ctx_small_sieve):
             assert int(inv.item()) == bad
     finally:
         ctx_small_sieve.set_tuning(small_max=old)
+
+
+def _f64_call(ctx, x, stream=None, invalid=None):
+    """isprime_f64_ctx through the C ABI; returns the output bytes."""
+    import ctypes
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(_dev())
+    out = torch.empty(t.numel(), dtype=torch.uint8, device=_dev())
+    s = stream or torch.cuda.current_stream(_dev())
+    st = ipg.lib().isprime_f64_ctx(ctx.handle, t.data_ptr(), out.data_ptr(), t.numel(),
+                                   None if invalid is None else ctypes.c_void_p(invalid.data_ptr()),
+                                   ctypes.c_void_p(s.cuda_stream))
+    assert st == ipg.OK, st
+    return t, out
+
+
+@pytest.mark.parametrize("small_max", [0, 1 << 20])
+def test_f64_sync_status_reports_edomain(small_max):
+    """The EDOMAIN contract: invalid doubles (NaN, infinities, negatives,
+    fractions, values above 2^53) are counted by the context itself even when
+    the caller passes no counter, and isprime_f64_sync_status returns
+    ISPRIME_EDOMAIN with that count, then resets it.  Calls on two streams
+    are both counted.  Checked on the queue path (small_max 0) and on the
+    one-launch path."""
+    import ctypes
+    L = ipg.lib()
+    good = np.array([2.0, 3.0, 97.0, 2.0**53 - 111, 0.0], dtype=np.float64)
+    bad = np.array([float("nan"), -1.0, 2.5, 2.0**53 + 2, float("inf"), 1e300, 7.0],
+                   dtype=np.float64)
+    with ipg.Context(0, sieve_limit=1 << 24) as c:
+        c.set_tuning(small_max=small_max)
+        cnt = ctypes.c_ulonglong(99)
+        assert L.isprime_f64_sync_status(c.handle, ctypes.byref(cnt)) == ipg.OK
+        assert cnt.value == 0
+        _, out = _f64_call(c, good)  # no invalid element: still OK
+        assert L.isprime_f64_sync_status(c.handle, ctypes.byref(cnt)) == ipg.OK and cnt.value == 0
+        assert out.cpu().numpy().tolist() == oracle.isprime_f64(good)[0].tolist()
+        s2 = torch.cuda.Stream(_dev())
+        keep = [_f64_call(c, bad), _f64_call(c, np.concatenate([bad, good]), stream=s2)]
+        want_bad = oracle.isprime_f64(bad)[1]
+        assert want_bad == 6
+        assert L.isprime_f64_sync_status(c.handle, ctypes.byref(cnt)) == ipg.EDOMAIN
+        assert cnt.value == 2 * want_bad
+        assert b"2^53" in L.isprime_last_error()
+        # the status call reset the count
+        assert L.isprime_f64_sync_status(c.handle, None) == ipg.OK
+        # a caller's counter and the context's count agree
+        inv = torch.zeros(1, dtype=torch.int64, device=_dev())
+        keep.append(_f64_call(c, bad, invalid=inv))
+        assert c.f64_status() == want_bad
+        torch.cuda.synchronize()
+        assert int(inv.item()) == want_bad
+        for (t, out), x in zip(keep, [bad, np.concatenate([bad, good]), bad]):
+            assert out.cpu().numpy().tolist() == oracle.isprime_f64(x)[0].tolist()
+        # the u64 path never counts
+        _gpu(np.array([1, 2, 3], dtype=np.uint64), c)
+        assert c.f64_status() == 0
+    assert L.isprime_f64_sync_status(None, None) == ipg.EINVAL
 
 
 # ------------------------------------------------------------------ edge cases
@@ -378,15 +424,19 @@ def test_batched_short_batch_takes_the_warp_form(n_arrays):
                 assert (rec["small"][1], rec["batched"][1]) == ((1, 0) if small_max else (0, 1))
 
 
-def test_batched_equals_plain_calls():
+def test_batched_and_plain_calls_match_oracle():
+    """The same arrays (empty, one value, ragged) through one batched launch
+    and through one plain call each: both equal the oracle."""
     vals = plain_mixed(1 << 18, seed=63)
     parts = np.split(vals, [1, 10, 1000, 50000, 50001])
     c = ipg.Context.default(0)
     outs = c.isprime_batched([_to_dev(p) for p in parts])
     plain = [_gpu(p, c) if p.size else np.zeros(0, np.uint8) for p in parts]
     torch.cuda.synchronize()
-    for o, p in zip(outs, plain):
-        assert np.array_equal(o.cpu().numpy(), p)
+    for o, p, v in zip(outs, plain, parts):
+        want = oracle.isprime_u64(v)
+        _assert_same(v, o.cpu().numpy(), want)
+        _assert_same(v, p, want)
 
 
 # ------------------------------------------------------------------ autotuner

@@ -1,0 +1,160 @@
+"""GPU parity of the kernel variants selected by tuning: folded trial
+division (td_fold), the base-2 queue split by s (base2_split), two survivors
+per thread in the base-2 kernel (base2_ilp) and 3-bit windows in the
+six-base kernel (rest_window).
+
+None of them may change a result, so every combination is compared with the
+CPU oracle bit for bit, on inputs that reach every branch they touch: values
+of every bit size from 33 to 64 (s = 1 and s >= 2, all fold residues),
+primes and their neighbours, the odd values just above 2^32 and just below
+2^64, multiples of every trial prime near 2^64, base-2 strong pseudoprimes
+near 2^63 (they must reach the six-base kernel), ragged lengths, a
+misaligned input pointer, several chunks per call, and the host-buffer path.
+"""
+import itertools
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import numtheory as nt
+from workloads import plain_large, plain_mixed
+from workloads.generators import load_pool
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+import paper_2108_04791_gb300 as ipg  # noqa: E402
+
+TRIAL_PRIMES = [3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53]
+
+
+def _spsp_near_2p63(count, seed):
+    rng = random.Random(seed)
+    out = []
+    while len(out) < count:  # p (2p - 1) with both prime, near 2^63, that pass base 2
+        p = rng.randrange(2**31, 3_000_000_000) | 1
+        q = 2 * p - 1
+        if nt.trial_is_prime(p) and nt.trial_is_prime(q) and nt.strong_base2(p * q):
+            out.append(p * q)
+    return out
+
+
+def _inputs():
+    rng = np.random.default_rng(2024)
+    cand = np.concatenate([rng.integers(1 << (b - 1), (1 << b) - 1, size=1200, dtype=np.uint64,
+                                        endpoint=True) | np.uint64(1) for b in range(33, 65)])
+    primes = cand[oracle.isprime_u64(cand).astype(bool)]
+    near = primes[primes < np.uint64(2**64 - 2)] + np.uint64(2)
+    # p * k near 2^64 and just above 2^32 for every trial prime: each fold must see them
+    mult = []
+    for p in TRIAL_PRIMES:
+        top = (2**64 - 1) // p
+        mult += [p * (top - j) for j in range(40)]
+        low = (2**32) // p + 1
+        mult += [p * (low + j) for j in range(40)]
+        mult += [p * p * (((2**61) // (p * p)) + j) for j in range(10)]
+    edges = (list(range(2**32 + 1, 2**32 + 300, 2)) + list(range(2**64 - 299, 2**64, 2))
+             + _spsp_near_2p63(24, seed=7) + [2**61 - 1, 2**64 - 59, 3215031751, 4759123141])
+    v = np.concatenate([cand, near, np.array(mult + edges, dtype=np.uint64),
+                        plain_large(20_000, seed=91), plain_mixed(20_000, seed=92)])
+    rng.shuffle(v)
+    return v
+
+
+@pytest.fixture(scope="module")
+def data():
+    v = _inputs()
+    return v, oracle.isprime_u64(v)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    with ipg.Context(0, sieve_limit=1 << 24) as c:
+        yield c
+
+
+def _run(c, v):
+    t = torch.from_numpy(np.ascontiguousarray(v).view(np.int64)).to("cuda:0")
+    out = c.isprime(t)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _same(v, got, want, what):
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (f"{what}: {bad.size} mismatches; first n={int(v[bad[0]])} "
+                           f"gpu={int(got[bad[0]])} oracle={int(want[bad[0]])}")
+
+
+COMBOS = list(itertools.product([0, 1, 2], [0, 1], [1, 2], [3, 4]))
+
+
+@pytest.mark.parametrize("fold,split,ilp,win", COMBOS)
+def test_variant_matches_oracle(fold, split, ilp, win, data, ctx):
+    v, want = data
+    ctx.set_tuning(td_fold=fold, base2_split=split, base2_ilp=ilp, rest_window=win, small_max=0,
+                   td_primes=15, chunk_log2=24, mont_impl=6, mont_impl_base2=6, base2_window=1,
+                   compact_min=33)
+    _same(v, _run(ctx, v), want, f"fold={fold} split={split} ilp={ilp} win={win}")
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 63, 65, 1023, 4097, 70001])
+def test_variants_on_ragged_and_misaligned(n, data, ctx):
+    """Odd lengths, lengths around a warp task (32 and 64 survivors), and an
+    input that starts 8 bytes past a 16-byte boundary."""
+    v, want = data
+    ctx.set_tuning(td_fold=2, base2_split=1, base2_ilp=2, rest_window=3, small_max=0,
+                   chunk_log2=24)
+    _same(v[:n], _run(ctx, v[:n]), want[:n], f"n={n}")
+    t = torch.from_numpy(np.ascontiguousarray(v[:n + 1]).view(np.int64)).to("cuda:0")
+    out = ctx.isprime(t[1:])
+    torch.cuda.synchronize()
+    _same(v[1:n + 1], out.cpu().numpy(), want[1:n + 1], f"misaligned n={n}")
+
+
+def test_variants_over_several_chunks(data, ctx):
+    """chunk_log2 = 16: the array runs as several chunks on one queue set, so
+    both q64 regions are refilled from zero for every chunk."""
+    v, want = data
+    ctx.set_tuning(td_fold=2, base2_split=1, base2_ilp=2, rest_window=3, small_max=0,
+                   chunk_log2=16)
+    try:
+        _same(v, _run(ctx, v), want, "chunk_log2=16")
+    finally:
+        ctx.set_tuning(chunk_log2=24)
+
+
+def test_variants_on_the_host_path(data, ctx):
+    """isprime_u64_host runs the same stages on its two staging slots' own queues."""
+    v, want = data
+    ctx.set_tuning(td_fold=1, base2_split=1, base2_ilp=2, rest_window=3, small_max=0,
+                   chunk_log2=16)
+    try:
+        _same(v, ctx.isprime_host(v), want, "host path")
+    finally:
+        ctx.set_tuning(chunk_log2=24)
+
+
+def test_variants_with_spread_rest_kernel(ctx):
+    """Short queues take the six-base kernel that spreads (survivor, base)
+    pairs over threads; its 3-bit-window form with the split base-2 queue."""
+    rng = random.Random(5)
+    pool = [int(x) for x in load_pool("primes_near_2p64.txt")[:500]]
+    for n in (7, 64, 1000, 9000):
+        vals = [rng.choice(pool) for _ in range(n // 2)] + _spsp_near_2p63(4, seed=n)
+        vals += [int(x) for x in plain_large(n - len(vals), seed=n)]
+        v = np.array(vals, dtype=np.uint64)
+        want = oracle.isprime_u64(v)
+        for win in (3, 4):
+            ctx.set_tuning(td_fold=2, base2_split=1, base2_ilp=1, rest_window=win, small_max=0)
+            _same(v, _run(ctx, v), want, f"spread n={n} win={win}")
+
+
+def test_tuning_rejects_out_of_range_variant_fields(ctx):
+    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
+               dict(rest_window=5), dict(rest_window=2)):
+        with pytest.raises(ipg.IsPrimeError):
+            ctx.set_tuning(**kw)

@@ -131,3 +131,65 @@ def test_mutant_is_caught(tmp_path, name):
     assert src.count(old) == 1, f"mutation site for {name} not unique"
     L = _build(src.replace(old, new), tmp_path, name)
     assert _battery(L), f"mutant {name} survived every pin"
+
+
+# Mistakes in the work counter alone (the primality results stay right, so
+# only the exact counts of test_oracle_pins.py can see them).
+WORK_MUTANTS = {
+    "tail_squaring_not_counted": ("    x = oracle_mulmod(x, x, n);\n    if (sq) ++*sq;",
+                                  "    x = oracle_mulmod(x, x, n);"),
+    "multiply_counted_as_squaring": ("      if (mu) ++*mu;", "      if (sq) ++*sq;"),
+    "base_counts_start_at_one": ("uint64_t sq = 0, mu = 0;", "uint64_t sq = 1, mu = 0;"),
+    "trial_bound_exclusive": ("odd_primes[k] <= td_bound", "odd_primes[k] < td_bound"),
+}
+
+WORK_KEYS = ("mr64_elements", "base2_squarings", "base2_doublings", "base2_passes",
+             "rest_squarings", "rest_multiplies", "base_tests", "trial_tests",
+             "mr32_elements", "primes")
+
+
+def _work(L, n):
+    a = np.array([n], dtype=np.uint64)
+    c = np.zeros(len(WORK_KEYS), dtype=np.uint64)
+    L.oracle_work_counts(a.ctypes.data, 1, 53, 1 << 32, c.ctypes.data)
+    return dict(zip(WORK_KEYS, (int(x) for x in c)))
+
+
+def _work_battery(L):
+    """The exact counts pinned by hand in test_oracle_pins.py."""
+    L.oracle_work_counts.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
+                                     ctypes.c_uint64, ctypes.c_void_p]
+    L.oracle_work_counts.restype = None
+    failed = []
+    w = _work(L, 2**32 + 1)
+    if (w["base2_squarings"], w["base2_doublings"], w["trial_tests"]) != (5, 0, 15):
+        failed.append("F5")
+    w = _work(L, 2**40 + 1)
+    if (w["base2_squarings"], w["base_tests"]) != (39, 1):
+        failed.append("2^40+1")
+    w = _work(L, 2**61 - 1)
+    if (w["base2_squarings"], w["base2_doublings"], w["rest_squarings"],
+            w["rest_multiplies"]) != (59, 59, 354, 354):
+        failed.append("2^61-1")
+    p = 2**40 + 141
+    nonres = sum(1 for a in [325, 9375, 28178, 450775, 9780504, 1795265022]
+                 if pow(a, (p - 1) // 2, p) == p - 1)
+    w = _work(L, p)
+    if (w["base2_squarings"], w["base2_doublings"], w["rest_squarings"],
+            w["rest_multiplies"]) != (39, 3, 228 + nonres, 18):
+        failed.append("2^40+141")
+    return failed
+
+
+def test_unmutated_counter_passes(tmp_path):
+    L = _build(open(SRC).read(), tmp_path, "orig_work")
+    assert _work_battery(L) == []
+
+
+@pytest.mark.parametrize("name", sorted(WORK_MUTANTS))
+def test_counter_mutant_is_caught(tmp_path, name):
+    old, new = WORK_MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    L = _build(src.replace(old, new), tmp_path, "w_" + name)
+    assert _work_battery(L), f"counter mutant {name} survived every exact count"

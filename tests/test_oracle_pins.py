@@ -303,3 +303,49 @@ def test_work_counter_exact_on_one_prime():
     assert w["base2_squarings"] == 59 and w["base2_doublings"] == 59
     assert w["rest_squarings"] == 6 * 59 and w["rest_multiplies"] == 6 * 59
     assert w["base_tests"] == 7 and w["trial_tests"] == 15
+
+
+def test_work_counter_exact_fermat_f5():
+    """n = F5 = 2^32 + 1 = 641 * 6700417 (no factor <= 53): n - 1 = 2^32, so
+    s = 32 and d = 1.  Base 2: a^d = 2 needs no squaring or multiplication,
+    then the tail squares 2 -> 4 -> 16 -> 256 -> 65536 -> 2^32 = -1 (mod n):
+    exactly 5 squarings, and F5 passes base 2 (a base-2 strong pseudoprime)."""
+    w = oracle.work_counts(np.array([2**32 + 1], dtype=np.uint64), td_bound=53)
+    assert w["trial_tests"] == 15 and w["mr64_elements"] == 1
+    assert w["base2_squarings"] == 5 and w["base2_doublings"] == 0
+    assert w["base2_passes"] == 1 and w["primes"] == 0
+    # the other bases: d = 1 again, so their whole work is tail squarings, at
+    # most s - 1 = 31 per base, and the composite fails at one of them
+    assert w["rest_multiplies"] == 0
+    assert 2 <= w["base_tests"] <= 7
+    assert w["rest_squarings"] <= 31 * (w["base_tests"] - 1)
+
+
+def test_work_counter_exact_composite_full_tail():
+    """n = 2^40 + 1 = 257 * 4278255361 (no factor <= 53): s = 40, d = 1.  The
+    order of 2 mod n is 80 (2^40 = -1), and 2^(2^r) = -1 would need
+    2^r = 40 (mod 80), = 1 would need 2^r = 0 (mod 80); neither happens, so
+    the tail runs all s - 1 = 39 squarings and n fails base 2 there."""
+    w = oracle.work_counts(np.array([2**40 + 1], dtype=np.uint64), td_bound=53)
+    assert w["mr64_elements"] == 1 and w["base_tests"] == 1
+    assert w["base2_squarings"] == 39 and w["base2_doublings"] == 0
+    assert w["base2_passes"] == 0 and w["rest_squarings"] == 0 and w["primes"] == 0
+
+
+def test_work_counter_exact_prime_s2():
+    """p = 2^40 + 141 = 1099511627917 is prime (certificate below) with
+    p = 5 (mod 8): s = 2 and d = (p - 1)/4 = 2^38 + 35 = 2^38 + 2^5 + 2 + 1,
+    so each base's a^d takes bitlen(d) - 1 = 38 squarings and popcount(d) - 1
+    = 3 multiplications.  With s = 2, a^(2d) = a^((p-1)/2) is the Legendre
+    symbol (a/p) (Euler's criterion): for (a/p) = -1 the tail squares once
+    and meets -1 (a^d is not +-1, its square being -1); for (a/p) = +1,
+    a^d = +-1 and the tail is empty.  2 is a non-residue mod p = 5 (mod 8)."""
+    p = 2**40 + 141
+    assert nt.pratt_prime(p) and p % 8 == 5
+    w = oracle.work_counts(np.array([p], dtype=np.uint64), td_bound=53)
+    assert w["primes"] == 1 and w["base2_passes"] == 1 and w["base_tests"] == 7
+    assert w["base2_squarings"] == 38 + 1 and w["base2_doublings"] == 3
+    bases = [325, 9375, 28178, 450775, 9780504, 1795265022]
+    nonres = sum(1 for a in bases if pow(a, (p - 1) // 2, p) == p - 1)
+    assert w["rest_squarings"] == 6 * 38 + nonres
+    assert w["rest_multiplies"] == 6 * 3

@@ -16,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from workloads import plain_large, plain_mixed
 
 torch = pytest.importorskip("torch")
@@ -64,6 +65,13 @@ def test_noalloc_matches_isprime_u64_two_calls_in_a_row():
         bad = np.flatnonzero(got != want)
         assert bad.size == 0, f"{bad.size} mismatches, first n={int(v[bad[0]])}"
         assert set(np.unique(got).tolist()) <= {0, 1}
+        # and against the CPU oracle directly: the special values plus a few
+        # thousand of the array (the two entry points share classify and the
+        # Montgomery arithmetic, so this check does not lean on isprime_u64)
+        k = np.r_[np.arange(min(v.size, 4096)), np.arange(max(0, v.size - 4096), v.size)]
+        ref = oracle.isprime_u64(v[k])
+        bad = np.flatnonzero(got[k] != ref)
+        assert bad.size == 0, f"oracle: {bad.size} mismatches, first n={int(v[k][bad[0]])}"
 
 
 def test_noalloc_limits():
