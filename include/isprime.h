@@ -437,6 +437,21 @@ typedef struct {
 int isprime_count_ops(isprime_ctx *ctx, const uint64_t *d_in, uint8_t *d_out, size_t n,
                       isprime_op_counts *out);
 
+/* Bounds checks of the debug build of the library (built with
+ * IP_DEBUG_CHECKS, `python -m paper_2108_04791_gb300._build --debug`): every
+ * queue append, queue read and output store of the kernels checks its index
+ * against the buffer's bound; a violation skips the access and is recorded
+ * (no trap, so the context stays usable).  *sites receives the OR of the
+ * violated sites' bits (bit k: site k; the sites are the classify queues
+ * and output, the Miller-Rabin queues and outputs, the batched kernel's
+ * shared queues and outputs, the range kernel's queue and output, the window
+ * gather and the one-warp kernels' outputs), *violations their count, for the
+ * current device, since the last reset (reset != 0 clears them after
+ * reading).  *compiled (nullable) is 1 in the debug build and 0 in the
+ * production build, where the checks are compiled out and both counts read 0.
+ * Reads device memory: synchronise the work to be checked first. */
+int isprime_debug_checks(int reset, uint32_t *sites, uint64_t *violations, int *compiled);
+
 /* ---------------------------------------------------------------- misc */
 
 const char *isprime_strerror(int status);

@@ -101,7 +101,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB_PATH
+            # ISPRIME_GB300_LIB selects another build of the same library (the
+            # debug build with bounds checks, see _build.build(debug=True))
+            path = os.environ.get("ISPRIME_GB300_LIB") or _build.LIB_PATH
             if not os.path.exists(path):
                 raise IsPrimeError(ECUDA, f"CUDA library not built ({path}); run "
                                    "paper_2108_04791_gb300.build() on a machine with nvcc")
@@ -137,6 +139,9 @@ def lib():
                 "isprime_timing_reset": ([vp], i32),
                 "isprime_measure_int_rates": ([i32, ctypes.POINTER(_IntRates)], i32),
                 "isprime_count_ops": ([vp, vp, vp, sz, ctypes.POINTER(_OpCounts)], i32),
+                "isprime_debug_checks": ([i32, ctypes.POINTER(ctypes.c_uint32),
+                                          ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.POINTER(ctypes.c_int)], i32),
                 "isprime_plan_contiguous": ([u64, ctypes.c_uint32, vp], i32),
                 "isprime_plan_batched": ([vp, sz, ctypes.c_uint32, vp, vp], i32),
                 "isprime_route_least_loaded": ([vp, ctypes.c_uint32,
@@ -460,6 +465,14 @@ def isprime_host(values, device: int = 0) -> np.ndarray:
 
 def isprime_scalar(value: int, device: int = 0) -> bool:
     return _default_ctx(device).isprime_scalar(value)
+
+
+def debug_checks(reset: bool = True) -> dict:
+    """Bounds-check record of the debug build (see isprime_debug_checks)."""
+    s, v, c = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_int()
+    _check(lib().isprime_debug_checks(1 if reset else 0, ctypes.byref(s), ctypes.byref(v),
+                                      ctypes.byref(c)))
+    return {"compiled": bool(c.value), "sites": int(s.value), "violations": int(v.value)}
 
 
 def int_rates(device: int = 0) -> dict:

@@ -450,11 +450,13 @@ int isprime_ctx_stats(const isprime_ctx* ctx, isprime_stats* out) {
 
 int isprime_u64_ctx(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
                     isprime_stream stream) {
+  IP_NVTX("isprime_u64_ctx");
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
   return run_array<false>(ctx, d_in, d_out, n, nullptr, (cudaStream_t)stream);
 }
 
 int isprime_u64(const uint64_t* d_in, uint8_t* d_out, size_t n, isprime_stream stream) {
+  IP_NVTX("isprime_u64");
   if (n == 0) return ISPRIME_OK;
   int st = check_array_args(d_in, d_out, n, 8);
   if (st) return st;
@@ -466,12 +468,14 @@ int isprime_u64(const uint64_t* d_in, uint8_t* d_out, size_t n, isprime_stream s
 
 int isprime_f64_ctx(isprime_ctx* ctx, const double* d_in, uint8_t* d_out, size_t n,
                     unsigned long long* d_invalid, isprime_stream stream) {
+  IP_NVTX("isprime_f64_ctx");
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
   return run_array<true>(ctx, d_in, d_out, n, d_invalid, (cudaStream_t)stream);
 }
 
 int isprime_f64(const double* d_in, uint8_t* d_out, size_t n, unsigned long long* d_invalid,
                 isprime_stream stream) {
+  IP_NVTX("isprime_f64");
   if (n == 0) return ISPRIME_OK;
   int st = check_array_args(d_in, d_out, n, 8);
   if (st) return st;
@@ -482,6 +486,7 @@ int isprime_f64(const double* d_in, uint8_t* d_out, size_t n, unsigned long long
 }
 
 int isprime_f64_sync_status(isprime_ctx* ctx, unsigned long long* count) {
+  IP_NVTX("isprime_f64_sync_status");
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
   if (count) *count = 0;
   std::lock_guard<std::mutex> lock(ctx->mu);
@@ -501,6 +506,7 @@ int isprime_f64_sync_status(isprime_ctx* ctx, unsigned long long* count) {
 
 int isprime_range(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out,
                   isprime_stream stream) {
+  IP_NVTX("isprime_range");
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
   if (count == 0) return ISPRIME_OK;
   if (!d_out) return set_error(ISPRIME_EINVAL, "d_out is NULL with count > 0");
@@ -522,6 +528,7 @@ int isprime_range(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out,
 
 int isprime_u64_batched(isprime_ctx* ctx, const isprime_array* arrays, size_t n_arrays,
                         isprime_stream stream) {
+  IP_NVTX("isprime_u64_batched");
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
   if (n_arrays == 0) return ISPRIME_OK;
   if (!arrays) return set_error(ISPRIME_EINVAL, "arrays is NULL");
@@ -541,6 +548,7 @@ int isprime_u64_batched(isprime_ctx* ctx, const isprime_array* arrays, size_t n_
 }
 
 int isprime_u64_scalar(isprime_ctx* ctx, uint64_t value, uint8_t* result) {
+  IP_NVTX("isprime_u64_scalar");
   if (!ctx || !result) return set_error(ISPRIME_EINVAL, "NULL argument");
   DeviceGuard g(ctx->device);
   {
@@ -552,6 +560,7 @@ int isprime_u64_scalar(isprime_ctx* ctx, uint64_t value, uint8_t* result) {
 
 int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, size_t n,
                      isprime_stream stream) {
+  IP_NVTX("isprime_u64_host");
   if (!ctx) return set_error(ISPRIME_EINVAL, "ctx is NULL");
   if (n == 0) return ISPRIME_OK;
   int st = check_array_args(h_in, h_out, n, 8);
@@ -646,6 +655,7 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
 }
 
 int isprime_sieve_count(isprime_ctx* ctx, uint64_t* out) {
+  IP_NVTX("isprime_sieve_count");
   if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
   *out = 0;
   if (ctx->sieve_limit == 0) return ISPRIME_OK;
@@ -704,6 +714,7 @@ int isprime_timing_reset(isprime_ctx* ctx) {
 
 int isprime_count_ops(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
                       isprime_op_counts* out) {
+  IP_NVTX("isprime_count_ops");
   if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
   memset(out, 0, sizeof *out);
   int st = check_array_args(d_in, d_out, n, 8);
@@ -745,6 +756,29 @@ int isprime_count_ops(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, si
   out->rest_squarings[1] = c[1][0][1];
   out->rest_products[0] = c[1][1][0];
   out->rest_products[1] = c[1][1][1];
+  return ISPRIME_OK;
+}
+
+int isprime_debug_checks(int reset, uint32_t* sites, uint64_t* violations, int* compiled) {
+  if (!sites || !violations) return set_error(ISPRIME_EINVAL, "NULL argument");
+#if defined(IP_DEBUG_CHECKS)
+  if (compiled) *compiled = 1;
+#else
+  if (compiled) *compiled = 0;
+#endif
+  *sites = 0;
+  *violations = 0;
+  int (*readers[])(uint32_t*, uint64_t*, bool) = {check_read_classify, check_read_mr,
+                                                   check_read_batched,  check_read_range,
+                                                   check_read_window,   check_read_small};
+  for (auto rd : readers) {
+    uint32_t s = 0;
+    uint64_t c = 0;
+    int st = rd(&s, &c, reset != 0);
+    if (st) return st;
+    *sites |= s;
+    *violations += c;
+  }
   return ISPRIME_OK;
 }
 

@@ -262,6 +262,7 @@ int autotune(isprime_ctx* ctx, const uint64_t* d_sample, uint8_t* d_out, size_t 
 
 extern "C" int isprime_autotune(isprime_ctx* ctx, const uint64_t* d_sample, uint8_t* d_scratch_out,
                                 size_t n, int mode, const char* cache_path, isprime_tuning* out) {
+  IP_NVTX("isprime_autotune");
   if (!ctx || !d_sample || !d_scratch_out || n == 0)
     return ip::set_error(ISPRIME_EINVAL, "autotune needs a context and a non-empty device sample");
   if (mode != ISPRIME_TUNE_PLAIN && mode != ISPRIME_TUNE_BATCHED)

@@ -38,7 +38,7 @@ struct BatchParams {
 };
 
 __device__ __forceinline__ void smem_push(bool want, uint64_t v, uint64_t addr, uint64_t* qv,
-                                          uint64_t* qa, uint32_t* count) {
+                                          uint64_t* qa, uint32_t* count, uint32_t cap) {
   const unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
   if (mask == 0) return;
   const int lane = threadIdx.x & 31;
@@ -48,8 +48,10 @@ __device__ __forceinline__ void smem_push(bool want, uint64_t v, uint64_t addr, 
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
   if (want) {
     const uint32_t pos = base + __popc(mask & ((1u << lane) - 1u));
-    qv[pos] = v;
-    qa[pos] = addr;
+    if (IP_CHECK(pos < cap, kChkSmemQueue)) {
+      qv[pos] = v;
+      qa[pos] = addr;
+    }
   }
 }
 
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
     const uint64_t nb = b2 ? v : 0xFFFFFFFFFFFFFFC5ull;
     const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(nb));
     const bool pass = base2_passes_shift<kImplB2>(nb, nib) && b2;
-    smem_push(pass, v, a, q2v, q2a, &s_n2);
+    smem_push(pass, v, a, q2v, q2a, &s_n2, q2cap);
     __syncthreads();
   };
   // Six-base round on `cnt` entries from the top of Q2 (cnt <= B).
@@ -146,9 +148,9 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
       if (e < e1) {
         v = d.in[e];
         dec = classify_value<kNtd>(v, p);
-        d.out[e] = (uint8_t)(dec == kPrime);
+        if (IP_CHECK(e < d.n, kChkBatchOut)) d.out[e] = (uint8_t)(dec == kPrime);
       }
-      smem_push(dec == kMR64 || dec == kMR32, v, (uint64_t)(d.out + e), q1v, q1a, &s_n1);
+      smem_push(dec == kMR64 || dec == kMR32, v, (uint64_t)(d.out + e), q1v, q1a, &s_n1, q1cap);
     }
     __syncthreads();
     uint32_t n1 = s_n1;
@@ -171,6 +173,8 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
     n2 = s_n2;
   }
 }
+
+IP_CHECK_READER(check_read_batched)
 
 using BatchLauncher = void (*)(const BatchParams&, unsigned, unsigned, size_t, cudaStream_t);
 
@@ -221,6 +225,7 @@ void batch_state_free(BatchState* b) {
 
 int batched_run(isprime_ctx* ctx, BatchState* bs, const isprime_array* arrays, size_t n_arrays,
                 uint64_t warp_max, cudaStream_t s) {
+  IP_NVTX("batched_run");
   const uint32_t block = ctx->tune.batch_block;
   uint64_t elems = 0;
   for (size_t i = 0; i < n_arrays; ++i) elems += arrays[i].n;

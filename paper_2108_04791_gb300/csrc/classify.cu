@@ -60,15 +60,19 @@ __device__ void classify_single(const ClassifyArgs& a, uint64_t i) {
   int d = ok ? classify_value<-1>(v, a) : kComposite;
   if (!ok && a.invalid) atomicAdd(a.invalid, 1ull);
   if (!ok && a.invalid_ctx) atomicAdd(a.invalid_ctx, 1ull);
-  a.out[i] = (uint8_t)(d == kPrime);
+  if (IP_CHECK(i < a.n, kChkOut)) a.out[i] = (uint8_t)(d == kPrime);
   if (d == kMR64) {
     const uint32_t pos = atomicAdd(&a.counters[0], 1u);
-    a.q64_n[pos] = v;
-    a.q64_idx[pos] = (uint32_t)i;
+    if (IP_CHECK(pos < a.q64_cap, kChkQ64Front)) {
+      a.q64_n[pos] = v;
+      a.q64_idx[pos] = (uint32_t)i;
+    }
   } else if (d == kMR32) {
     const uint32_t pos = atomicAdd(&a.counters[1], 1u);
-    a.q32_n[pos] = (uint32_t)v;
-    a.q32_idx[pos] = (uint32_t)i;
+    if (IP_CHECK(pos < a.q64_cap, kChkQ32)) {
+      a.q32_n[pos] = (uint32_t)v;
+      a.q32_idx[pos] = (uint32_t)i;
+    }
   }
 }
 
@@ -167,9 +171,10 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
         const uint64_t i0 = head + 2 * p;
         const uint8_t o0 = (uint8_t)(((dm >> (4 * k)) & 3u) == kPrime);
         const uint8_t o1 = (uint8_t)(((dm >> (4 * k + 2)) & 3u) == kPrime);
-        if (a.pair_store)
+        if (!IP_CHECK(i0 + 1 < a.n, kChkOut)) {
+        } else if (a.pair_store) {
           *reinterpret_cast<uint16_t*>(a.out + i0) = (uint16_t)(o0 | (o1 << 8));
-        else {
+        } else {
           a.out[i0] = o0;
           a.out[i0 + 1] = o1;
         }
@@ -217,18 +222,24 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
         const int dj = (int)((dm >> (2 * j)) & 3u);
         if (dj == kMR64) {
           if (!kSplit || ((s1 >> (2 * j)) & 1u)) {
-            a.q64_n[pos64] = v[j];
-            a.q64_idx[pos64] = i0 + h;
+            if (IP_CHECK(pos64 < a.q64_cap, kChkQ64Front)) {
+              a.q64_n[pos64] = v[j];
+              a.q64_idx[pos64] = i0 + h;
+            }
             ++pos64;
           } else {
             const uint32_t pb = a.q64_cap - 1u - posb;
-            a.q64_n[pb] = v[j];
-            a.q64_idx[pb] = i0 + h;
+            if (IP_CHECK(posb < a.q64_cap, kChkQ64Back)) {
+              a.q64_n[pb] = v[j];
+              a.q64_idx[pb] = i0 + h;
+            }
             ++posb;
           }
         } else if (dj == kMR32) {
-          a.q32_n[pos32] = (uint32_t)v[j];
-          a.q32_idx[pos32] = i0 + h;
+          if (IP_CHECK(pos32 < a.q64_cap, kChkQ32)) {
+            a.q32_n[pos32] = (uint32_t)v[j];
+            a.q32_idx[pos32] = i0 + h;
+          }
           ++pos32;
         }
       }
@@ -245,7 +256,7 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
 // Trial-division counts with a compiled specialisation; other counts use
 // the runtime-count kernel.
 // The fold levels and the s-split are compiled for the default count (15,
-// the odd primes 3..53, all of which kFoldOf covers); other counts take the
+// the odd primes 3..53, the primes fold_width knows); other counts take the
 // unfolded, unsplit kernel (the results are the same either way).
 template <typename T>
 static void launch_classify_kernel(const ClassifyArgs& a, unsigned grid, unsigned block,
@@ -302,6 +313,8 @@ int launch_classify_u64_raw(const ClassifyArgs& a, unsigned grid, unsigned block
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "classify_kernel<u64>");
 }
+
+IP_CHECK_READER(check_read_classify)
 
 uint64_t td_square_for(uint32_t ntd) {
   const uint64_t next = ntd < (uint32_t)kMaxTdPrimes ? kTdPrimeList[ntd] : kTdNextPrimeAfterList;

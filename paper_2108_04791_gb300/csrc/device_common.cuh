@@ -21,6 +21,55 @@ static __constant__ BaseTable c_bases = make_base_table();
 
 enum : int { kComposite = 0, kPrime = 1, kMR64 = 2, kMR32 = 3, kSieveLookup = 4 };
 
+// Bounds checks of the debug build (compiled with IP_DEBUG_CHECKS; see
+// isprime_debug_checks).  IP_CHECK(cond, site) guards one queue append,
+// queue read or output store: in the debug build a false cond sets the
+// site's bit in this translation unit's check word, counts the violation and
+// skips the access (no trap); in the production build it is the constant
+// true and costs nothing.  IP_CHECK_READER(name) defines the host function
+// that reads (and optionally clears) the translation unit's word.
+enum : int {
+  kChkQ64Front = 0, kChkQ64Back, kChkQ32, kChkOut, kChkQ64Read, kChkQ64b, kChkMrOut, kChkRestRead,
+  kChkRestOut, kChkMr32, kChkSmemQueue, kChkBatchOut, kChkRangeQueue, kChkRangeOut, kChkWindow,
+  kChkSmallOut, kChkSites
+};
+#if defined(IP_DEBUG_CHECKS)
+static __device__ unsigned int g_ip_check_sites;
+static __device__ unsigned long long g_ip_check_count;
+__device__ __forceinline__ bool ip_check(bool ok, int site) {
+  if (!ok) {
+    atomicOr(&g_ip_check_sites, 1u << site);
+    atomicAdd(&g_ip_check_count, 1ull);
+  }
+  return ok;
+}
+#define IP_CHECK(cond, site) (::ip::ip_check((cond), (site)))
+#define IP_CHECK_READER(name)                                                        \
+  int name(uint32_t* sites, uint64_t* count, bool reset) {                           \
+    unsigned int s = 0;                                                              \
+    unsigned long long c = 0;                                                        \
+    IP_CUDA(cudaMemcpyFromSymbol(&s, g_ip_check_sites, sizeof s));                   \
+    IP_CUDA(cudaMemcpyFromSymbol(&c, g_ip_check_count, sizeof c));                   \
+    *sites = s;                                                                      \
+    *count = c;                                                                      \
+    if (reset) {                                                                     \
+      s = 0;                                                                         \
+      c = 0;                                                                         \
+      IP_CUDA(cudaMemcpyToSymbol(g_ip_check_sites, &s, sizeof s));                   \
+      IP_CUDA(cudaMemcpyToSymbol(g_ip_check_count, &c, sizeof c));                   \
+    }                                                                                \
+    return ISPRIME_OK;                                                               \
+  }
+#else
+#define IP_CHECK(cond, site) (true)
+#define IP_CHECK_READER(name)                              \
+  int name(uint32_t* sites, uint64_t* count, bool) {       \
+    *sites = 0;                                            \
+    *count = 0;                                            \
+    return ISPRIME_OK;                                     \
+  }
+#endif
+
 // Double input: finite, >= 0, integral and <= 2^53 (Sec. 8.1) converts
 // exactly; anything else is invalid (output 0, counted).
 __device__ __forceinline__ bool f64_to_u64(double x, uint64_t* v) {
@@ -32,7 +81,7 @@ __device__ __forceinline__ bool f64_to_u64(double x, uint64_t* v) {
 constexpr int kWin = 4;
 constexpr int kTab = 1 << kWin;
 
-// Chunk sums of n = hi 2^32 + lo modulo 2^k - 1 (see kFoldOf in tables.cuh);
+// Chunk sums of n = hi 2^32 + lo modulo 2^k - 1 (see fold_width in tables.cuh);
 // each result is below 2^32 and congruent to n modulo 2^k - 1.
 __device__ __forceinline__ uint32_t fold_sum32(uint32_t lo, uint32_t hi) {
   const uint64_t s = (uint64_t)lo + hi;  // < 2^33; the carry wraps around

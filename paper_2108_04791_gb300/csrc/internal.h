@@ -1,6 +1,7 @@
 // internal.h -- library-private declarations shared by the .cu files.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -14,6 +15,16 @@ namespace ip {
 // Records the error text for isprime_last_error() and returns `status`.
 int set_error(int status, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
+
+// An NVTX range over the rest of the enclosing scope (entry points, batches,
+// server dispatches): visible to Nsight tools, a few instructions otherwise.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define IP_NVTX(name) ::ip::NvtxRange ip_nvtx_range_(name)
 
 #define IP_CUDA(call)                                     \
   do {                                                    \
@@ -199,6 +210,15 @@ int array_minmax(isprime_ctx* ctx, const uint64_t* d_in, size_t n, cudaStream_t 
 // The autotuner's crossover fit of the window path near the value `near`
 // (arrays of up to n values); the context's tuning is unchanged.
 int window_fit(isprime_ctx* ctx, uint64_t near, size_t n, cudaStream_t s, uint32_t* ratio16);
+
+// Readers of the debug build's check words, one per translation unit with
+// kernels (IP_CHECK_READER in device_common.cuh).
+int check_read_classify(uint32_t* sites, uint64_t* count, bool reset);
+int check_read_mr(uint32_t* sites, uint64_t* count, bool reset);
+int check_read_batched(uint32_t* sites, uint64_t* count, bool reset);
+int check_read_range(uint32_t* sites, uint64_t* count, bool reset);
+int check_read_window(uint32_t* sites, uint64_t* count, bool reset);
+int check_read_small(uint32_t* sites, uint64_t* count, bool reset);
 
 // probe.cu
 int measure_int_rates(int device, isprime_int_rates* out);

@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) {
       pass[u] = false;
+      valid[u] = valid[u] && IP_CHECK(pos[u] < cap, kChkQ64Read);
       n[u] = valid[u] ? qn[pos[u]] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 (prime) when idle
     }
     if (kIlp == 2) {
@@ -127,15 +128,17 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
         const bool prime = kRest == 2 ? lucas_warp<kImpl>(m, pass[u])
                                       : rest64_is_prime_warp<kImpl>(m, pass[u], s_tab + threadIdx.x,
                                                                     (int)blockDim.x);
-        if (prime) out[qidx[pos[u]]] = 1;
+        if (prime && IP_CHECK(qidx[pos[u]] < cap, kChkMrOut)) out[qidx[pos[u]]] = 1;
       } else if (mask) {
         const int leader = __ffs(mask) - 1;
         uint32_t base = 0;
         if (lane == leader) base = atomicAdd(&counters[2], (uint32_t)__popc(mask));
         base = __shfl_sync(0xFFFFFFFFu, base, leader);
         if (pass[u]) {
-          q64b[base + __popc(mask & ((1u << lane) - 1u))] = pos[u];
-          if (mark) out[qidx[pos[u]]] = 1;  // prime unless a later base clears it (spread rest kernel)
+          const uint32_t k = base + __popc(mask & ((1u << lane) - 1u));
+          if (IP_CHECK(k < cap, kChkQ64b)) q64b[k] = pos[u];
+          // prime unless a later base clears it (spread rest kernel)
+          if (mark && IP_CHECK(qidx[pos[u]] < cap, kChkMrOut)) out[qidx[pos[u]]] = 1;
         }
       }
     }
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
                                                         const uint32_t* __restrict__ q64b,
                                                         const uint32_t* __restrict__ counters,
                                                         uint8_t* __restrict__ out,
-                                                        uint32_t spread_threads) {
+                                                        uint32_t spread_threads, uint32_t cap) {
   extern __shared__ uint64_t s_tab[];  // 2^kW x blockDim
   uint64_t* tab = s_tab + threadIdx.x;
   const int ld = blockDim.x;
@@ -182,10 +185,11 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
         const uint32_t g = wbase + lane;
         const bool valid = g < pairs;
         const uint32_t e = valid ? g / f : 0u;
-        const uint32_t j = valid ? q64b[e] : 0u;
+        uint32_t j = valid ? q64b[e] : 0u;
+        if (!IP_CHECK(j < cap, kChkRestRead)) j = 0;
         const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
         const bool pass = bases_pass_warp<kImpl, kW>(n, 1 + (int)(g - e * f) * per, per, tab, ld);
-        if (valid && !pass) out[qidx[j]] = 0;
+        if (valid && !pass && IP_CHECK(qidx[j] < cap, kChkRestOut)) out[qidx[j]] = 0;
       }
       return;
     }
@@ -193,11 +197,13 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   for (uint32_t wbase = first; wbase < count; wbase += nthreads) {
     const uint32_t i = wbase + lane;
     const bool valid = i < count;
-    const uint32_t j = valid ? q64b[i] : 0u;
+    uint32_t j = valid ? q64b[i] : 0u;
+    if (!IP_CHECK(j < cap, kChkRestRead)) j = 0;
     const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
     const bool prime =
         kLucas ? lucas_warp<kImpl>(n, valid) : rest64_is_prime_warp<kImpl, kW>(n, valid, tab, ld);
-    if (kSpread) {
+    if (!IP_CHECK(!valid || qidx[j] < cap, kChkRestOut)) {
+    } else if (kSpread) {
       if (valid && !prime) out[qidx[j]] = 0;
     } else if (prime) {
       out[qidx[j]] = 1;
@@ -208,10 +214,10 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
 __global__ void __launch_bounds__(256) mr32_kernel(const uint32_t* __restrict__ qn,
                                                    const uint32_t* __restrict__ qidx,
                                                    const uint32_t* __restrict__ counters,
-                                                   uint8_t* __restrict__ out) {
+                                                   uint8_t* __restrict__ out, uint32_t cap) {
   const uint32_t count = *(volatile const uint32_t*)&counters[1];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
-    if (mr32_is_prime(qn[i])) out[qidx[i]] = 1;
+    if (IP_CHECK(i < cap && qidx[i] < cap, kChkMr32) && mr32_is_prime(qn[i])) out[qidx[i]] = 1;
 }
 
 // Grid of a grid-stride kernel: at most the blocks that can be resident.
@@ -290,11 +296,11 @@ static void launch_rest_w(const Queues& q, uint8_t* out, unsigned grid, unsigned
     const uint32_t spread_threads = spread_grid * block;
     const void* fn = reinterpret_cast<const void*>(&mr64_rest_kernel<kImpl, false, true, kW>);
     const unsigned g = resident_grid(fn, block, smem, sm_count, spread_grid);
-    mr64_rest_kernel<kImpl, false, true, kW><<<g, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
-                                                                    q.counters, out, spread_threads);
+    mr64_rest_kernel<kImpl, false, true, kW><<<g, block, smem, s>>>(
+        q.q64_n, q.q64_idx, q.q64b, q.counters, out, spread_threads, (uint32_t)q.capacity);
   } else {
-    mr64_rest_kernel<kImpl, false, false, kW><<<grid, block, smem, s>>>(q.q64_n, q.q64_idx, q.q64b,
-                                                                       q.counters, out, 0u);
+    mr64_rest_kernel<kImpl, false, false, kW><<<grid, block, smem, s>>>(
+        q.q64_n, q.q64_idx, q.q64b, q.counters, out, 0u, (uint32_t)q.capacity);
   }
 }
 
@@ -303,7 +309,7 @@ static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned b
                         const MrOpts& o, unsigned spread_grid, int sm_count, cudaStream_t s) {
   if (o.lucas) {
     mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
-                                                                out, 0u);
+                                                                out, 0u, (uint32_t)q.capacity);
   } else if ((kImpl == 6 || kImpl == 17) && o.rest_win == 3) {
     launch_rest_w<kImpl, 3>(q, out, grid, block, spread_grid, sm_count, s);
   } else {
@@ -371,7 +377,7 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
   int st;
   if (sieve_cut(ctx) < (1ull << 32)) {
     if ((st = launch_begin(ctx, ISPRIME_K_MR32, s, &tl))) return st;
-    mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
+    mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out, (uint32_t)q.capacity);
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
   MrOpts o;
@@ -393,7 +399,8 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
 // used by the allocation-free entry point.
 int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, unsigned block,
                   cudaStream_t s) {
-  if (with_mr32) mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out);
+  if (with_mr32)
+    mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out, (uint32_t)q.capacity);
   // Montgomery formulation 6; base 2 by the binary schedule (its launch needs
   // no occupancy query, so no SM count)
   MrOpts o;
@@ -402,6 +409,8 @@ int launch_mr_raw(const Queues& q, uint8_t* out, bool with_mr32, unsigned grid, 
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ISPRIME_OK : cuda_fail(e, "Miller-Rabin kernels");
 }
+
+IP_CHECK_READER(check_read_mr)
 
 // The operation counters of this translation unit (arith.cuh, g_ip_ops):
 // out receives [stage][kind][warp issues, active lanes] summed over the

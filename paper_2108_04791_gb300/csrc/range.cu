@@ -34,6 +34,7 @@ struct RangeArgs {
   uint32_t* q64_idx;
   uint32_t* counters;
   const uint32_t* sieve;  // resident bitmap (expand kernel)
+  uint32_t q64_cap;       // capacity of the survivor queue
 };
 
 // Single-thread expansion of a few values (alignment head and tail).
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kRangeThreads) range_sieve_kernel(RangeArgs a)
         mr = true;
         o = 0;
       }
-      a.out[v - a.lo] = o;
+      if (IP_CHECK(v - a.lo < a.count, kChkRangeOut)) a.out[v - a.lo] = o;
     }
     // block-aggregated append of the undecided survivors
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, mr);
@@ -173,8 +174,10 @@ __global__ void __launch_bounds__(kRangeThreads) range_sieve_kernel(RangeArgs a)
     __syncthreads();
     if (mr) {
       const uint32_t pos = s_base + s_scan[warp] + __popc(bal & ((1u << lane) - 1u));
-      a.q64_n[pos] = v;
-      a.q64_idx[pos] = (uint32_t)(v - a.lo);
+      if (IP_CHECK(pos < a.q64_cap, kChkRangeQueue)) {
+        a.q64_n[pos] = v;
+        a.q64_idx[pos] = (uint32_t)(v - a.lo);
+      }
     }
     __syncthreads();
   }
@@ -225,6 +228,8 @@ int launch_range_sieve(isprime_ctx* ctx, const RangeArgs& a, cudaStream_t s) {
   return launch_end(ctx, s, &tl, "range_sieve_kernel");
 }
 
+IP_CHECK_READER(check_read_range)
+
 int range_run(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out, cudaStream_t s) {
   uint64_t done = 0;
   int st = ISPRIME_OK;
@@ -255,6 +260,7 @@ int range_run(isprime_ctx* ctx, uint64_t lo, uint64_t count, uint8_t* d_out, cud
     a.q64_n = ctx->q.q64_n;
     a.q64_idx = ctx->q.q64_idx;
     a.counters = ctx->q.counters;
+    a.q64_cap = (uint32_t)ctx->q.capacity;
     if ((st = launch_range_sieve(ctx, a, s))) return st;
     if ((st = launch_mr(ctx, ctx->q, d_out + done, c_n, s))) return st;
     done += c_n;

@@ -237,6 +237,7 @@ void dispatcher_loop(isprime_server* S) {
     lk.unlock();
     const cudaStream_t stream = cls == 1 ? sl.fast : sl.stream;
     // copy-in, one batched launch, copy-out
+    IP_NVTX(cls == 1 ? "server batch (short requests)" : "server batch");
     int st = ISPRIME_OK;
     std::vector<isprime_array> arrays(batch.size());
     for (size_t i = 0; i < batch.size() && !st; ++i) {

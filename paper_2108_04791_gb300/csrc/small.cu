@@ -158,6 +158,8 @@ int launch_inline(isprime_ctx* ctx, const uint64_t* h_in, uint32_t n, cudaStream
 
 }  // namespace
 
+IP_CHECK_READER(check_read_small)
+
 int launch_small_u64(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
                      cudaStream_t s) {
   TimedLaunch tl;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(kSmallBlock)
     const uint64_t j = e - descs[a].tile_begin;
     // a plain load: the array may be mapped host memory (the server's short requests)
     const bool prime = warp_isprime(descs[a].in[j], sieve, S, lane);
-    if (lane == 0) descs[a].out[j] = prime ? 1 : 0;
+    if (lane == 0 && IP_CHECK(j < descs[a].n, kChkSmallOut)) descs[a].out[j] = prime ? 1 : 0;
   }
 }
 

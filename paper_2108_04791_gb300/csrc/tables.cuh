@@ -80,16 +80,31 @@ constexpr TdTable kTdHost = make_td_table();
 //   2^24 - 1 = 3^2 * 5 * 7 * 13 * 17 * 241
 //   2^20 - 1 = 3 * 5^2 * 11 * 31 * 41
 //   2^28 - 1 = 3 * 5 * 29 * 43 * 113 * 127
-// kFoldOf[i] is the k whose chunk sum serves the i-th odd prime at fold level
-// 2 (0: the 64-bit test); level 1 leaves out k = 28.  The shifts, masks and
-// adds of the folds run on the ALU pipe, the tests they replace on the
-// multiply pipe, so the level trades one pipe's work for the other's.
+// fold_width(i, level) is the k whose chunk sum serves the i-th odd prime
+// (0: the 64-bit test) at fold level 1 (k = 32, 24, 20) or 2 (also 28): 3, 5
+// and 17 by 2^32 - 1, 7 and 13 by 2^24 - 1, 11, 31 and 41 by 2^20 - 1, 29 and
+// 43 by 2^28 - 1.  It is plain arithmetic on i (no table), since device code
+// calls it.  The shifts, masks and adds of the folds run on the ALU pipe, the
+// tests they replace on the multiply pipe, so the level trades one pipe's
+// work for the other's.
 constexpr int kFoldPrimes = 15;  // 3 .. 53
-constexpr int kFoldOf[kFoldPrimes] = {32, 32, 24, 20, 24, 32, 0, 0, 28, 20, 0, 20, 28, 0, 0};
 constexpr int fold_width(int i, int level) {
-  return (i >= kFoldPrimes || level <= 0) ? 0
-         : (kFoldOf[i] == 28 && level < 2) ? 0
-                                            : kFoldOf[i];
+  return level <= 0 ? 0
+         : (i == 0 || i == 1 || i == 5)             ? 32
+         : (i == 2 || i == 4)                       ? 24
+         : (i == 3 || i == 9 || i == 11)            ? 20
+         : ((i == 8 || i == 12) && level >= 2)      ? 28
+                                                    : 0;
 }
+// Every prime given a fold divides 2^k - 1 (checked at compile time).
+constexpr bool fold_widths_divide() {
+  for (int level = 1; level <= 2; ++level)
+    for (int i = 0; i < kMaxTdPrimes; ++i) {
+      const int k = fold_width(i, level);
+      if (k != 0 && (i >= kFoldPrimes || ((1ull << k) - 1) % kTdPrimeList[i] != 0)) return false;
+    }
+  return true;
+}
+static_assert(fold_widths_divide(), "a folded prime does not divide 2^k - 1");
 
 }  // namespace ip

@@ -67,11 +67,15 @@ __global__ void __launch_bounds__(256) minmax_kernel(const uint64_t* __restrict_
 __global__ void __launch_bounds__(256) window_gather_kernel(const uint64_t* __restrict__ in,
                                                             uint8_t* __restrict__ out, uint64_t n,
                                                             const uint8_t* __restrict__ win,
-                                                            uint64_t lo) {
+                                                            uint64_t lo, uint64_t w) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    out[i] = win[__ldcs(in + i) - lo];
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = __ldcs(in + i) - lo;
+    if (IP_CHECK(k < w, kChkWindow)) out[i] = win[k];
+  }
 }
+
+IP_CHECK_READER(check_read_window)
 
 // Min and max of a device array (synchronous on s).
 int array_minmax(isprime_ctx* ctx, const uint64_t* d_in, size_t n, cudaStream_t s, uint64_t* lo,
@@ -202,7 +206,7 @@ int window_try(isprime_ctx* ctx, const uint64_t* d_in, uint8_t* d_out, size_t n,
   if ((st = launch_begin(ctx, ISPRIME_K_RANGE, s, &tl))) return st;
   const uint64_t gcap = (uint64_t)ctx->sm_count * 16;
   window_gather_kernel<<<(unsigned)std::min(want, gcap), 256, 0, s>>>(d_in, d_out, n,
-                                                                        ctx->d_window, lo);
+                                                                        ctx->d_window, lo, w);
   if ((st = launch_end(ctx, s, &tl, "window_gather_kernel"))) return st;
   ctx->stats.window_calls++;
   *taken = true;

@@ -1,16 +1,22 @@
-"""The per-element work figures bench.py uses for the roofline are what the
-oracle's work counter measures on the benchmark's array.  CPU only."""
+"""The per-element work figures bench.py uses for its rooflines are what the
+oracle's work counter measures on the benchmark's inputs, and both arms of
+the benchmark describe the workload with the same config.  CPU only."""
+import json
 import os
+import subprocess
 import sys
 
 import numpy as np
 
 import oracle
+from workloads import generators as wg
 from workloads import plain_large
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "work_counts.json")
 
 
 def test_plain_large_work_per_element():
@@ -18,6 +24,43 @@ def test_plain_large_work_per_element():
     w = oracle.work_counts(v, td_bound=53, sieve_limit=1 << 32)
     for k, per in bench.WORK_PLAIN_LARGE.items():
         assert abs(w[k] / v.size - per) < 1e-4, (k, w[k] / v.size, per)
+    g = json.load(open(GOLDEN))["plain_large"]
+    assert g["totals"] == w and g["elements"] == v.size
+
+
+def test_batched_and_served_work_on_a_sample():
+    """The stored full-workload figures (written by make_work_counts.py over
+    every element) agree with a recount of 2^18 elements taken in 16 blocks
+    spread over each workload, within sampling error."""
+    g = json.load(open(GOLDEN))
+    for name, seed, total in (("batched", 3, g["batched"]["elements"]),
+                              ("served_pool", 4, g["served_pool"]["elements"])):
+        assert total == (293_037_204 if name == "batched" else 1 << 27)
+        parts = []
+        for k in range(16):
+            off = (total // 16) * k
+            v = wg.bitlen_uniform(seed, 1 << 14, 2, 64, offset=off)
+            parts.append(wg._replace_with_pools(v, seed, off))
+        v = np.concatenate(parts)
+        w = oracle.work_counts(v, td_bound=53, sieve_limit=1 << 32)
+        per = g[name]["per_element"]
+        for k in ("base2_squarings", "rest_squarings", "rest_multiplies", "trial_tests"):
+            got = w[k] / v.size
+            assert abs(got - per[k]) < 0.05 * per[k] + 0.05, (name, k, got, per[k])
+    # the slots per element the bench derives from them
+    s = bench._slots_per_element(g["batched"]["per_element"])
+    assert 2500 < s < 3700
+
+
+def test_both_arms_print_the_same_config(tmp_path):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    v, desc = bench._workload("plain_large", 0)
+    assert line["config"] == bench._config("plain_large", v.size, desc, 1)
+    assert line["impl"] == "reference" and line["e2e"]["h2d_bytes_per_step"] == 0
 
 
 def test_bench_workload_is_the_generator_array():

@@ -141,14 +141,15 @@ def mixed_doubles(n: int = 1 << 20, seed: int = 2) -> np.ndarray:
     return (r >> np.uint64(11)).astype(np.float64)
 
 
-def _replace_with_pools(v: np.ndarray, seed: int) -> np.ndarray:
+def _replace_with_pools(v: np.ndarray, seed: int, offset: int = 0) -> np.ndarray:
+    """v holds the stream's values at indices offset .. offset + v.size - 1."""
     n = v.size
     big = load_pool("primes_near_2p64.txt")
     small = load_pool("primes_near_2p32.txt")
-    r = splitmix64(seed ^ 0xBA7C4, n)
+    r = splitmix64(seed ^ 0xBA7C4, n, offset)
     u = (r >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
-    pick = splitmix64(seed ^ 0x9001, n)
-    pick2 = splitmix64(seed ^ 0x9002, n)
+    pick = splitmix64(seed ^ 0x9001, n, offset)
+    pick2 = splitmix64(seed ^ 0x9002, n, offset)
     is_p = u < 0.25
     is_sp = (u >= 0.25) & (u < 0.35)
     v = v.copy()
