@@ -101,7 +101,7 @@ def _parse():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--workload", default="plain_large",
                    choices=["plain_large", "plain_small", "plain_mixed", "batched", "served",
-                            "range_1e8", "range_unix2021", "range_2p64", "scalar_t4"])
+                            "range_1e8", "range_unix2021", "range_2p64", "scalar_t4", "window"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-probe", action="store_true", help="skip the integer-rate probe")
@@ -856,6 +856,59 @@ def run_scalar(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_window(args, world, rank, local):
+    """The per-call path choice: the window path (sieve [min, max], gather)
+    against the queue path on arrays of N values spread over windows of
+    W = N / density integers, at two magnitudes; device time per call of each
+    arm (the window arm includes its min/max read-back)."""
+    import torch
+    import paper_2108_04791_gb300 as ipg
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ctx = ipg.Context.default(local)
+    _apply_tune(ctx, args)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    reps = max(3, min(args.steps, 10))
+    for lo in (1 << 40, (1 << 64) - (1 << 34)):
+        for n in (1 << 20, 1 << 22, 1 << 24):
+            for dens in (8.0, 2.0, 1.0, 0.5, 0.25, 0.125):
+                w = max(int(n / dens), 16)
+                rng = np.random.default_rng(n + w)
+                v = (np.uint64(lo) + rng.integers(0, w, size=n, dtype=np.uint64)).astype(np.uint64)
+                t = torch.from_numpy(v.view(np.int64)).to(dev)
+                out = torch.empty(n, dtype=torch.uint8, device=dev)
+                row = {"lo_log2": round(float(np.log2(float(lo))), 3), "n": n, "density": dens,
+                       "window": int(v.max() - v.min()) + 1}
+                for arm, r16 in (("window_ms", 4096), ("queue_ms", 0)):
+                    ctx.set_tuning(window_ratio16=r16, small_max=0)
+                    for _ in range(2):
+                        ctx.isprime(t, out=out)
+                    torch.cuda.synchronize(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(reps):
+                        ctx.isprime(t, out=out)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    row[arm] = e0.elapsed_time(e1) / reps
+                row["winner"] = "window" if row["window_ms"] < row["queue_ms"] else "queue"
+                rows.append(row)
+                del t, out
+    ctx.set_tuning(window_ratio16=0)
+    if rank == 0:
+        best = max(rows, key=lambda r: r["queue_ms"] / r["window_ms"])
+        line = {"metric": METRIC, "value": best["n"] / (best["window_ms"] / 1e3), "unit": UNIT,
+                "n_gpus": world, "steps": reps, "warmup": 2, "ms_per_step": best["window_ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic",
+                "config": {"workload": "window", "description": "N values uniform over a window "
+                           "of N / density integers at 2^40 and near 2^64"},
+                "crossover": rows, "tuning": ctx.tuning.as_dict()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse()
     world, rank, local = _dist_init(args)
@@ -869,6 +922,8 @@ def main():
         run_range(args, world, rank, local)
     elif args.workload == "scalar_t4":
         run_scalar(args, world, rank, local)
+    elif args.workload == "window":
+        run_window(args, world, rank, local)
     else:
         run_mine(args, world, rank, local)
     if world > 1:

@@ -119,6 +119,8 @@ typedef struct {
                               with the range kernels and gathers the array's bytes from that
                               window instead of running the queue path.  0..4096; the
                               autotuner measures the crossover on this GPU */
+  uint32_t base2_blocks_per_sm; /* cap on resident blocks per SM of the base-2 kernel (a single
+                              wave of persistent blocks; 0 = as many as fit, 1..32) */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */
@@ -307,6 +309,17 @@ int isprime_plan_batched(const uint64_t *sizes, size_t n_arrays, uint32_t n_shar
  * a NULL pointer: ISPRIME_EINVAL. */
 int isprime_route_least_loaded(const uint64_t *outstanding, uint32_t n_devices,
                                uint32_t *device);
+
+/* One host-array job on several devices: h_in (n values) is split by
+ * isprime_plan_contiguous into n_devices ranges, range k runs on device
+ * devices[k] through isprime_u64_host with that device's default context, in
+ * a host thread of its own, and the results land in h_out in input order.
+ * Nothing is exchanged between devices.  A device may appear more than once
+ * (its ranges then run one after another).  Synchronous; returns the first
+ * shard's error, if any.  n_devices == 0, a NULL pointer with n > 0 or a
+ * device out of range: ISPRIME_EINVAL, before any device is touched. */
+int isprime_u64_host_multi(const int *devices, uint32_t n_devices, const uint64_t *h_in,
+                           uint8_t *h_out, size_t n);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -49,7 +49,7 @@ class Tuning(ctypes.Structure):
                 ("sieve_cutover_log2", ctypes.c_uint32), ("serve_short_max", ctypes.c_uint32),
                 ("td_fold", ctypes.c_uint32), ("base2_split", ctypes.c_uint32),
                 ("base2_ilp", ctypes.c_uint32), ("rest_window", ctypes.c_uint32),
-                ("window_ratio16", ctypes.c_uint32)]
+                ("window_ratio16", ctypes.c_uint32), ("base2_blocks_per_sm", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -144,6 +144,7 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int)], i32),
                 "isprime_plan_contiguous": ([u64, ctypes.c_uint32, vp], i32),
                 "isprime_plan_batched": ([vp, sz, ctypes.c_uint32, vp, vp], i32),
+                "isprime_u64_host_multi": ([vp, ctypes.c_uint32, vp, vp, sz], i32),
                 "isprime_route_least_loaded": ([vp, ctypes.c_uint32,
                                                 ctypes.POINTER(ctypes.c_uint32)], i32),
                 "isprime_strerror": ([i32], ctypes.c_char_p),
@@ -507,6 +508,17 @@ def plan_batched(sizes, n_shards: int) -> tuple[np.ndarray, np.ndarray]:
                                       n_shards, owner.ctypes.data if sizes.size else None,
                                       load.ctypes.data))
     return owner, load
+
+
+def isprime_host_multi(values, devices) -> np.ndarray:
+    """A host array split over several devices (isprime_u64_host_multi)."""
+    a = np.ascontiguousarray(values, dtype=np.uint64)
+    out = np.empty(a.shape, dtype=np.uint8)
+    d = np.ascontiguousarray(devices, dtype=np.int32)
+    _check(lib().isprime_u64_host_multi(d.ctypes.data if d.size else None, d.size,
+                                        a.ctypes.data if a.size else None,
+                                        out.ctypes.data if a.size else None, a.size))
+    return out
 
 
 def route_least_loaded(outstanding) -> int:

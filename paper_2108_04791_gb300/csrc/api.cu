@@ -94,6 +94,7 @@ static isprime_tuning default_tuning() {
   t.base2_ilp = 1;
   t.rest_window = 4;
   t.window_ratio16 = 0;
+  t.base2_blocks_per_sm = 0;
   return t;
 }
 
@@ -121,6 +122,7 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.base2_ilp != 1 && t.base2_ilp != 2) return set_error(ISPRIME_EINVAL, "base2_ilp must be 1 or 2");
   if (t.rest_window != 3 && t.rest_window != 4) return set_error(ISPRIME_EINVAL, "rest_window must be 3 or 4");
   if (t.window_ratio16 > 4096) return set_error(ISPRIME_EINVAL, "window_ratio16 must be in [0, 4096]");
+  if (t.base2_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "base2_blocks_per_sm must be in [0, 32]");
   return ISPRIME_OK;
 }
 

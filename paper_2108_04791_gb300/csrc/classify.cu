@@ -11,9 +11,7 @@
 //   the 32-bit (n < 2^32) or 64-bit Miller-Rabin queue, and their output byte
 //   is written 0 here and set to 1 later if they are prime.
 // Loads are 16-byte vector loads (coalesced, eight elements per thread per
-// tile); queue appends are block-aggregated (one atomic per queue and tile).
-#include <type_traits>
-
+// tile); queue appends are warp-aggregated (one atomic per queue and warp).
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -76,42 +74,11 @@ __device__ void classify_single(const ClassifyArgs& a, uint64_t i) {
   }
 }
 
-// Exclusive block-wide prefix sum of v; *total receives the block sum.
-// Every thread of the block must call it (two barriers).  V is uint32_t or
-// uint64_t (several small counts packed in bit fields add field by field).
-template <typename V>
-__device__ __forceinline__ V block_exclusive_scan(V v, V* s_warp, V* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = (blockDim.x + 31) >> 5;
-  V incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const V t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const V w = lane < nwarps ? s_warp[lane] : (V)0;
-    V wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const V t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-      if (lane >= o) wi += t;
-    }
-    s_warp[lane] = wi - w;
-    if (lane == 31) s_warp[32] = wi;
-  }
-  __syncthreads();
-  *total = s_warp[32];
-  return s_warp[warp] + incl - v;
-}
-
 constexpr int kPairsPerThread = 4;  // 8 elements per thread per tile
 
 // One tile = blockDim * kPairsPerThread pairs.  Pair p covers the elements
 // head + 2p and head + 2p + 1.  Survivors of a tile are appended to the
-// queues with one atomic per queue for the whole block.  40 registers give
+// queues with one atomic per queue per warp.  40 registers give
 // six 256-thread blocks per SM (measured: 0.115 ms per 2^24 large values,
 // 0.547 ms per 2^26 mixed values, against 0.117 / 0.596 ms at 45).
 // kFold: fold level of the 64-bit trial division (classify_value).
@@ -122,9 +89,6 @@ constexpr int kPairsPerThread = 4;  // 8 elements per thread per tile
 // survivor goes to the front.
 template <typename T, int kNtd, int kFold = 0, bool kSplit = false>
 __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
-  using ScanT = typename std::conditional<kSplit, unsigned long long, uint32_t>::type;
-  __shared__ ScanT s_scan[33];
-  __shared__ uint32_t s_base[3];
   const uint64_t head = a.head;
   const uint64_t npairs = (a.n - head) / 2;
   const uint64_t tile_pairs = (uint64_t)blockDim.x * kPairsPerThread;
@@ -186,32 +150,36 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
     const uint32_t m64 = dhi & ~dlo, n32 = __popc(dhi & dlo);
     const uint32_t n64f = __popc(kSplit ? (m64 & s1) : m64);
     const uint32_t n64b = kSplit ? __popc(m64 & ~s1) : 0u;
-    // counts fit in 16 bits each (<= 8 per thread, <= 8192 per block); the
-    // split form packs three counts in 21-bit fields of a 64-bit word
-    ScanT total;
-    const ScanT packed = kSplit ? (ScanT)n64f | ((ScanT)n64b << 21) | ((ScanT)n32 << 42)
-                                : (ScanT)n64f | ((ScanT)n32 << 16);
-    const ScanT pre = block_exclusive_scan<ScanT>(packed, s_scan, &total);
-    constexpr int kSh32 = kSplit ? 42 : 16;
-    constexpr ScanT kMask = kSplit ? (ScanT)0x1FFFFF : (ScanT)0xFFFF;
-    if (threadIdx.x == 0) {
-      const uint32_t tf = (uint32_t)(total & kMask), t32 = (uint32_t)(total >> kSh32);
-      const uint32_t tb = kSplit ? (uint32_t)((total >> 21) & kMask) : 0u;
-      s_base[0] = tf ? atomicAdd(&a.counters[0], tf) : 0u;
-      s_base[1] = t32 ? atomicAdd(&a.counters[1], t32) : 0u;
-      s_base[2] = tb ? atomicAdd(&a.counters[4], tb) : 0u;
+    // Warp-aggregated appends: the three counts (at most 8 per thread, 256 per
+    // warp) packed in 10-bit fields, an exclusive scan over the warp, and one
+    // atomic per queue per warp (no barrier, no shared memory).
+    const int lane = threadIdx.x & 31;
+    const uint32_t packed = n64f | (n64b << 10) | (n32 << 20);
+    uint32_t incl = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t pre = incl - packed;
+    const uint32_t wtot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    uint32_t bf = 0, bb = 0, b32 = 0;
+    if (lane == 0) {
+      const uint32_t tf = wtot & 0x3FFu, tb = (wtot >> 10) & 0x3FFu, t32 = wtot >> 20;
+      if (tf) bf = atomicAdd(&a.counters[0], tf);
+      if (tb) bb = atomicAdd(&a.counters[4], tb);
+      if (t32) b32 = atomicAdd(&a.counters[1], t32);
     }
     if (a.invalid || a.invalid_ctx) {
       const unsigned bad = __reduce_add_sync(0xFFFFFFFFu, nbad);
-      if ((threadIdx.x & 31) == 0 && bad) {
+      if (lane == 0 && bad) {
         if (a.invalid) atomicAdd(a.invalid, (unsigned long long)bad);
         if (a.invalid_ctx) atomicAdd(a.invalid_ctx, (unsigned long long)bad);
       }
     }
-    __syncthreads();
-    uint32_t pos64 = s_base[0] + (uint32_t)(pre & kMask);
-    uint32_t pos32 = s_base[1] + (uint32_t)(pre >> kSh32);
-    uint32_t posb = kSplit ? s_base[2] + (uint32_t)((pre >> 21) & kMask) : 0u;
+    uint32_t pos64 = __shfl_sync(0xFFFFFFFFu, bf, 0) + (pre & 0x3FFu);
+    uint32_t posb = __shfl_sync(0xFFFFFFFFu, bb, 0) + ((pre >> 10) & 0x3FFu);
+    uint32_t pos32 = __shfl_sync(0xFFFFFFFFu, b32, 0) + (pre >> 20);
 #pragma unroll
     for (int k = 0; k < kPairsPerThread; ++k) {
       const uint64_t p = tile * tile_pairs + (uint64_t)k * blockDim.x + threadIdx.x;
@@ -244,7 +212,6 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
         }
       }
     }
-    __syncthreads();  // s_base / s_scan are reused by the next tile
   }
   // Alignment head (at most one element) and odd tail (at most one).
   if (blockIdx.x == 0 && threadIdx.x == 0) {

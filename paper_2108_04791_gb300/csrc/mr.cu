@@ -240,6 +240,7 @@ struct MrOpts {
   uint32_t compact_min = 33;
   int ilp = 1;        // base2_ilp
   int rest_win = 4;   // rest_window
+  int b2_per_sm = 0;  // base2_blocks_per_sm (0: as many as fit)
 };
 
 // Modes 1 and 4 run one wave of resident blocks (the kernel balances the
@@ -247,10 +248,13 @@ struct MrOpts {
 // 16 x block words of shared memory.
 template <int kImpl, int kMode, int kRest, int kIlp>
 static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
-                             uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s) {
+                             uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s,
+                             int per_sm_cap) {
   const size_t smem = (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t) : 0;
   const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, kMode, kRest, kIlp>);
   grid = resident_grid(fn, block, smem, sm_count, grid);
+  if (per_sm_cap > 0 && sm_count > 0 && grid > (unsigned)(sm_count * per_sm_cap))
+    grid = (unsigned)(sm_count * per_sm_cap);
   mr64_base2_kernel<kImpl, kMode, kRest, kIlp><<<grid, block, smem, s>>>(
       q.q64_n, q.q64_idx, q.counters, q.q64b, out, compact_min, mark, (uint32_t)q.capacity);
 }
@@ -261,13 +265,17 @@ static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsi
   if (o.compact_min > 32) {
     // two survivors per thread: formulation 6, estimated-quotient windows
     if ((kImpl == 6 || kImpl == 16) && kMode == 1 && o.ilp == 2)
-      launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+      launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                       o.b2_per_sm);
     else
-      launch_base2_win<kImpl, kMode, 0, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+      launch_base2_win<kImpl, kMode, 0, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                           o.b2_per_sm);
   } else if (o.lucas == 1) {
-    launch_base2_win<kImpl, kMode, 2, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+    launch_base2_win<kImpl, kMode, 2, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                         o.b2_per_sm);
   } else {
-    launch_base2_win<kImpl, kMode, 1, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s);
+    launch_base2_win<kImpl, kMode, 1, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                         o.b2_per_sm);
   }
 }
 
@@ -388,6 +396,7 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
   o.compact_min = ctx->tune.compact_min;
   o.ilp = (int)ctx->tune.base2_ilp;
   o.rest_win = (int)ctx->tune.rest_window;
+  o.b2_per_sm = (int)ctx->tune.base2_blocks_per_sm;
   if (ctx->count_ops) {  // isprime_count_ops: formulation 6 with its operations counted
     o.impl_b2 = 16;
     o.impl = 17;

@@ -19,8 +19,12 @@
 
 namespace ip {
 
+// Segments: 512 words (32,768 integers) per block; windows too short to give
+// every SM a few such blocks take 64-word segments (4,096 integers), which
+// repeat the per-prime set-up eight times as often but fill the GPU.
 constexpr int kRangeSegWords = 512;                 // 16,384 odd values per segment
 constexpr int kRangeSegInts = kRangeSegWords * 64;  // integers covered by a segment
+constexpr int kRangeSegWordsSmall = 64;
 constexpr int kRangeThreads = 256;
 constexpr uint64_t kSieveComplete = 65537ull * 65537ull;  // all primes < 2^16 sieve below this
 
@@ -85,20 +89,22 @@ __device__ __forceinline__ void range_clear(uint32_t* seg, uint32_t j) {
   atomicAnd(&seg[j >> 5], ~(1u << (j & 31)));
 }
 
-// Block b sieves the integers [S0, S0 + kRangeSegInts), S0 = even base of the
-// chunk + b * kRangeSegInts.  Bit j of the segment <-> the odd value S0 + 2j + 1.
+// Block b sieves the integers [S0, S0 + kSegInts), S0 = even base of the
+// chunk + b * kSegInts.  Bit j of the segment <-> the odd value S0 + 2j + 1.
+template <int kSegWords>
 __global__ void __launch_bounds__(kRangeThreads) range_sieve_kernel(RangeArgs a) {
-  __shared__ uint32_t seg[kRangeSegWords];
+  constexpr uint32_t kSegInts = kSegWords * 64;
+  __shared__ uint32_t seg[kSegWords];
   __shared__ uint32_t s_scan[33];
   __shared__ uint32_t s_base;
   const uint32_t tid = threadIdx.x;
   const uint64_t base0 = a.lo & ~1ull;
-  const uint64_t S0 = base0 + (uint64_t)blockIdx.x * kRangeSegInts;
+  const uint64_t S0 = base0 + (uint64_t)blockIdx.x * kSegInts;
   // last value of the chunk and of this segment (no overflow: the window ends at or below 2^64 - 1)
   const uint64_t last = a.lo + (a.count - 1);
-  const uint64_t seg_last = (last - S0 < (uint64_t)kRangeSegInts) ? last : S0 + kRangeSegInts - 1;
+  const uint64_t seg_last = (last - S0 < (uint64_t)kSegInts) ? last : S0 + kSegInts - 1;
 
-  for (uint32_t w = tid; w < kRangeSegWords; w += kRangeThreads) seg[w] = 0xFFFFFFFFu;
+  for (uint32_t w = tid; w < kSegWords; w += kRangeThreads) seg[w] = 0xFFFFFFFFu;
   __syncthreads();
   // cross off odd multiples m >= max(p^2, S0) of every odd prime p with p^2 <= seg_last
   const uint32_t np = *a.nprimes;
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kRangeThreads) range_sieve_kernel(RangeArgs a)
     if (!(off & 1)) off += p;  // S0 even, p odd: an even offset gives an even multiple
     const uint64_t p2 = p * p;
     if (S0 < p2 && S0 + off < p2) off = p2 - S0;  // p2 - S0 is odd here
-    if (off >= (uint64_t)kRangeSegInts) return false;
+    if (off >= (uint64_t)kSegInts) return false;
     *j0 = (uint32_t)((off - 1) >> 1);
     return true;
   };
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(kRangeThreads) range_sieve_kernel(RangeArgs a)
     if (p >= 2048) break;
     uint32_t j0;
     if (!first_bit(p, &j0)) continue;
-    for (uint32_t j = j0 + lane * (uint32_t)p; j < kRangeSegWords * 32u; j += 32u * (uint32_t)p)
+    for (uint32_t j = j0 + lane * (uint32_t)p; j < kSegWords * 32u; j += 32u * (uint32_t)p)
       range_clear(seg, j);
   }
   uint32_t i_split = 0;
@@ -136,13 +142,13 @@ __global__ void __launch_bounds__(kRangeThreads) range_sieve_kernel(RangeArgs a)
     if (p * p > seg_last) break;
     uint32_t j0;
     if (!first_bit(p, &j0)) continue;
-    for (uint32_t j = j0; j < kRangeSegWords * 32u; j += (uint32_t)p) range_clear(seg, j);
+    for (uint32_t j = j0; j < kSegWords * 32u; j += (uint32_t)p) range_clear(seg, j);
   }
   __syncthreads();
 
   // Outputs: thread t writes values S0 + t, S0 + t + B, ... (coalesced bytes);
   // survivors that the sieve cannot decide are appended to the queue.
-  for (uint32_t r = 0; r < (uint32_t)kRangeSegInts; r += kRangeThreads) {
+  for (uint32_t r = 0; r < (uint32_t)kSegInts; r += kRangeThreads) {
     const uint64_t off = r + tid;
     const uint64_t v = S0 + off;
     const bool inside = off <= seg_last - S0 && v >= a.lo;
@@ -224,7 +230,13 @@ int launch_range_sieve(isprime_ctx* ctx, const RangeArgs& a, cudaStream_t s) {
   TimedLaunch tl;
   int st = launch_begin(ctx, ISPRIME_K_RANGE, s, &tl);
   if (st) return st;
-  range_sieve_kernel<<<(unsigned)nseg, kRangeThreads, 0, s>>>(a);
+  if (nseg < 4 * (uint64_t)ctx->sm_count) {
+    constexpr uint64_t kSmallInts = (uint64_t)kRangeSegWordsSmall * 64;
+    const uint64_t nsmall = (last - base0) / kSmallInts + 1;
+    range_sieve_kernel<kRangeSegWordsSmall><<<(unsigned)nsmall, kRangeThreads, 0, s>>>(a);
+  } else {
+    range_sieve_kernel<kRangeSegWords><<<(unsigned)nseg, kRangeThreads, 0, s>>>(a);
+  }
   return launch_end(ctx, s, &tl, "range_sieve_kernel");
 }
 

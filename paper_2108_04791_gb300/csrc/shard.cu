@@ -3,7 +3,9 @@
 // The result for each element depends on that element alone (Sec. 1), so a
 // job splits across devices with no data exchange: contiguous ranges of a
 // plain array, whole arrays of a batch balanced by size, and served requests
-// sent to the least-loaded device.  Nothing here touches a device.
+// sent to the least-loaded device.  The planners touch no device;
+// isprime_u64_host_multi runs a plain job on several devices by the
+// contiguous plan, one host thread per device, with no exchange between them.
 // The batch plan is longest-processing-time first (Graham, SIAM J. Appl.
 // Math. 17, 1969): its largest shard is at most (4/3 - 1/(3k)) of the best
 // possible for k shards, and at most the mean plus the largest array.
@@ -11,6 +13,7 @@
 #include <functional>
 #include <numeric>
 #include <queue>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -57,6 +60,42 @@ int isprime_route_least_loaded(const uint64_t* outstanding, uint32_t n_devices, 
   for (uint32_t d = 1; d < n_devices; ++d)
     if (outstanding[d] < outstanding[best]) best = d;
   *device = best;
+  return ISPRIME_OK;
+}
+
+int isprime_u64_host_multi(const int* devices, uint32_t n_devices, const uint64_t* h_in,
+                           uint8_t* h_out, size_t n) {
+  IP_NVTX("isprime_u64_host_multi");
+  if (n_devices == 0 || !devices) return ip::set_error(ISPRIME_EINVAL, "no devices given");
+  if (n == 0) return ISPRIME_OK;
+  if (!h_in || !h_out) return ip::set_error(ISPRIME_EINVAL, "NULL pointer with n > 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) ndev = 0;
+  for (uint32_t k = 0; k < n_devices; ++k)
+    if (devices[k] < 0 || devices[k] >= ndev) return ip::set_error(ISPRIME_EINVAL, "device out of range");
+  std::vector<uint64_t> begin(n_devices + 1);
+  isprime_plan_contiguous(n, n_devices, begin.data());
+  // contexts first (building a device's resident sieve is not thread-safe
+  // with that device's other first uses), then one thread per shard
+  std::vector<isprime_ctx*> ctx(n_devices, nullptr);
+  for (uint32_t k = 0; k < n_devices; ++k) {
+    int st = isprime_default_ctx(devices[k], &ctx[k]);
+    if (st) return st;
+  }
+  std::vector<int> status(n_devices, ISPRIME_OK);
+  std::vector<std::string> error(n_devices);
+  std::vector<std::thread> threads;
+  for (uint32_t k = 0; k < n_devices; ++k) {
+    const uint64_t b = begin[k], len = begin[k + 1] - begin[k];
+    if (len == 0) continue;
+    threads.emplace_back([&, k, b, len] {
+      status[k] = isprime_u64_host(ctx[k], h_in + b, h_out + b, len, nullptr);
+      if (status[k]) error[k] = isprime_last_error();
+    });
+  }
+  for (auto& t : threads) t.join();
+  for (uint32_t k = 0; k < n_devices; ++k)
+    if (status[k]) return ip::set_error(status[k], "device " + std::to_string(devices[k]) + ": " + error[k]);
   return ISPRIME_OK;
 }
 

@@ -108,16 +108,16 @@ __global__ void window_fill_kernel(uint64_t* v, uint64_t n, uint64_t lo, uint64_
 }
 
 // Fits the crossover of the window path on this GPU for arrays whose values
-// lie near `near` (autotuner).  On n = 2^k distinct values filling a window
-// of n and of 4n integers (densities 1 and 1/4), times the queue path and
+// lie near `near` (autotuner).  On m = 2^22 distinct values filling a window
+// of m and of 4m integers (densities 1 and 1/4), times the queue path and
 // the window path; with the window path's time linear in the window width
 // W, t_win(W) = alpha + beta W, the window path wins for W < (t_queue -
 // alpha) / beta, so ratio16 = 16 (t_queue - alpha) / (beta n) (0 when it
 // never wins).  The context's tuning is left as it was.
 int window_fit(isprime_ctx* ctx, uint64_t near, size_t n, cudaStream_t s, uint32_t* ratio16) {
   *ratio16 = 0;
-  size_t m = (size_t)1 << 16;
-  while (m * 2 <= n && m * 2 <= ((size_t)1 << 22)) m *= 2;
+  (void)n;
+  const size_t m = (size_t)1 << 22;  // a size that fills the GPU in both arms
   uint64_t lo = near > 4 * (uint64_t)m ? near - 4 * (uint64_t)m : 0;
   const uint64_t cut = sieve_cut(ctx);
   if (lo < cut) lo = cut;

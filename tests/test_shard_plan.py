@@ -140,3 +140,19 @@ def test_two_gloo_ranks_split_a_batch_by_plan():
     assert sorted(done) == list(range(len(sizes)))
     got = np.concatenate([done[a] for a in range(len(sizes))])
     assert np.array_equal(got, oracle.isprime_u64(vals))
+
+
+def test_host_multi_rejects_bad_arguments_without_a_device():
+    """Argument errors of isprime_u64_host_multi come before any device is used."""
+    import ctypes
+    L = ipg.lib()
+    a = np.arange(10, dtype=np.uint64)
+    o = np.zeros(10, dtype=np.uint8)
+    d = np.array([0], dtype=np.int32)
+    assert L.isprime_u64_host_multi(d.ctypes.data, 0, a.ctypes.data, o.ctypes.data, 10) == ipg.EINVAL
+    assert L.isprime_u64_host_multi(None, 1, a.ctypes.data, o.ctypes.data, 10) == ipg.EINVAL
+    assert L.isprime_u64_host_multi(d.ctypes.data, 1, None, o.ctypes.data, 10) == ipg.EINVAL
+    assert L.isprime_u64_host_multi(d.ctypes.data, 1, a.ctypes.data, o.ctypes.data, 0) == ipg.OK
+    bad = np.array([-1], dtype=np.int32)
+    assert L.isprime_u64_host_multi(bad.ctypes.data, 1, a.ctypes.data, o.ctypes.data, 10) == ipg.EINVAL
+    assert ctypes.c_char_p(L.isprime_last_error()).value
