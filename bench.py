@@ -541,8 +541,9 @@ def batched_record(ctx, dev, steps: int, warm: int, world: int, with_cpu: bool) 
                               "calls_per_step": len(ins)},
            "speedup_vs_plain_calls": value / plain_value,
            "roofline": roof, "gpu_launches": launches, "clocks": clk,
-           "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]} for k, v in kt.items()
-                       if v[1]}}
+           "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in kt.items()
+                       if v[1]},
+           "kernels_note": "the launches include the warm-up replays"}
     if with_cpu:
         rec["cpu_baseline"] = _cpu_rate_on(d_all[: 1 << 24].cpu().numpy().view(np.uint64), 4.0,
                                            "the batch (arrays in order)")

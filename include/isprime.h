@@ -67,11 +67,13 @@ typedef struct {
                               product with PTX word-level reduction, 3 fused product scanning,
                               4 128-bit multiply with fused squaring, 5 128-bit product with
                               squaring as a general multiply, 6 128-bit form in 32-bit words
-                              (PTX, wide products and carry chains, no m0 n0 product; default),
+                              (PTX, wide products and carry chains, no m0 n0 product),
                               7 formulation 6 with the partial sums carried in the wide
                               products' 64-bit addends, 8 formulation 7 with squaring as a
-                              general multiply */
-  uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..8) */
+                              general multiply, 9 formulation 6 with its final "+ n when
+                              negative" as multiply-adds (multiply pipe) instead of ANDs and
+                              adds (ALU pipe; default) */
+  uint32_t mont_impl_base2;/* the same choice for the base-2 kernel (0..9) */
   uint32_t batch_block;    /* threads per block of the batched kernel (32..256, multiple of 32; the
                               shared memory of batch_block and batch_tile_log2 must fit a block) */
   uint32_t batch_tile_log2;/* elements per tile of the batched kernel = 2^batch_tile_log2 (8..14) */
@@ -107,9 +109,9 @@ typedef struct {
                               queued apart from the others, so the base-2 kernel's warps of those
                               run no strong-test tail; 0: one queue */
   uint32_t base2_ilp;      /* survivors per thread in the base-2 kernel (1 or 2; 2 takes effect
-                              with base2_window 1, mont_impl_base2 6 and compact_min 33) */
+                              with base2_window 1, mont_impl_base2 6 or 9 and compact_min 33) */
   uint32_t rest_window;    /* window bits of the six-base exponentiations (3 or 4; 3 takes effect
-                              with mont_impl 6) */
+                              with mont_impl 6 or 9) */
   uint32_t window_ratio16; /* per-call path choice of the uint64 array entry points (Sec. 6.2's
                               choice between sieving up to max(N) and testing each element):
                               0 never (default); otherwise a call of at least 2^16 values reads

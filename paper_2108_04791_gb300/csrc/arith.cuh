@@ -260,6 +260,74 @@ __device__ __forceinline__ uint64_t mont_sqr_c(uint64_t a, uint64_t n, uint64_t 
       IP_MONT_C_TAIL "}" IP_MONT_C_OPERANDS);
   return ((uint64_t)r1 << 32) | r0;
 }
+// Formulation 9: formulation 6 with the final "+ n when negative" done on the
+// multiply pipe: the borrow becomes b in {0, 1} and r + b n is two
+// multiply-adds with carry (mad.lo.cc / madc.lo) instead of two ANDs and two
+// adds on the ALU pipe.  The arithmetic is the same; only the pipe that does
+// the correction changes (for kernels whose ALU pipe is the busier one).
+#define IP_MONT_E_TAIL(prefix)                                                  \
+  prefix                                                                        \
+  "sub.cc.u32 bo, t1, sl;\n\t"                                                  \
+  "subc.cc.u32 %0, t2, x;\n\t"                                                  \
+  "subc.cc.u32 %1, t3, y;\n\t"                                                  \
+  "subc.u32 bo, 0, 0;\n\t"                                                      \
+  "and.b32 bo, bo, 1;\n\t"                                                      \
+  "mad.lo.cc.u32 %0, bo, %6, %0;\n\t"                                           \
+  "madc.lo.u32 %1, bo, %7, %1;\n\t"
+#define IP_MONT_E_BODY                                                          \
+  /* p11 and t = a b = t3:t2:t1:p00l */                                         \
+  "mul.wide.u32 w, %3, %5;\n\t"                                                 \
+  "mov.b64 {p11l, p11h}, w;\n\t"                                                \
+  "add.cc.u32 t1, p00h, p01l;\n\t"                                              \
+  "addc.cc.u32 t2, p01h, p11l;\n\t"                                             \
+  "addc.u32 t3, p11h, 0;\n\t"                                                   \
+  "add.cc.u32 t1, t1, p10l;\n\t"                                                \
+  "addc.cc.u32 t2, t2, p10h;\n\t"                                               \
+  "addc.u32 t3, t3, 0;\n\t"                                                     \
+  "mul.wide.u32 w, p00l, %8;\n\t"                                               \
+  "mov.b64 {m0, m1}, w;\n\t"                                                    \
+  "mad.lo.u32 m1, p00l, %9, m1;\n\t"                                            \
+  "mad.lo.u32 m1, t1, %8, m1;\n\t"                                              \
+  "mul.wide.u32 w, m0, %7;\n\t"                                                 \
+  "mov.b64 {q01l, q01h}, w;\n\t"                                                \
+  "mul.wide.u32 w, m1, %6;\n\t"                                                 \
+  "mov.b64 {q10l, q10h}, w;\n\t"                                                \
+  "mul.wide.u32 w, m1, %7;\n\t"                                                 \
+  "mov.b64 {q11l, q11h}, w;\n\t"                                                \
+  "add.cc.u32 sl, q01l, q10l;\n\t"                                              \
+  "addc.cc.u32 x, q11l, q01h;\n\t"                                              \
+  "addc.u32 y, q11h, 0;\n\t"                                                    \
+  "add.cc.u32 x, x, q10h;\n\t"                                                  \
+  "addc.u32 y, y, 0;\n\t"
+
+__device__ __forceinline__ uint64_t mont_mul_e(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) {
+  IP_MONT_C_DECL
+  asm("{\n\t" IP_MONT_C_REGS
+      "mul.wide.u32 w, %2, %4;\n\t"
+      "mov.b64 {p00l, p00h}, w;\n\t"
+      "mul.wide.u32 w, %2, %5;\n\t"
+      "mov.b64 {p01l, p01h}, w;\n\t"
+      "mul.wide.u32 w, %3, %4;\n\t"
+      "mov.b64 {p10l, p10h}, w;\n\t"
+      IP_MONT_E_TAIL(IP_MONT_E_BODY) "}" IP_MONT_C_OPERANDS);
+  return ((uint64_t)r1 << 32) | r0;
+}
+
+__device__ __forceinline__ uint64_t mont_sqr_e(uint64_t a, uint64_t n, uint64_t ninv) {
+  const uint64_t b = a;
+  IP_MONT_C_DECL
+  asm("{\n\t" IP_MONT_C_REGS
+      "mul.wide.u32 w, %2, %4;\n\t"
+      "mov.b64 {p00l, p00h}, w;\n\t"
+      "mul.wide.u32 w, %2, %5;\n\t"
+      "mov.b64 {p01l, p01h}, w;\n\t"
+      "mov.u32 p10l, p01l;\n\t"
+      "mov.u32 p10h, p01h;\n\t"
+      IP_MONT_E_TAIL(IP_MONT_E_BODY) "}" IP_MONT_C_OPERANDS);
+  return ((uint64_t)r1 << 32) | r0;
+}
+#undef IP_MONT_E_TAIL
+#undef IP_MONT_E_BODY
 #undef IP_MONT_C_DECL
 #undef IP_MONT_C_REGS
 #undef IP_MONT_C_TAIL
@@ -520,6 +588,7 @@ IP_HD Mont64 mont64_setup(uint64_t n) {
 //   6: 128-bit form in 32-bit words as PTX, no m0 n0 product (device)
 //   7: formulation 6 with the partial sums in the wide products' addends
 //   8: formulation 7, squaring as a general multiplication
+//   9: formulation 6 with the final correction on the multiply pipe
 template <int kImpl>
 struct MontOps;
 
@@ -564,6 +633,16 @@ struct MontOps<6> {
   }
   static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
     return mont_sqr_c(a, M.n, M.ninv);
+  }
+};
+
+template <>
+struct MontOps<9> {
+  static __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b, const Mont64& M) {
+    return mont_mul_e(a, b, M.n, M.ninv);
+  }
+  static __device__ __forceinline__ uint64_t sqr(uint64_t a, const Mont64& M) {
+    return mont_sqr_e(a, M.n, M.ninv);
   }
 };
 

@@ -26,6 +26,12 @@
 
 namespace ip {
 
+// Arithmetic: Montgomery formulation 6 (32-bit words in PTX) in both stages,
+// 3-bit windows for the six bases (as the plain path's default), and folded
+// trial division when the count is the default 15 primes.
+constexpr int kImplB2 = 6, kImplRest = 6;
+constexpr int kBatchWin = 3;
+
 struct BatchParams {
   const BatchDesc* descs;
   const BatchHeader* hdr;
@@ -56,13 +62,12 @@ __device__ __forceinline__ void smem_push(bool want, uint64_t v, uint64_t addr, 
 }
 
 // Shared-memory bytes of one block: Q1 (tile + block entries), Q2 (2 block
-// entries), 16 bytes per entry, plus the window tables (kTab per thread).
+// entries), 16 bytes per entry, plus the window tables (2^kBatchWin per thread).
 size_t batched_smem_bytes(uint32_t block, uint32_t tile) {
-  return (size_t)(tile + block) * 16 + (size_t)(2 * block) * 16 + (size_t)kTab * block * 8;
+  return (size_t)(tile + block) * 16 + (size_t)(2 * block) * 16 +
+         ((size_t)1 << kBatchWin) * block * 8;
 }
 
-// Arithmetic: Montgomery formulation 6 (32-bit words in PTX) in both stages.
-constexpr int kImplB2 = 6, kImplRest = 6;
 
 template <int kNtd, bool kLucas>
 __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
@@ -116,7 +121,8 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
     if (tid == 0) s_n2 = n2 - cnt;
     if (kLucas) {  // every thread of the block takes part (warp-synchronous test)
       if (lucas_warp<kImplRest>(mine ? v : 0xFFFFFFFFFFFFFFC5ull, mine)) *reinterpret_cast<uint8_t*>(a) = 1;
-    } else if (rest64_is_prime_warp<kImplRest>(mine ? v : 0xFFFFFFFFFFFFFFC5ull, mine, tab, (int)B)) {
+    } else if (rest64_is_prime_warp<kImplRest, kBatchWin>(mine ? v : 0xFFFFFFFFFFFFFFC5ull, mine, tab,
+                                                          (int)B)) {
       *reinterpret_cast<uint8_t*>(a) = 1;
     }
     __syncthreads();
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
       uint64_t v = 0;
       if (e < e1) {
         v = d.in[e];
-        dec = classify_value<kNtd>(v, p);
+        dec = classify_value<kNtd, BatchParams, false, (kNtd == 15 ? 2 : 0)>(v, p);
         if (IP_CHECK(e < d.n, kChkBatchOut)) d.out[e] = (uint8_t)(dec == kPrime);
       }
       smem_push(dec == kMR64 || dec == kMR32, v, (uint64_t)(d.out + e), q1v, q1a, &s_n1, q1cap);

@@ -189,20 +189,17 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
         const int j = 2 * k + h;
         const int dj = (int)((dm >> (2 * j)) & 3u);
         if (dj == kMR64) {
-          if (!kSplit || ((s1 >> (2 * j)) & 1u)) {
-            if (IP_CHECK(pos64 < a.q64_cap, kChkQ64Front)) {
-              a.q64_n[pos64] = v[j];
-              a.q64_idx[pos64] = i0 + h;
-            }
-            ++pos64;
-          } else {
-            const uint32_t pb = a.q64_cap - 1u - posb;
-            if (IP_CHECK(posb < a.q64_cap, kChkQ64Back)) {
-              a.q64_n[pb] = v[j];
-              a.q64_idx[pb] = i0 + h;
-            }
-            ++posb;
+          // the front slot for s = 1 (or without the split), else the back one;
+          // one store path either way, so the warp does not split here
+          const bool front = !kSplit || ((s1 >> (2 * j)) & 1u);
+          const uint32_t slot = front ? pos64 : a.q64_cap - 1u - posb;
+          if (IP_CHECK(front ? pos64 < a.q64_cap : posb < a.q64_cap,
+                       front ? kChkQ64Front : kChkQ64Back)) {
+            a.q64_n[slot] = v[j];
+            a.q64_idx[slot] = i0 + h;
           }
+          pos64 += front ? 1u : 0u;
+          posb += front ? 0u : 1u;
         } else if (dj == kMR32) {
           if (IP_CHECK(pos32 < a.q64_cap, kChkQ32)) {
             a.q32_n[pos32] = (uint32_t)v[j];

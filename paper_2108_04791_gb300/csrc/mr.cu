@@ -264,7 +264,7 @@ static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsi
                               const MrOpts& o, uint32_t mark, int sm_count, cudaStream_t s) {
   if (o.compact_min > 32) {
     // two survivors per thread: formulation 6, estimated-quotient windows
-    if ((kImpl == 6 || kImpl == 16) && kMode == 1 && o.ilp == 2)
+    if ((kImpl == 6 || kImpl == 9 || kImpl == 16) && kMode == 1 && o.ilp == 2)
       launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s,
                                        o.b2_per_sm);
     else
@@ -318,7 +318,7 @@ static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned b
   if (o.lucas) {
     mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
                                                                 out, 0u, (uint32_t)q.capacity);
-  } else if ((kImpl == 6 || kImpl == 17) && o.rest_win == 3) {
+  } else if ((kImpl == 6 || kImpl == 9 || kImpl == 17) && o.rest_win == 3) {
     launch_rest_w<kImpl, 3>(q, out, grid, block, spread_grid, sm_count, s);
   } else {
     launch_rest_w<kImpl, kWin>(q, out, grid, block, spread_grid, sm_count, s);
@@ -346,6 +346,7 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
     case 6: launch_base2<6>(q, out, grid, block, o, mark, sm_count, s); break;
     case 7: launch_base2<7>(q, out, grid, block, o, mark, sm_count, s); break;
     case 8: launch_base2<8>(q, out, grid, block, o, mark, sm_count, s); break;
+    case 9: launch_base2<9>(q, out, grid, block, o, mark, sm_count, s); break;
     case 16: launch_base2<16>(q, out, grid, block, o, mark, sm_count, s); break;
     default: launch_base2<0>(q, out, grid, block, o, mark, sm_count, s); break;
   }
@@ -360,6 +361,7 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
     case 6: launch_rest<6>(q, out, grid, block, o, spread_grid, sm_count, s); break;
     case 7: launch_rest<7>(q, out, grid, block, o, spread_grid, sm_count, s); break;
     case 8: launch_rest<8>(q, out, grid, block, o, spread_grid, sm_count, s); break;
+    case 9: launch_rest<9>(q, out, grid, block, o, spread_grid, sm_count, s); break;
     case 17: launch_rest<17>(q, out, grid, block, o, spread_grid, sm_count, s); break;
     default: launch_rest<0>(q, out, grid, block, o, spread_grid, sm_count, s); break;
   }

@@ -99,29 +99,31 @@ int array_minmax(isprime_ctx* ctx, const uint64_t* d_in, size_t n, cudaStream_t 
   return ISPRIME_OK;
 }
 
-// v[i] = lo + (i a mod w) for i < n: n distinct values of the window
-// [lo, lo + w) when w is a power of two, a is odd and n <= w.
+// v[i] = lo + (i a mod w) for i < n, w a power of two and a odd: every
+// integer of the window [lo, lo + w) equally often (n >= w) or n distinct
+// ones (n <= w).
 __global__ void window_fill_kernel(uint64_t* v, uint64_t n, uint64_t lo, uint64_t w, uint64_t a) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x)
     v[i] = lo + ((i * a) & (w - 1));
 }
 
-// Fits the crossover of the window path on this GPU for arrays whose values
-// lie near `near` (autotuner).  On m = 2^22 distinct values filling a window
-// of m and of 4m integers (densities 1 and 1/4), times the queue path and
-// the window path; with the window path's time linear in the window width
-// W, t_win(W) = alpha + beta W, the window path wins for W < (t_queue -
-// alpha) / beta, so ratio16 = 16 (t_queue - alpha) / (beta n) (0 when it
-// never wins).  The context's tuning is left as it was.
+// Fits the crossover of the window path on this GPU for arrays of about n
+// values near `near` (autotuner).  On m values (n rounded down to a power of
+// two in [2^16, 2^24]) spread over windows of m/4 and of m integers
+// (densities 4 and 1), times the queue path and the window path; with the
+// window path's time linear in the window width W, t_win(W) = alpha + beta W,
+// it wins for W < W* = (t_queue - alpha) / beta, so ratio16 = 16 W* / m (0
+// when W* <= 0: the fixed cost alone exceeds the queue path's time).  The
+// context's tuning is left as it was.
 int window_fit(isprime_ctx* ctx, uint64_t near, size_t n, cudaStream_t s, uint32_t* ratio16) {
   *ratio16 = 0;
-  (void)n;
-  const size_t m = (size_t)1 << 22;  // a size that fills the GPU in both arms
-  uint64_t lo = near > 4 * (uint64_t)m ? near - 4 * (uint64_t)m : 0;
+  size_t m = (size_t)1 << 16;
+  while (m * 2 <= n && m * 2 <= ((size_t)1 << 24)) m *= 2;
+  uint64_t lo = near > (uint64_t)m ? near - (uint64_t)m : 0;
   const uint64_t cut = sieve_cut(ctx);
   if (lo < cut) lo = cut;
-  if (lo > UINT64_MAX - 4 * (uint64_t)m) lo = UINT64_MAX - 4 * (uint64_t)m;
+  if (lo > UINT64_MAX - (uint64_t)m) lo = UINT64_MAX - (uint64_t)m;
   uint64_t* d_v = nullptr;
   uint8_t* d_o = nullptr;
   IP_CUDA(cudaMalloc(&d_v, m * sizeof(uint64_t)));
@@ -155,19 +157,19 @@ int window_fit(isprime_ctx* ctx, uint64_t near, size_t n, cudaStream_t s, uint32
     }
     return ISPRIME_OK;
   };
-  float tq = 0, tw1 = 0, tw4 = 0;
+  float tq = 0, tw1 = 0, tw4 = 0;  // tw1: W = m / 4, tw4: W = m
   int st = timed((uint64_t)m, 0, &tq);
-  if (!st) st = timed((uint64_t)m, 4096, &tw1);
-  if (!st) st = timed(4 * (uint64_t)m, 4096, &tw4);
+  if (!st) st = timed((uint64_t)m / 4, 4096, &tw1);
+  if (!st) st = timed((uint64_t)m, 4096, &tw4);
   isprime_ctx_set_tuning(ctx, &saved);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(d_v);
   cudaFree(d_o);
   if (st) return st;
-  const double beta = (double)(tw4 - tw1) / (3.0 * (double)m);  // ms per window integer
-  const double alpha = (double)tw1 - beta * (double)m;
-  if (tw1 >= tq || beta <= 0) return ISPRIME_OK;
+  const double beta = (double)(tw4 - tw1) / (0.75 * (double)m);  // ms per window integer
+  const double alpha = (double)tw1 - beta * 0.25 * (double)m;
+  if (beta <= 0 || alpha >= (double)tq) return ISPRIME_OK;
   const double r = 16.0 * ((double)tq - alpha) / (beta * (double)m);
   *ratio16 = (uint32_t)std::min(4096.0, std::max(0.0, r));
   ctx->fitted_window_ratio16 = *ratio16;

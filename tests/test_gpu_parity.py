@@ -274,7 +274,9 @@ def test_tuning_does_not_change_results():
                    dict(mont_impl=7), dict(mont_impl=8), dict(mont_impl_base2=7),
                    dict(mont_impl_base2=8), dict(mont_impl=7, mont_impl_base2=8, base2_window=0),
                    dict(mont_impl=8, rest_test=1), dict(mont_impl_base2=7, base2_window=4),
-                   dict(mont_impl=7, compact_min=8),
+                   dict(mont_impl=7, compact_min=8), dict(mont_impl=9), dict(mont_impl_base2=9),
+                   dict(mont_impl=9, mont_impl_base2=9, base2_window=0),
+                   dict(mont_impl=9, rest_window=4), dict(mont_impl_base2=9, base2_window=4),
                    dict(compact_min=0), dict(compact_min=1), dict(compact_min=16),
                    dict(compact_min=4, rest_test=1), dict(compact_min=8, mont_impl_base2=5),
                    dict(compact_min=2, base2_window=0), dict(compact_min=33),

@@ -153,8 +153,20 @@ def test_variants_with_spread_rest_kernel(ctx):
             _same(v, _run(ctx, v), want, f"spread n={n} win={win}")
 
 
+@pytest.mark.parametrize("impl,impl_b2,ilp", [(9, 9, 1), (9, 9, 2), (6, 9, 1), (9, 6, 2)])
+def test_formulation_9_matches_oracle(impl, impl_b2, ilp, data, ctx):
+    """Formulation 9 (the final correction on the multiply pipe) in both stages."""
+    v, want = data
+    ctx.set_tuning(mont_impl=impl, mont_impl_base2=impl_b2, base2_ilp=ilp, td_fold=2,
+                   base2_split=1, rest_window=3, small_max=0, base2_window=1, compact_min=33)
+    try:
+        _same(v, _run(ctx, v), want, f"impl={impl} impl_b2={impl_b2} ilp={ilp}")
+    finally:
+        ctx.set_tuning(mont_impl=6, mont_impl_base2=6, base2_ilp=1)
+
+
 def test_tuning_rejects_out_of_range_variant_fields(ctx):
-    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
+    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0), dict(mont_impl=10), dict(mont_impl_base2=10),
                dict(rest_window=5), dict(rest_window=2)):
         with pytest.raises(ipg.IsPrimeError):
             ctx.set_tuning(**kw)

@@ -102,7 +102,7 @@ def test_autotuner_fits_and_installs_the_crossover():
     a given density is this GPU's measurement, tabulated by the benchmark);
     a sparse sample keeps the path off.  Results stay exact either way."""
     with ipg.Context(0, sieve_limit=1 << 24) as c:
-        n, w = 1 << 20, 1 << 18  # density 4: every window integer about four times
+        n, w = 1 << 22, 1 << 19  # density 8: every window integer about eight times
         v = _dense(1 << 44, w, n, seed=9)
         t = torch.from_numpy(v.view(np.int64)).to("cuda:0")
         tuned = c.autotune(t)
