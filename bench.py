@@ -328,9 +328,10 @@ def run_mine(args, world, rank, local):
 
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # The timed pass runs without the library's per-kernel timing events (they
+    # sit between the kernels on the stream and add their own gaps); a second
+    # pass below takes the per-kernel times.
     launches0 = ctx.stats()["kernel_launches"]
-    ctx.timing_reset()
-    ctx.timing(True)
     clocks = ClockSampler(local)
     clocks.start()
     _barrier(world)
@@ -345,12 +346,21 @@ def run_mine(args, world, rank, local):
     _barrier(world)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    ctx.timing(False)
     launches = ctx.stats()["kernel_launches"] - launches0
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
     total_s = sum(step_ms) / 1e3
     total_s = _max_over_ranks(total_s, world, dev)
     value = n * world * args.steps / total_s
+    # per-kernel times: a separate pass of the same steps with the library's
+    # CUDA events around every launch (on the launching stream)
+    k_steps = max(3, min(args.steps, 50))
+    ctx.timing_reset()
+    ctx.timing(True)
+    for k in range(k_steps):
+        flush.fill_(k & 0xFF)
+        ctx.isprime(d_in, out=out)
+    torch.cuda.synchronize(dev)
+    ctx.timing(False)
     ktimes = ctx.timing_read()
 
     # ---- roofline: the whole step, and the dominant kernel
@@ -396,7 +406,7 @@ def run_mine(args, world, rank, local):
                 "traffic_note": "DRAM bytes per step (sum of the three kernels) from the ncu "
                                 "capture whose source hash and tuning match this build; "
                                 "null otherwise"}
-    kernels = {k: {"ms_per_step": v[0] / max(args.steps, 1), "launches": v[1]}
+    kernels = {k: {"ms_per_step": v[0] / k_steps, "launches": v[1]}
                for k, v in ktimes.items() if v[1]}
 
     # ---- end to end through the C ABI with host buffers
@@ -427,6 +437,10 @@ def run_mine(args, world, rank, local):
     subs = {}
     if args.workload == "plain_large" and world == 1 and not args.no_sub:
         with_cpu = rank == 0 and not args.no_cpu_baseline
+        subs["plain_small"] = plain_record(ctx, dev, "plain_small", max(20, min(args.steps * 10, 200)),
+                                           with_cpu)
+        subs["plain_mixed"] = plain_record(ctx, dev, "plain_mixed", max(5, min(args.steps, 20)),
+                                           with_cpu)
         subs["batched"] = batched_record(ctx, dev, max(3, min(args.steps, 10)), 3, world, with_cpu)
         subs["served"] = served_record(ctx, dev, 3, world, rank, with_cpu)
 
@@ -486,6 +500,80 @@ def _cpu_rate_on(vals: np.ndarray, target_s: float, what: str) -> dict:
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {n} values of {what}, one pass, {cores} threads", "seconds": dt}
+
+
+def plain_record(ctx, dev, workload: str, steps: int, with_cpu: bool) -> dict:
+    """A plain workload through isprime_u64_ctx (plain_small: 10^5 values below
+    10^6, the launch-bound case; plain_mixed: 2^26 values of uniform bit
+    length, plus its 2^20 doubles through isprime_f64_ctx): device time per
+    call with inputs resident (L2 flushed between calls), the per-kernel times
+    from a second pass, and end to end through isprime_u64_host."""
+    import torch
+    import paper_2108_04791_gb300 as ipg
+    vals, desc = _workload(workload, 0)
+    n = vals.size
+    d_in = torch.from_numpy(vals.view(np.int64)).to(dev)
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, k):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for i in range(k):
+            flush.fill_(i & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tot += e0.elapsed_time(e1)
+        return tot / k
+
+    ms = timed(lambda: ctx.isprime(d_in, out=out), steps)
+    ctx.timing_reset()
+    ctx.timing(True)
+    k_steps = max(3, min(steps, 20))
+    for _ in range(k_steps):
+        ctx.isprime(d_in, out=out)
+    torch.cuda.synchronize(dev)
+    ctx.timing(False)
+    kt = ctx.timing_read()
+    h_in = torch.from_numpy(vals.view(np.int64)).pin_memory()
+    h_out = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hv, ho = h_in.numpy().view(np.uint64), h_out.numpy()
+    L = ipg.lib()
+    sh = ipg.ctypes.c_void_p(stream.cuda_stream)
+    for _ in range(2):
+        ipg._check(L.isprime_u64_host(ctx.handle, hv.ctypes.data, ho.ctypes.data, n, sh))
+    ke = max(3, min(steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ipg._check(L.isprime_u64_host(ctx.handle, hv.ctypes.data, ho.ctypes.data, n, sh))
+    e2e_s = (time.perf_counter() - t0) / ke
+    rec = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "config": _config(workload, n, desc, 1),
+           "kernels": {k: {"ms_per_step": v[0] / k_steps, "launches": v[1]} for k, v in kt.items()
+                       if v[1]},
+           "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": n, "steps": ke}}
+    if workload == "plain_mixed":
+        x = wg.mixed_doubles(1 << 20)
+        d_x = torch.from_numpy(x).to(dev)
+        o_x = torch.empty(x.size, dtype=torch.uint8, device=dev)
+        ms_f = timed(lambda: ctx.isprime(d_x, out=o_x), steps)
+        rec["doubles"] = {"value": x.size / (ms_f / 1e3), "unit": UNIT, "ms_per_step": ms_f,
+                          "elements": int(x.size),
+                          "description": "2^20 doubles holding integers uniform in [0, 2^53), "
+                                         "through isprime_f64_ctx"}
+        del d_x, o_x
+    if with_cpu:
+        rec["cpu_baseline"] = _cpu_rate_on(vals, 3.0, f"the {workload} array")
+    del d_in, out, flush
+    return rec
 
 
 def batched_record(ctx, dev, steps: int, warm: int, world: int, with_cpu: bool) -> dict:

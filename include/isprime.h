@@ -123,6 +123,10 @@ typedef struct {
                               autotuner measures the crossover on this GPU */
   uint32_t base2_blocks_per_sm; /* cap on resident blocks per SM of the base-2 kernel (a single
                               wave of persistent blocks; 0 = as many as fit, 1..32) */
+  uint32_t pdl;            /* 1: the Miller-Rabin kernels are launched with programmatic stream
+                              serialisation, so a launch overlaps the end of the kernel before it
+                              (each waits for that kernel before reading the queues; default);
+                              0: plain stream order */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -48,7 +48,8 @@ std::vector<Param> params() {
       {"base2_split", &isprime_tuning::base2_split, {0, 1}, P},
       {"base2_ilp", &isprime_tuning::base2_ilp, {1, 2}, P},
       {"rest_window", &isprime_tuning::rest_window, {4, 3}, P},
-      {"base2_blocks_per_sm", &isprime_tuning::base2_blocks_per_sm, {0, 6, 5}, P},
+      {"base2_blocks_per_sm", &isprime_tuning::base2_blocks_per_sm, {4, 0, 6, 5}, P},
+      {"pdl", &isprime_tuning::pdl, {0, 1}, P},
       {"sieve_cutover_log2", &isprime_tuning::sieve_cutover_log2, {32, 28, 24, 20}, P | B},
       {"batch_block", &isprime_tuning::batch_block, {64, 128, 256}, B},
       {"batch_tile_log2", &isprime_tuning::batch_tile_log2, {8, 9, 10, 11, 12}, B},
@@ -74,7 +75,7 @@ const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_prim
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
                          "compact_min", "sieve_cutover_log2", "serve_short_max", "td_fold",
                          "base2_split", "base2_ilp", "rest_window", "window_ratio16",
-                         "base2_blocks_per_sm"};
+                         "base2_blocks_per_sm", "pdl"};
 FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
@@ -84,8 +85,8 @@ FieldPtr kFieldPtr[] = {
     &isprime_tuning::compact_min, &isprime_tuning::sieve_cutover_log2,
     &isprime_tuning::serve_short_max, &isprime_tuning::td_fold, &isprime_tuning::base2_split,
     &isprime_tuning::base2_ilp, &isprime_tuning::rest_window, &isprime_tuning::window_ratio16,
-    &isprime_tuning::base2_blocks_per_sm};
-constexpr int kNumFields = 22;
+    &isprime_tuning::base2_blocks_per_sm, &isprime_tuning::pdl};
+constexpr int kNumFields = 23;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

@@ -36,6 +36,33 @@
 
 namespace ip {
 
+// Programmatic dependent launch (tuning pdl): the Miller-Rabin kernels may be
+// launched while the previous kernel on the stream is still running; each
+// waits here, before its first read of the queues, until that kernel has
+// finished and its writes are visible.  Without the launch attribute the
+// wait returns at once.
+__device__ __forceinline__ void wait_for_producer() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                     cudaStream_t s, bool pdl, Args... args) {
+  if (!pdl) {
+    kernel<<<grid, block, smem, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // kMode: the base-2 schedule (the tuning field base2_window): 0 binary with
 // a modular doubling per set bit, 1 4-bit windows with x 2^w mod n by a
 // quotient estimate, 4 4-bit windows with the table 2^w R in shared memory.
@@ -61,6 +88,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
                                                          uint32_t cap) {
   extern __shared__ uint64_t s_tab[];  // mode 4 or kRest 1: 16 x blockDim
   constexpr uint32_t kTask = 32u * kIlp;
+  wait_for_producer();
   const uint32_t count_f = *(volatile uint32_t*)&counters[0];
   const uint32_t count_b = *(volatile uint32_t*)&counters[4];
   const uint32_t front_pad = (count_f + kTask - 1) / kTask * kTask;
@@ -159,6 +187,7 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
   extern __shared__ uint64_t s_tab[];  // 2^kW x blockDim
   uint64_t* tab = s_tab + threadIdx.x;
   const int ld = blockDim.x;
+  wait_for_producer();
   const uint32_t count = *(volatile const uint32_t*)&counters[2];
   // whole warps per iteration: both tests are warp-synchronous
   const int lane = threadIdx.x & 31;
@@ -215,6 +244,7 @@ __global__ void __launch_bounds__(256) mr32_kernel(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ qidx,
                                                    const uint32_t* __restrict__ counters,
                                                    uint8_t* __restrict__ out, uint32_t cap) {
+  wait_for_producer();
   const uint32_t count = *(volatile const uint32_t*)&counters[1];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
     if (IP_CHECK(i < cap && qidx[i] < cap, kChkMr32) && mr32_is_prime(qn[i])) out[qidx[i]] = 1;
@@ -241,6 +271,7 @@ struct MrOpts {
   int ilp = 1;        // base2_ilp
   int rest_win = 4;   // rest_window
   int b2_per_sm = 0;  // base2_blocks_per_sm (0: as many as fit)
+  bool pdl = false;   // launch with programmatic stream serialization
 };
 
 // Modes 1 and 4 run one wave of resident blocks (the kernel balances the
@@ -249,14 +280,14 @@ struct MrOpts {
 template <int kImpl, int kMode, int kRest, int kIlp>
 static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
                              uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s,
-                             int per_sm_cap) {
+                             int per_sm_cap, bool pdl) {
   const size_t smem = (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t) : 0;
   const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, kMode, kRest, kIlp>);
   grid = resident_grid(fn, block, smem, sm_count, grid);
   if (per_sm_cap > 0 && sm_count > 0 && grid > (unsigned)(sm_count * per_sm_cap))
     grid = (unsigned)(sm_count * per_sm_cap);
-  mr64_base2_kernel<kImpl, kMode, kRest, kIlp><<<grid, block, smem, s>>>(
-      q.q64_n, q.q64_idx, q.counters, q.q64b, out, compact_min, mark, (uint32_t)q.capacity);
+  launch_k(mr64_base2_kernel<kImpl, kMode, kRest, kIlp>, grid, block, smem, s, pdl, q.q64_n,
+           q.q64_idx, q.counters, q.q64b, out, compact_min, mark, (uint32_t)q.capacity);
 }
 
 template <int kImpl, int kMode>
@@ -266,16 +297,16 @@ static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsi
     // two survivors per thread: formulation 6, estimated-quotient windows
     if ((kImpl == 6 || kImpl == 9 || kImpl == 16) && kMode == 1 && o.ilp == 2)
       launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s,
-                                       o.b2_per_sm);
+                                       o.b2_per_sm, o.pdl);
     else
       launch_base2_win<kImpl, kMode, 0, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
-                                           o.b2_per_sm);
+                                           o.b2_per_sm, o.pdl);
   } else if (o.lucas == 1) {
     launch_base2_win<kImpl, kMode, 2, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
-                                         o.b2_per_sm);
+                                         o.b2_per_sm, o.pdl);
   } else {
     launch_base2_win<kImpl, kMode, 1, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
-                                         o.b2_per_sm);
+                                         o.b2_per_sm, o.pdl);
   }
 }
 
@@ -287,8 +318,8 @@ static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned 
   } else if (o.window == 1) {
     launch_base2_mode<kImpl, 1>(q, out, grid, block, o, mark, sm_count, s);
   } else {
-    mr64_base2_kernel<kImpl, 0, 0><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.counters, q.q64b,
-                                                          out, 33u, mark, (uint32_t)q.capacity);
+    launch_k(mr64_base2_kernel<kImpl, 0, 0>, grid, block, 0, s, o.pdl, q.q64_n, q.q64_idx,
+             q.counters, q.q64b, out, 33u, mark, (uint32_t)q.capacity);
   }
 }
 
@@ -296,7 +327,7 @@ static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned 
 // over the threads whenever the queue is at most a sixth of its threads.
 template <int kImpl, int kW>
 static void launch_rest_w(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
-                          unsigned spread_grid, int sm_count, cudaStream_t s) {
+                          unsigned spread_grid, int sm_count, cudaStream_t s, bool pdl) {
   const size_t smem = ((size_t)1 << kW) * block * sizeof(uint64_t);
   if (spread_grid) {
     // at most the blocks that can be resident: more would only queue up (and
@@ -304,11 +335,11 @@ static void launch_rest_w(const Queues& q, uint8_t* out, unsigned grid, unsigned
     const uint32_t spread_threads = spread_grid * block;
     const void* fn = reinterpret_cast<const void*>(&mr64_rest_kernel<kImpl, false, true, kW>);
     const unsigned g = resident_grid(fn, block, smem, sm_count, spread_grid);
-    mr64_rest_kernel<kImpl, false, true, kW><<<g, block, smem, s>>>(
-        q.q64_n, q.q64_idx, q.q64b, q.counters, out, spread_threads, (uint32_t)q.capacity);
+    launch_k(mr64_rest_kernel<kImpl, false, true, kW>, g, block, smem, s, pdl, q.q64_n, q.q64_idx,
+             q.q64b, q.counters, out, spread_threads, (uint32_t)q.capacity);
   } else {
-    mr64_rest_kernel<kImpl, false, false, kW><<<grid, block, smem, s>>>(
-        q.q64_n, q.q64_idx, q.q64b, q.counters, out, 0u, (uint32_t)q.capacity);
+    launch_k(mr64_rest_kernel<kImpl, false, false, kW>, grid, block, smem, s, pdl, q.q64_n,
+             q.q64_idx, q.q64b, q.counters, out, 0u, (uint32_t)q.capacity);
   }
 }
 
@@ -316,12 +347,12 @@ template <int kImpl>
 static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
                         const MrOpts& o, unsigned spread_grid, int sm_count, cudaStream_t s) {
   if (o.lucas) {
-    mr64_rest_kernel<kImpl, true, false><<<grid, block, 0, s>>>(q.q64_n, q.q64_idx, q.q64b, q.counters,
-                                                                out, 0u, (uint32_t)q.capacity);
+    launch_k(mr64_rest_kernel<kImpl, true, false>, grid, block, 0, s, o.pdl, q.q64_n, q.q64_idx,
+             q.q64b, q.counters, out, 0u, (uint32_t)q.capacity);
   } else if ((kImpl == 6 || kImpl == 9 || kImpl == 17) && o.rest_win == 3) {
-    launch_rest_w<kImpl, 3>(q, out, grid, block, spread_grid, sm_count, s);
+    launch_rest_w<kImpl, 3>(q, out, grid, block, spread_grid, sm_count, s, o.pdl);
   } else {
-    launch_rest_w<kImpl, kWin>(q, out, grid, block, spread_grid, sm_count, s);
+    launch_rest_w<kImpl, kWin>(q, out, grid, block, spread_grid, sm_count, s, o.pdl);
   }
 }
 
@@ -387,7 +418,8 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
   int st;
   if (sieve_cut(ctx) < (1ull << 32)) {
     if ((st = launch_begin(ctx, ISPRIME_K_MR32, s, &tl))) return st;
-    mr32_kernel<<<grid, block, 0, s>>>(q.q32_n, q.q32_idx, q.counters, out, (uint32_t)q.capacity);
+    launch_k(mr32_kernel, grid, block, 0, s, ctx->tune.pdl != 0 && !ctx->timing, q.q32_n, q.q32_idx,
+             q.counters, out, (uint32_t)q.capacity);
     if ((st = launch_end(ctx, s, &tl, "mr32_kernel"))) return st;
   }
   MrOpts o;
@@ -399,6 +431,7 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
   o.ilp = (int)ctx->tune.base2_ilp;
   o.rest_win = (int)ctx->tune.rest_window;
   o.b2_per_sm = (int)ctx->tune.base2_blocks_per_sm;
+  o.pdl = ctx->tune.pdl != 0 && !ctx->timing;  // timing events between launches would serialise them
   if (ctx->count_ops) {  // isprime_count_ops: formulation 6 with its operations counted
     o.impl_b2 = 16;
     o.impl = 17;

@@ -277,6 +277,8 @@ def test_tuning_does_not_change_results():
                    dict(mont_impl=7, compact_min=8), dict(mont_impl=9), dict(mont_impl_base2=9),
                    dict(mont_impl=9, mont_impl_base2=9, base2_window=0),
                    dict(mont_impl=9, rest_window=4), dict(mont_impl_base2=9, base2_window=4),
+                   dict(pdl=1), dict(pdl=1, sieve_cutover_log2=20), dict(pdl=1, base2_window=0),
+                   dict(pdl=1, rest_test=1), dict(pdl=1, chunk_log2=16), dict(pdl=0),
                    dict(compact_min=0), dict(compact_min=1), dict(compact_min=16),
                    dict(compact_min=4, rest_test=1), dict(compact_min=8, mont_impl_base2=5),
                    dict(compact_min=2, base2_window=0), dict(compact_min=33),

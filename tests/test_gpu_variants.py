@@ -165,8 +165,22 @@ def test_formulation_9_matches_oracle(impl, impl_b2, ilp, data, ctx):
         ctx.set_tuning(mont_impl=6, mont_impl_base2=6, base2_ilp=1)
 
 
+@pytest.mark.parametrize("n", [70001, 1 << 20])
+def test_programmatic_dependent_launch_matches_oracle(n, data, ctx):
+    """pdl = 1: the Miller-Rabin kernels launched to overlap the kernel before
+    them (a short chunk takes the spreading six-base kernel, a long one not)."""
+    v, want = data
+    reps = -(-n // v.size)
+    vv, ww = np.tile(v, reps)[:n], np.tile(want, reps)[:n]
+    ctx.set_tuning(pdl=1, small_max=0)
+    try:
+        _same(vv, _run(ctx, vv), ww, f"pdl n={n}")
+    finally:
+        ctx.set_tuning(pdl=0)
+
+
 def test_tuning_rejects_out_of_range_variant_fields(ctx):
-    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0), dict(mont_impl=10), dict(mont_impl_base2=10),
+    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0), dict(mont_impl=10), dict(mont_impl_base2=10), dict(pdl=2),
                dict(rest_window=5), dict(rest_window=2)):
         with pytest.raises(ipg.IsPrimeError):
             ctx.set_tuning(**kw)
