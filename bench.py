@@ -368,10 +368,11 @@ def run_mine(args, world, rank, local):
         imad_rate = ipg.int_rates(local)
     peak_ops = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6
     if args.workload == "plain_large":
-        w = WORK_PLAIN_LARGE
+        w, stage2, schedule = _plain_large_work(ctx.tuning.as_dict())
         slots = {
-            "classify_u64": w["trial_tests"] * IMAD_SLOTS_PER_TRIAL_TEST,
-            "mr64_base2": w["base2_squarings"] * IMAD_SLOTS_PER_SQUARING,
+            "classify_u64": WORK_PLAIN_LARGE["trial_tests"] * IMAD_SLOTS_PER_TRIAL_TEST,
+            "mr64_base2": (stage2 * IMAD_SLOTS_PER_TRIAL_TEST
+                           + w["base2_squarings"] * IMAD_SLOTS_PER_SQUARING),
             "mr64_rest": w["rest_squarings"] * IMAD_SLOTS_PER_SQUARING
             + w["rest_multiplies"] * IMAD_SLOTS_PER_MULMOD,
         }
@@ -398,6 +399,7 @@ def run_mine(args, world, rank, local):
                                "64 mad.lo.u32 lanes/clk/SM)",
                 "algorithmic_slots_per_element": step_slots,
                 "roofline_tests_per_s": peak_ops / step_slots,
+                "schedule": schedule,
                 "frac_by_kernel": per_kernel,
                 "traffic_note": "DRAM bytes per step (sum of the three kernels) from the ncu "
                                 "capture whose source hash and tuning match this build; "
@@ -460,6 +462,25 @@ def _golden_work(name: str) -> dict:
     oracle's work counter (tests/golden/make_work_counts.py wrote the file)."""
     with open(os.path.join(ROOT, "tests", "golden", "work_counts.json")) as f:
         return json.load(f)[name]
+
+
+def _plain_large_work(tuning: dict) -> tuple[dict, float, str]:
+    """The per-element work of plain_large under the schedule the tuning runs:
+    (operation counts, second-stage trial tests, description).  With the
+    base-2 kernel's second trial stage (td2_groups = G) the first stage still
+    tests the odd primes <= 53 on every odd element, the base-2 kernel tests
+    the next 3 G primes on that stage's survivors, and only the values no
+    prime divides reach the base-2 test; the oracle's count at the larger
+    trial bound gives the Miller-Rabin work of that schedule."""
+    groups = int(tuning.get("td2_groups", 0))
+    if not groups:
+        return (WORK_PLAIN_LARGE, 0.0,
+                "trial division by the 15 odd primes <= 53, then the bases of Eq. 4")
+    g = _golden_work("plain_large_td2")["groups"][str(groups)]
+    return (g["per_element"], 3 * groups * WORK_PLAIN_LARGE["mr64_elements"],
+            f"trial division by the 15 odd primes <= 53 (classify), then by the next "
+            f"{3 * groups} odd primes up to {g['td_bound']} on its survivors (base-2 kernel, "
+            f"td2_groups = {groups}), then the bases of Eq. 4")
 
 
 def _slots_per_element(w: dict) -> float:

@@ -127,6 +127,16 @@ typedef struct {
                               serialisation, so a launch overlaps the end of the kernel before it
                               (each waits for that kernel before reading the queues; default);
                               0: plain stream order */
+  uint32_t td2_groups;     /* second trial-division stage: the base-2 kernel first tests its
+                              queue's values against the odd primes after 53 in this many
+                              groups of three (0, 8, 12, 16 or 24: primes up to 173, 239, 311,
+                              457) and runs the base-2 test only on those no prime divides,
+                              staged per warp so that the tests run on full warps (with
+                              base2_window 1, base2_ilp 1, formulations 6 and 9); 0: off */
+  uint32_t dual_stream;    /* 1: arrays of at least 2^20 values run as at least two chunks that
+                              alternate between the caller's stream and a second stream of the
+                              context with its own queues (fork and join by events, so the call
+                              keeps the caller's stream order); 0: one stream */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -375,7 +375,8 @@ int oracle_isprime_wheel(uint64_t n) {
 /*
  * Replays the array method's schedule for each element and counts its work:
  *   odd n >= sieve_limit are trial-divided by the odd primes <= td_bound
- *   (every such prime is tested: a data-parallel lane does not exit early);
+ *   (at most 499, the end of the list; every such prime is tested: a
+ *   data-parallel lane does not exit early);
  *   survivors >= 2^32 go through the seven-base test in order until a base
  *   fails; each base computes a^d by binary left-to-right square-and-multiply
  *   and then squares while looking for n-1.
@@ -396,7 +397,10 @@ void oracle_work_counts(const uint64_t *in, size_t n, uint32_t td_bound,
       3,   5,   7,   11,  13,  17,  19,  23,  29,  31,  37,  41,  43,  47,
       53,  59,  61,  67,  71,  73,  79,  83,  89,  97,  101, 103, 107, 109,
       113, 127, 131, 137, 139, 149, 151, 157, 163, 167, 173, 179, 181, 191,
-      193, 197, 199, 211, 223, 227, 229, 233, 239, 241, 251};
+      193, 197, 199, 211, 223, 227, 229, 233, 239, 241, 251, 257, 263, 269,
+      271, 277, 281, 283, 293, 307, 311, 313, 317, 331, 337, 347, 349, 353,
+      359, 367, 373, 379, 383, 389, 397, 401, 409, 419, 421, 431, 433, 439,
+      443, 449, 457, 461, 463, 467, 479, 487, 491, 499};
   const int nodd = (int)(sizeof(odd_primes) / sizeof(odd_primes[0]));
   for (int k = 0; k < 10; ++k) counts[k] = 0;
   for (size_t i = 0; i < n; ++i) {

@@ -50,7 +50,8 @@ class Tuning(ctypes.Structure):
                 ("td_fold", ctypes.c_uint32), ("base2_split", ctypes.c_uint32),
                 ("base2_ilp", ctypes.c_uint32), ("rest_window", ctypes.c_uint32),
                 ("window_ratio16", ctypes.c_uint32), ("base2_blocks_per_sm", ctypes.c_uint32),
-                ("pdl", ctypes.c_uint32)]
+                ("pdl", ctypes.c_uint32), ("td2_groups", ctypes.c_uint32),
+                ("dual_stream", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -12,6 +12,8 @@
 #pragma once
 #include <stdint.h>
 
+#include "tables.cuh"
+
 #if defined(__CUDACC__)
 #define IP_HD __host__ __device__ __forceinline__
 #else
@@ -763,6 +765,32 @@ IP_HD bool sprp2_64(const Mont64& M, uint64_t d, int s) {
     if (x == M.one) return false;
   }
   return false;
+}
+
+// Second trial-division stage: true when a prime of the first kGroups groups
+// of T divides n (n > 457, so such a divisor makes n composite).  Per group
+// of product m (odd, < 2^32), with n = n1 2^32 + n0:
+//   q = n0 (-m^-1) mod 2^32,  u = q m + n0 < 2^64 (its low word is 0),
+//   t = n1 + u / 2^32 = (n + q m) / 2^32,
+// so t = n 2^-32 (mod m) and t <= 2^32 - 1 + m (u / 2^32 <= m); subtracting m
+// once when t >= m leaves r < 2^32 with the same residue.  2^-32 is a unit
+// modulo every odd p | m, so p | n exactly when p | r, and p | r is the
+// 32-bit test r p^-1 mod 2^32 <= floor((2^32 - 1) / p).
+template <int kGroups>
+IP_HD bool td2_divisible(uint64_t n, const Td2Table& T) {
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  bool div = false;
+  IP_UNROLL
+  for (int g = 0; g < kGroups; ++g) {
+    const uint32_t m = T.m[g];
+    const uint32_t q = n0 * T.mneg[g];
+    const uint64_t u = (uint64_t)q * m + n0;
+    const uint64_t t = (uint64_t)n1 + (u >> 32);
+    const uint32_t r = (uint32_t)(t >= m ? t - m : t);
+    IP_UNROLL
+    for (int k = 3 * g; k < 3 * g + 3; ++k) div |= (uint32_t)(r * T.inv[k]) <= T.lim[k];
+  }
+  return div;
 }
 
 // Finishes a strong test once x = a^d (Montgomery form) is known.

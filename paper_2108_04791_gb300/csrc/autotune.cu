@@ -50,6 +50,8 @@ std::vector<Param> params() {
       {"rest_window", &isprime_tuning::rest_window, {4, 3}, P},
       {"base2_blocks_per_sm", &isprime_tuning::base2_blocks_per_sm, {4, 0, 6, 5}, P},
       {"pdl", &isprime_tuning::pdl, {0, 1}, P},
+      {"td2_groups", &isprime_tuning::td2_groups, {0, 8, 12, 16, 24}, P},
+      {"dual_stream", &isprime_tuning::dual_stream, {0, 1}, P},
       {"sieve_cutover_log2", &isprime_tuning::sieve_cutover_log2, {32, 28, 24, 20}, P | B},
       {"batch_block", &isprime_tuning::batch_block, {64, 128, 256}, B},
       {"batch_tile_log2", &isprime_tuning::batch_tile_log2, {8, 9, 10, 11, 12}, B},
@@ -75,7 +77,7 @@ const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_prim
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
                          "compact_min", "sieve_cutover_log2", "serve_short_max", "td_fold",
                          "base2_split", "base2_ilp", "rest_window", "window_ratio16",
-                         "base2_blocks_per_sm", "pdl"};
+                         "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream"};
 FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
@@ -85,8 +87,9 @@ FieldPtr kFieldPtr[] = {
     &isprime_tuning::compact_min, &isprime_tuning::sieve_cutover_log2,
     &isprime_tuning::serve_short_max, &isprime_tuning::td_fold, &isprime_tuning::base2_split,
     &isprime_tuning::base2_ilp, &isprime_tuning::rest_window, &isprime_tuning::window_ratio16,
-    &isprime_tuning::base2_blocks_per_sm, &isprime_tuning::pdl};
-constexpr int kNumFields = 23;
+    &isprime_tuning::base2_blocks_per_sm, &isprime_tuning::pdl, &isprime_tuning::td2_groups,
+    &isprime_tuning::dual_stream};
+constexpr int kNumFields = 25;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

@@ -18,6 +18,7 @@ namespace ip {
 // Each translation unit keeps its own copy of the constant tables.
 static __constant__ TdTable c_td = make_td_table();
 static __constant__ BaseTable c_bases = make_base_table();
+static __constant__ Td2Table c_td2 = make_td2_table();
 
 enum : int { kComposite = 0, kPrime = 1, kMR64 = 2, kMR32 = 3, kSieveLookup = 4 };
 
@@ -203,6 +204,7 @@ __device__ __forceinline__ bool rest64_is_prime_warp(uint64_t n, bool valid, uin
     const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b], r2, M);
     const uint64_t x = mont_pow_win<kImpl, kW>(M, aR, d, tab, ld, nib);
     prime = prime && sprp_tail64<kImpl>(M, x, s);
+    __syncwarp();
   }
   return valid && prime;
 }
@@ -225,6 +227,7 @@ __device__ __forceinline__ bool bases_pass_warp(uint64_t n, int first, int cnt, 
   for (int k = 0; k < cnt; ++k) {
     const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[first + k], r2, M);
     pass = pass && sprp_tail64<kImpl>(M, mont_pow_win<kImpl, kW>(M, aR, d, tab, ld, nib), s);
+    __syncwarp();
   }
   return pass;
 }

@@ -95,6 +95,9 @@ struct isprime_ctx {
   uint32_t* d_nprimes = nullptr;     // their count (device)
   uint32_t n_base_primes = 0;
   ip::Queues q;
+  ip::Queues q2;                     // second queue set of the two-stream form (dual_stream)
+  cudaStream_t dual_s = nullptr;     // its stream
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   isprime_tuning tune{};
   cudaEvent_t order_ev = nullptr;    // last use of the scratch queues
   bool order_ev_valid = false;

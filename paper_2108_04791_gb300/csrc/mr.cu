@@ -78,7 +78,15 @@ static void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, si
 // strong-test tail, which a warp runs for its largest s, is empty for the
 // front's warps.  Tasks of 32 * kIlp positions walk the front region (its
 // last task padded) and then the back region.
-template <int kImpl, int kMode, int kRest, int kIlp = 1>
+//
+// kTd2 > 0 (mode 1, kRest 0, kIlp 1): the second trial-division stage by the
+// first kTd2 groups of c_td2 runs on every fetched task first, and the warp
+// stages the values that survive it in its slice of shared memory (a stack of
+// at most 63 positions and values); whenever 32 are staged, the warp runs the
+// base-2 test on the top 32, so the exponentiations run on full warps while
+// about a quarter of the queue never reaches them.  A warp with no task left
+// runs what it still holds.
+template <int kImpl, int kMode, int kRest, int kIlp = 1, int kTd2 = 0>
 __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restrict__ qn,
                                                          const uint32_t* __restrict__ qidx,
                                                          uint32_t* __restrict__ counters,
@@ -104,6 +112,76 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   // warps without a first task issue none.
   const uint32_t first_tasks = gridDim.x * (blockDim.x >> 5) * kTask;
   uint32_t next = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kTask;
+  // Appends the lanes with pass set to q64b (one atomic per warp) and, for the
+  // spreading six-base kernel, marks them prime.
+  auto append_passing = [&](bool pass, uint32_t pos) {
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, pass);
+    if (!mask) return;
+    const int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&counters[2], (uint32_t)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (pass) {
+      const uint32_t k = base + __popc(mask & ((1u << lane) - 1u));
+      if (IP_CHECK(k < cap, kChkQ64b)) q64b[k] = pos;
+      if (mark && IP_CHECK(qidx[pos] < cap, kChkMrOut)) out[qidx[pos]] = 1;
+    }
+  };
+  if constexpr (kTd2 > 0) {
+    static_assert(kMode == 1 && kRest == 0 && kIlp == 1, "second trial stage: shift windows only");
+    // this warp's stack: 64 values, then 64 positions
+    uint64_t* st_n = s_tab + (threadIdx.x >> 5) * 96;
+    uint32_t* st_pos = reinterpret_cast<uint32_t*>(st_n + 64);
+    int held = 0;  // staged values, the same in every lane
+    for (;;) {
+      const bool have = next < vcount;
+      if (have) {
+        const uint32_t vbase = next;
+        if (lane == 0) next = first_tasks + atomicAdd(&counters[3], kTask);
+        const uint32_t v = vbase + lane;
+        uint32_t pos;
+        bool valid;
+        if (vbase < front_pad) {
+          pos = v;
+          valid = v < count_f;
+        } else {
+          pos = back0 + (v - front_pad);
+          valid = v < vcount;
+        }
+        valid = valid && IP_CHECK(pos < cap, kChkQ64Read);
+        const uint64_t n = valid ? qn[pos] : 0ull;
+        const bool keep = valid && !td2_divisible<kTd2>(n, c_td2);
+        const unsigned km = __ballot_sync(0xFFFFFFFFu, keep);
+        if (keep) {
+          const int k = held + __popc(km & ((1u << lane) - 1u));
+          if (IP_CHECK(k < 64, kChkSmemQueue)) {
+            st_n[k] = n;
+            st_pos[k] = pos;
+          }
+        }
+        held += __popc(km);
+        next = __shfl_sync(0xFFFFFFFFu, next, 0);
+        __syncwarp();
+      }
+      // full batches from the top of the stack; with no task left, the rest
+      while (held >= 32 || (!have && held > 0)) {
+        const int b0 = held >= 32 ? held - 32 : 0;
+        const bool valid = lane < held - b0;
+        const uint64_t n = valid ? st_n[b0 + lane] : 0xFFFFFFFFFFFFFFC5ull;
+        const uint32_t pos = valid ? st_pos[b0 + lane] : 0u;
+        __syncwarp();  // read before the next task's values overwrite the slots
+        held = b0;
+        bool pass = false;
+        if (valid) {
+          const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
+          pass = base2_passes_shift<kImpl>(n, nib);
+        }
+        append_passing(pass, pos);
+      }
+      if (!have) break;
+    }
+    return;
+  }
   while (next < vcount) {
     const uint32_t vbase = next;
     if (lane == 0) next = first_tasks + atomicAdd(&counters[3], kTask);
@@ -157,17 +235,9 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
                                       : rest64_is_prime_warp<kImpl>(m, pass[u], s_tab + threadIdx.x,
                                                                     (int)blockDim.x);
         if (prime && IP_CHECK(qidx[pos[u]] < cap, kChkMrOut)) out[qidx[pos[u]]] = 1;
-      } else if (mask) {
-        const int leader = __ffs(mask) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&counters[2], (uint32_t)__popc(mask));
-        base = __shfl_sync(0xFFFFFFFFu, base, leader);
-        if (pass[u]) {
-          const uint32_t k = base + __popc(mask & ((1u << lane) - 1u));
-          if (IP_CHECK(k < cap, kChkQ64b)) q64b[k] = pos[u];
-          // prime unless a later base clears it (spread rest kernel)
-          if (mark && IP_CHECK(qidx[pos[u]] < cap, kChkMrOut)) out[qidx[pos[u]]] = 1;
-        }
+      } else {
+        // prime unless a later base clears it (spread rest kernel)
+        append_passing(pass[u], pos[u]);
       }
     }
     next = __shfl_sync(0xFFFFFFFFu, next, 0);
@@ -272,35 +342,58 @@ struct MrOpts {
   int rest_win = 4;   // rest_window
   int b2_per_sm = 0;  // base2_blocks_per_sm (0: as many as fit)
   bool pdl = false;   // launch with programmatic stream serialization
+  int td2 = 0;        // td2_groups: second trial stage in the base-2 kernel
 };
 
 // Modes 1 and 4 run one wave of resident blocks (the kernel balances the
 // warps itself); the table of mode 4 and the finishing of kRest 1 take
 // 16 x block words of shared memory.
-template <int kImpl, int kMode, int kRest, int kIlp>
+template <int kImpl, int kMode, int kRest, int kIlp, int kTd2 = 0>
 static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
                              uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s,
                              int per_sm_cap, bool pdl) {
-  const size_t smem = (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t) : 0;
-  const void* fn = reinterpret_cast<const void*>(&mr64_base2_kernel<kImpl, kMode, kRest, kIlp>);
-  grid = resident_grid(fn, block, smem, sm_count, grid);
+  // the table of mode 4 and the finishing of kRest 1: 16 words per thread;
+  // the second trial stage: 96 words per warp (64 values, 64 positions)
+  const size_t smem = kTd2 > 0 ? (size_t)96 * (block / 32) * sizeof(uint64_t)
+                      : (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t)
+                                                   : 0;
+  auto kern = mr64_base2_kernel<kImpl, kMode, kRest, kIlp, kTd2>;
+  grid = resident_grid(reinterpret_cast<const void*>(kern), block, smem, sm_count, grid);
   if (per_sm_cap > 0 && sm_count > 0 && grid > (unsigned)(sm_count * per_sm_cap))
     grid = (unsigned)(sm_count * per_sm_cap);
-  launch_k(mr64_base2_kernel<kImpl, kMode, kRest, kIlp>, grid, block, smem, s, pdl, q.q64_n,
-           q.q64_idx, q.counters, q.q64b, out, compact_min, mark, (uint32_t)q.capacity);
+  launch_k(kern, grid, block, smem, s, pdl, q.q64_n, q.q64_idx, q.counters, q.q64b, out,
+           compact_min, mark, (uint32_t)q.capacity);
 }
 
 template <int kImpl, int kMode>
 static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
                               const MrOpts& o, uint32_t mark, int sm_count, cudaStream_t s) {
   if (o.compact_min > 32) {
-    // two survivors per thread: formulation 6, estimated-quotient windows
-    if ((kImpl == 6 || kImpl == 9 || kImpl == 16) && kMode == 1 && o.ilp == 2)
-      launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s,
-                                       o.b2_per_sm, o.pdl);
-    else
-      launch_base2_win<kImpl, kMode, 0, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
-                                           o.b2_per_sm, o.pdl);
+    constexpr bool kFast = (kImpl == 6 || kImpl == 9 || kImpl == 16) && kMode == 1;
+    if constexpr (kFast) {
+      // the second trial stage (formulations 6 and 9 and the counting build,
+      // estimated-quotient windows, one survivor per thread)
+      if (o.ilp == 1 && o.td2 > 0) {
+        switch (o.td2) {
+          case 8: launch_base2_win<kImpl, 1, 0, 1, 8>(q, out, grid, block, o.compact_min, mark,
+                                                      sm_count, s, o.b2_per_sm, o.pdl); return;
+          case 12: launch_base2_win<kImpl, 1, 0, 1, 12>(q, out, grid, block, o.compact_min, mark,
+                                                        sm_count, s, o.b2_per_sm, o.pdl); return;
+          case 16: launch_base2_win<kImpl, 1, 0, 1, 16>(q, out, grid, block, o.compact_min, mark,
+                                                        sm_count, s, o.b2_per_sm, o.pdl); return;
+          default: launch_base2_win<kImpl, 1, 0, 1, 24>(q, out, grid, block, o.compact_min, mark,
+                                                        sm_count, s, o.b2_per_sm, o.pdl); return;
+        }
+      }
+      // two survivors per thread
+      if (o.ilp == 2) {
+        launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                         o.b2_per_sm, o.pdl);
+        return;
+      }
+    }
+    launch_base2_win<kImpl, kMode, 0, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                         o.b2_per_sm, o.pdl);
   } else if (o.lucas == 1) {
     launch_base2_win<kImpl, kMode, 2, 1>(q, out, grid, block, o.compact_min, mark, sm_count, s,
                                          o.b2_per_sm, o.pdl);
@@ -432,6 +525,7 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
   o.rest_win = (int)ctx->tune.rest_window;
   o.b2_per_sm = (int)ctx->tune.base2_blocks_per_sm;
   o.pdl = ctx->tune.pdl != 0 && !ctx->timing;  // timing events between launches would serialise them
+  o.td2 = (int)ctx->tune.td2_groups;
   if (ctx->count_ops) {  // isprime_count_ops: formulation 6 with its operations counted
     o.impl_b2 = 16;
     o.impl = 17;

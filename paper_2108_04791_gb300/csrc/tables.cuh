@@ -107,4 +107,61 @@ constexpr bool fold_widths_divide() {
 }
 static_assert(fold_widths_divide(), "a folded prime does not divide 2^k - 1");
 
+// Second trial-division stage (tuning td2_groups): the odd primes after 53,
+// tested only on the survivors of the first stage (the base-2 kernel's
+// queue), where a removed value saves a whole base-2 exponentiation.  They
+// come in groups of three with product m < 2^32: a 64-bit n is reduced to one
+// 32-bit residue per group (td2_divisible in arith.cuh) and each prime of the
+// group is tested on it with the 32-bit multiply-by-inverse test.
+constexpr int kTd2MaxGroups = 24;
+constexpr int kTd2Primes = 3 * kTd2MaxGroups;  // 59 .. 457
+
+struct Td2Table {
+  uint32_t m[kTd2MaxGroups];     // product of the group's three primes
+  uint32_t mneg[kTd2MaxGroups];  // -m^-1 mod 2^32
+  uint32_t p[kTd2Primes];
+  uint32_t inv[kTd2Primes];      // p^-1 mod 2^32
+  uint32_t lim[kTd2Primes];      // floor((2^32 - 1) / p)
+};
+
+constexpr bool ce_is_prime(uint32_t n) {
+  if (n < 2) return false;
+  for (uint32_t d = 2; d * d <= n; ++d)
+    if (n % d == 0) return false;
+  return true;
+}
+
+constexpr Td2Table make_td2_table() {
+  Td2Table t{};
+  uint32_t c = kTdPrimeList[kFoldPrimes - 1];  // 53, the last prime of the first stage
+  for (int i = 0; i < kTd2Primes; ++i) {
+    c += 2;
+    while (!ce_is_prime(c)) c += 2;
+    t.p[i] = c;
+    t.inv[i] = (uint32_t)ce_inv64(c);
+    t.lim[i] = 0xFFFFFFFFu / c;
+  }
+  for (int g = 0; g < kTd2MaxGroups; ++g) {
+    const uint64_t m = (uint64_t)t.p[3 * g] * t.p[3 * g + 1] * t.p[3 * g + 2];
+    t.m[g] = (uint32_t)m;
+    t.mneg[g] = 0u - (uint32_t)ce_inv64(m);
+  }
+  return t;
+}
+
+constexpr Td2Table kTd2Host = make_td2_table();
+
+// Every group's product fits 32 bits and every inverse is one (compile time).
+constexpr bool td2_table_ok() {
+  for (int g = 0; g < kTd2MaxGroups; ++g) {
+    const uint64_t m = (uint64_t)kTd2Host.p[3 * g] * kTd2Host.p[3 * g + 1] * kTd2Host.p[3 * g + 2];
+    if (m >= ((uint64_t)1 << 32) || (uint32_t)(kTd2Host.m[g] * (0u - kTd2Host.mneg[g])) != 1u)
+      return false;
+  }
+  for (int i = 0; i < kTd2Primes; ++i)
+    if ((uint32_t)(kTd2Host.p[i] * kTd2Host.inv[i]) != 1u) return false;
+  return kTd2Host.p[0] == 59;
+}
+static_assert(td2_table_ok(), "second-stage trial-division table");
+
 }  // namespace ip

@@ -39,6 +39,20 @@ int h_sprp32(uint32_t n, uint32_t a) {
 int h_td64(uint64_t n, int i) { return n * ip::kTdHost.inv64[i] <= ip::kTdHost.lim64[i]; }
 int h_td32(uint32_t n, int i) { return (uint32_t)(n * ip::kTdHost.inv32[i]) <= ip::kTdHost.lim32[i]; }
 uint32_t h_td_prime(int i) { return ip::kTdHost.p[i]; }
+// The second trial-division stage over its first `groups` groups (-1: not a
+// compiled group count).
+int h_td2(uint64_t n, int groups) {
+  switch (groups) {
+    case 1: return ip::td2_divisible<1>(n, ip::kTd2Host);
+    case 8: return ip::td2_divisible<8>(n, ip::kTd2Host);
+    case 12: return ip::td2_divisible<12>(n, ip::kTd2Host);
+    case 16: return ip::td2_divisible<16>(n, ip::kTd2Host);
+    case 24: return ip::td2_divisible<24>(n, ip::kTd2Host);
+    default: return -1;
+  }
+}
+uint32_t h_td2_prime(int i) { return ip::kTd2Host.p[i]; }
+uint32_t h_td2_modulus(int g) { return ip::kTd2Host.m[g]; }
 }
 
 extern "C" {

@@ -33,6 +33,8 @@ def H(tmp_path_factory):
                             ("h_sprp64", [u64, u64], i32), ("h_mont_mul32", [u32, u32, u32], u32),
                             ("h_sprp32", [u32, u32], i32), ("h_td64", [u64, i32], i32),
                             ("h_td32", [u32, i32], i32), ("h_td_prime", [i32], u32),
+                            ("h_td2", [u64, i32], i32), ("h_td2_prime", [i32], u32),
+                            ("h_td2_modulus", [i32], u32),
                             ("h_mont_mul_w", [u64, u64, u64], u64), ("h_mont_sqr_w", [u64, u64], u64),
                             ("h_mont_sqr_h", [u64, u64], u64),
                             ("h_mont_mul_f", [u64, u64, u64], u64), ("h_mont_sqr_f", [u64, u64], u64),
@@ -146,6 +148,38 @@ def test_divisibility_by_inverse(H):
             assert bool(H.h_td64(v, i)) == (v % p == 0)
             v32 = v & 0xFFFFFFFF
             assert bool(H.h_td32(v32, i)) == (v32 % p == 0)
+
+
+def test_second_trial_stage(H):
+    """td2_divisible (the base-2 kernel's second trial stage): its primes are
+    the 72 odd primes after 53 in order, each group's modulus is the product
+    of its three, and the Montgomery-reduced residue decides divisibility
+    exactly as n % p does, on random values and on the edges of the
+    reduction: n0 = 0 or 2^32 - 1, n1 = 2^32 - 1 (t close to 2^32 + m),
+    multiples of each prime and of each modulus near 2^64, and m k + r for
+    small r."""
+    primes = [p for p in range(55, 500, 2) if nt.trial_is_prime(p)][:72]
+    assert [H.h_td2_prime(i) for i in range(72)] == primes
+    assert primes[0] == 59 and primes[-1] == 457
+    for g in range(24):
+        assert H.h_td2_modulus(g) == primes[3 * g] * primes[3 * g + 1] * primes[3 * g + 2] < 2**32
+    rng = random.Random(27)
+    vals = [rng.randrange(2**32, R) for _ in range(3000)]
+    vals += [(rng.randrange(1, 2**32) << 32) for _ in range(200)]            # n0 = 0
+    vals += [(rng.randrange(1, 2**32) << 32) | 0xFFFFFFFF for _ in range(200)]
+    vals += [(0xFFFFFFFF << 32) | rng.randrange(2**32) for _ in range(300)]  # n1 = 2^32 - 1
+    vals += [R - 1 - k for k in range(200)] + [2**32 + k for k in range(200)]
+    for p in primes:
+        vals += [p * (R // p - j) for j in range(3)] + [p * rng.randrange(2**32 // p, R // p)]
+    for g in range(24):
+        m = H.h_td2_modulus(g)
+        vals += [m * (R // m - j) + r for j in range(2) for r in (0, 1, m - 1) if m * (R // m - j) + r < R]
+        vals += [m * rng.randrange(1, R // m) + r for r in (0, 1, 2) for _ in range(3)]
+    for groups in (1, 8, 12, 16, 24):
+        ps = primes[:3 * groups]
+        for v in vals:
+            assert H.h_td2(v, groups) == int(any(v % p == 0 for p in ps)), (v, groups)
+    assert H.h_td2(2**40, 5) == -1
 
 
 def test_jacobi_and_squares(H):

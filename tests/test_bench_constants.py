@@ -28,6 +28,34 @@ def test_plain_large_work_per_element():
     assert g["totals"] == w and g["elements"] == v.size
 
 
+def test_plain_large_two_stage_trial_work():
+    """The stored counts of the base-2 kernel's second trial stage: at the
+    larger trial bound fewer elements reach base 2, the same ones pass it (no
+    prime is removed, and no base-2 strong pseudoprime of this array has a
+    factor below 457), and the trial tests are the first stage's plus 3 G per
+    first-stage survivor; a recount of every td_bound on 2^18 elements agrees
+    within sampling error, and the bench reads the schedule from the tuning."""
+    g = json.load(open(GOLDEN))
+    base = g["plain_large"]["per_element"]
+    v = plain_large(1 << 18)
+    for groups, bound in ((8, 173), (12, 239), (16, 311), (24, 457)):
+        e = g["plain_large_td2"]["groups"][str(groups)]
+        per = e["per_element"]
+        assert e["td_bound"] == bound
+        assert per["mr64_elements"] < base["mr64_elements"]
+        assert per["base2_squarings"] < base["base2_squarings"]
+        assert per["base2_passes"] == base["base2_passes"] and per["primes"] == base["primes"]
+        assert abs(per["trial_tests"] - (base["trial_tests"] + 3 * groups * base["mr64_elements"])) < 1e-9
+        w = oracle.work_counts(v, td_bound=bound, sieve_limit=1 << 32)
+        for k in ("mr64_elements", "base2_squarings"):
+            assert abs(w[k] / v.size - per[k]) < 0.02 * per[k], (groups, k)
+        work, stage2, sched = bench._plain_large_work({"td2_groups": groups})
+        assert work == per and abs(stage2 - 3 * groups * bench.WORK_PLAIN_LARGE["mr64_elements"]) < 1e-12
+        assert str(bound) in sched
+    work, stage2, _ = bench._plain_large_work({"td2_groups": 0})
+    assert work == bench.WORK_PLAIN_LARGE and stage2 == 0
+
+
 def test_batched_and_served_work_on_a_sample():
     """The stored full-workload figures (written by make_work_counts.py over
     every element) agree with a recount of 2^18 elements taken in 16 blocks

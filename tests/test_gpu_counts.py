@@ -39,7 +39,7 @@ def ctx():
 
 @pytest.mark.parametrize("ilp,win", [(1, 4), (2, 4), (1, 3), (2, 3)])
 def test_counts_exact_on_a_hand_derived_input(ilp, win, ctx):
-    ctx.set_tuning(base2_window=1, base2_ilp=ilp, rest_window=win, compact_min=33)
+    ctx.set_tuning(base2_window=1, base2_ilp=ilp, rest_window=win, compact_min=33, td2_groups=0)
     v = np.full(64, 2**61 - 1, dtype=np.uint64)
     t = torch.from_numpy(v.view(np.int64)).to("cuda:0")
     c = ctx.count_ops(t)
@@ -59,7 +59,7 @@ def test_counts_bound_the_canonical_count_on_the_bench_array(ctx):
     executed at least the canonical squarings of the binary schedule minus
     what the windows save (at most one squaring per value per base, the top
     digit's), and the warps paid at most a bounded padding over them."""
-    ctx.set_tuning(base2_window=1, base2_ilp=1, rest_window=4, compact_min=33)
+    ctx.set_tuning(base2_window=1, base2_ilp=1, rest_window=4, compact_min=33, td2_groups=0)
     v = plain_large(1 << 22, seed=1)
     t = torch.from_numpy(v.view(np.int64)).to("cuda:0")
     c = ctx.count_ops(t)

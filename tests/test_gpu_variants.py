@@ -179,8 +179,134 @@ def test_programmatic_dependent_launch_matches_oracle(n, data, ctx):
         ctx.set_tuning(pdl=0)
 
 
+@pytest.mark.parametrize("n,chunk_log2", [(1 << 20, 24), ((1 << 20) + 12345, 24),
+                                           (3 * (1 << 20) + 7, 24), ((1 << 20) + 999, 16)])
+def test_dual_stream_matches_oracle(n, chunk_log2, data, ctx):
+    """dual_stream = 1: chunks alternate between the caller's stream (first
+    queue set) and the context's second stream (second queue set); two
+    chunks, or with chunk_log2 = 16 seventeen, a ragged last one.  The call
+    runs on a side stream of the caller, whose next kernel must see every
+    output; a second call right after reuses both queue sets."""
+    v, want = data
+    reps = -(-n // v.size)
+    vv, ww = np.tile(v, reps)[:n], np.tile(want, reps)[:n]
+    ctx.set_tuning(dual_stream=1, small_max=0, chunk_log2=chunk_log2)
+    try:
+        side = torch.cuda.Stream()
+        t = torch.from_numpy(vv.view(np.int64)).to("cuda:0")
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            out1 = ctx.isprime(t)
+            s1 = out1.to(torch.int64).sum()      # ordered on the side stream after the call
+            out2 = ctx.isprime(t.flip(0))
+        torch.cuda.synchronize()
+        _same(vv, out1.cpu().numpy(), ww, f"dual n={n} chunk_log2={chunk_log2}")
+        _same(vv[::-1], out2.cpu().numpy(), ww[::-1], f"dual second call n={n}")
+        assert int(s1) == int(ww.sum())
+    finally:
+        ctx.set_tuning(dual_stream=0, chunk_log2=24)
+
+
+def test_dual_stream_double_path_counts_invalid(ctx):
+    """The double path in two-stream form: results and the invalid count
+    (kernels of both streams add to it) equal the oracle's."""
+    rng = np.random.default_rng(77)
+    n = (1 << 21) + 3
+    d = rng.integers(0, 1 << 53, size=n, endpoint=True).astype(np.float64)
+    d[rng.integers(0, n, size=1000)] = 0.5
+    d[rng.integers(0, n, size=1000)] = -3.0
+    d[rng.integers(0, n, size=10)] = float(1 << 60)
+    want, bad = oracle.isprime_f64(d)
+    ctx.set_tuning(dual_stream=1, small_max=0, chunk_log2=20)
+    try:
+        t = torch.from_numpy(d).to("cuda:0")
+        inv = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+        ctx.f64_status()
+        got = ctx.isprime(t, invalid=inv)
+        torch.cuda.synchronize()
+        _same(d, got.cpu().numpy(), want, "dual f64")
+        assert int(inv.item()) == bad
+        assert ctx.f64_status() == bad
+    finally:
+        ctx.set_tuning(dual_stream=0, chunk_log2=24)
+
+
+TD2_PRIMES = [p for p in range(55, 500, 2) if nt.trial_is_prime(p)][:72]  # 59 .. 457
+
+
+@pytest.fixture(scope="module")
+def td2_data(data):
+    """The variant inputs plus values that the second trial stage removes:
+    multiples of each of its primes near 2^64, just above 2^32 and at random,
+    p q with p one of its primes and q a prime near 2^64 / p, and the same
+    with p the first prime after its last group (459 < p: never removed)."""
+    v, _ = data
+    rng = random.Random(31)
+    extra = []
+    pool = [int(x) for x in load_pool("primes_near_2p64.txt")[:200]]
+    for p in TD2_PRIMES + [461, 463, 467]:
+        top = (2**64 - 1) // p
+        extra += [p * (top - j) for j in range(6)]
+        extra += [p * ((2**32) // p + 1 + j) for j in range(6)]
+        extra += [p * rng.randrange(2**32 // p, top) for _ in range(6)]
+        q = rng.choice(pool) // p
+        while not oracle.isprime1(q):
+            q -= 1
+        extra.append(p * q)
+    w = np.concatenate([v, np.array(extra, dtype=np.uint64)])
+    np.random.default_rng(32).shuffle(w)
+    return w, oracle.isprime_u64(w)
+
+
+@pytest.mark.parametrize("td2,split,chunk_log2", [(8, 1, 24), (12, 0, 24), (16, 1, 24),
+                                                  (24, 1, 24), (16, 0, 16), (24, 1, 16)])
+def test_second_trial_stage_matches_oracle(td2, split, chunk_log2, td2_data, ctx):
+    """td2_groups > 0: the base-2 kernel tests its queue against the primes
+    59 .. 457 first and stages the survivors per warp; with the s-split on and
+    off, one chunk and many (every chunk's stacks drain at its end)."""
+    v, want = td2_data
+    ctx.set_tuning(td2_groups=td2, base2_split=split, chunk_log2=chunk_log2, small_max=0,
+                   td_fold=2, base2_ilp=1, rest_window=3)
+    try:
+        _same(v, _run(ctx, v), want, f"td2={td2} split={split} chunk_log2={chunk_log2}")
+    finally:
+        ctx.set_tuning(td2_groups=0, base2_split=1, chunk_log2=24)
+
+
+def test_second_trial_stage_on_short_queues(td2_data, ctx):
+    """Short queues (the spreading six-base kernel, which relies on the base-2
+    kernel's marks) and partial stacks: every length from 1 to 70 and a few
+    longer ones, each slice of the inputs on its own."""
+    v, want = td2_data
+    ctx.set_tuning(td2_groups=16, small_max=0)
+    try:
+        rng = np.random.default_rng(33)
+        for n in list(range(1, 71)) + [127, 1000, 4097, 30001]:
+            o = int(rng.integers(0, v.size - n))
+            _same(v[o:o + n], _run(ctx, v[o:o + n]), want[o:o + n], f"td2 short n={n}")
+    finally:
+        ctx.set_tuning(td2_groups=0)
+
+
+def test_second_trial_stage_host_and_double_paths(td2_data, ctx):
+    v, want = td2_data
+    ctx.set_tuning(td2_groups=24, small_max=0, chunk_log2=16)
+    try:
+        _same(v, ctx.isprime_host(v), want, "td2 host path")
+        d = (v[:200_000] >> np.uint64(11)).astype(np.float64)  # integers below 2^53
+        wd, bad = oracle.isprime_f64(d)
+        got = ctx.isprime(torch.from_numpy(d).to("cuda:0"))
+        torch.cuda.synchronize()
+        assert bad == 0
+        _same(d, got.cpu().numpy(), wd, "td2 double path")
+    finally:
+        ctx.set_tuning(td2_groups=0, chunk_log2=24)
+
+
 def test_tuning_rejects_out_of_range_variant_fields(ctx):
-    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0), dict(mont_impl=10), dict(mont_impl_base2=10), dict(pdl=2),
+    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
+               dict(mont_impl=10), dict(mont_impl_base2=10), dict(pdl=2), dict(dual_stream=2),
+               dict(td2_groups=4), dict(td2_groups=25),
                dict(rest_window=5), dict(rest_window=2)):
         with pytest.raises(ipg.IsPrimeError):
             ctx.set_tuning(**kw)

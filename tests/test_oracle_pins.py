@@ -295,6 +295,30 @@ def test_work_counter_invariants():
     assert w["trial_tests"] == 15 * odd
 
 
+@pytest.mark.parametrize("bound", [53, 173, 239, 311, 457, 499])
+def test_work_counter_trial_bound(bound):
+    """The trial stage follows td_bound up to the end of the counter's list
+    (499): every odd n >= 2^32 is tested against each odd prime <= td_bound
+    (counted here by plain trial division of the small numbers), and n = p q
+    (p the largest odd prime <= td_bound, q a prime near 2^50 found by the
+    independent Pratt certificate) is removed at that bound and reaches the
+    base-2 test one prime below it, failing there (checked by Python's pow)."""
+    odd = [p for p in range(3, bound + 1, 2) if nt.trial_is_prime(p)]
+    p = odd[-1]
+    q = (1 << 50) + 1
+    while nt.pratt_prime(q, random.Random(q)) is not True:
+        q += 2
+    n = p * q
+    w = oracle.work_counts(np.array([n], dtype=np.uint64), td_bound=bound)
+    assert w["trial_tests"] == len(odd)
+    assert w["mr64_elements"] == 0 and w["base_tests"] == 0
+    w = oracle.work_counts(np.array([n], dtype=np.uint64), td_bound=p - 1)
+    assert w["trial_tests"] == len(odd) - 1
+    assert w["mr64_elements"] == 1
+    assert not nt.strong_base2(n)
+    assert w["base2_passes"] == 0 and w["base_tests"] == 1
+
+
 def test_work_counter_exact_on_one_prime():
     """n = 2^61 - 1: n - 1 = 2 (2^60 - 1), s = 1, d = 2^60 - 1 (60 one bits):
     every base does 59 squarings and 59 multiplications, no extra squaring."""
