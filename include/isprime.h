@@ -104,7 +104,10 @@ typedef struct {
                               0 every prime by the 64-bit multiply-by-inverse test; 1 the primes
                               dividing 2^32-1, 2^24-1 and 2^20-1 (3, 5, 7, 11, 13, 17, 31, 41)
                               by the 32-bit test on a sum of chunks of n that is congruent to n
-                              modulo that number; 2 also 29 and 43 by 2^28-1 */
+                              modulo that number; 2 also 29 and 43 by 2^28-1; 3 every prime by
+                              the 32-bit test on one of two residues of n, modulo
+                              29*31*41*43*47*53 and 3*5*7*11*13*17*19*23*37 (each below 2^32,
+                              one Montgomery reduction step each) */
   uint32_t base2_split;    /* 1: 64-bit survivors with n = 3 (mod 4) (s = 1 in n-1 = 2^s d) are
                               queued apart from the others, so the base-2 kernel's warps of those
                               run no strong-test tail; 0: one queue */
@@ -137,6 +140,8 @@ typedef struct {
                               alternate between the caller's stream and a second stream of the
                               context with its own queues (fork and join by events, so the call
                               keeps the caller's stream order); 0: one stream */
+  uint32_t host_chunk_log2;  /* isprime_u64_host: chunks of at most 2^host_chunk_log2 values
+                              (and at most 2^chunk_log2), 16..24, default 22 */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -92,7 +92,7 @@ static isprime_tuning default_tuning() {
   // measured on plain_large (GB300): folds 2 and the s-split shorten the
   // step by 1.5% and 0.4%, 3-bit windows the six-base kernel by 1%, four
   // resident base-2 blocks per SM the base-2 kernel by 1.4%
-  t.td_fold = 2;
+  t.td_fold = 3;  // two residues: classify 0.106 -> 0.088 ms on plain_large
   t.base2_split = 1;
   t.base2_ilp = 1;
   t.rest_window = 3;
@@ -101,6 +101,7 @@ static isprime_tuning default_tuning() {
   t.pdl = 1;  // programmatic dependent launch of the Miller-Rabin kernels: 0.6% on plain_large
   t.td2_groups = 16;  // second trial stage, primes 59 .. 311: base 2 -12%, step -4.8% on plain_large
   t.dual_stream = 0;
+  t.host_chunk_log2 = 22;  // host path: 1.089 ms per 2^24 values against 1.26 (23) and 1.15 (21)
   return t;
 }
 
@@ -123,7 +124,7 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.compact_min > 33) return set_error(ISPRIME_EINVAL, "compact_min must be in [0, 33]");
   if (t.sieve_cutover_log2 > 32) return set_error(ISPRIME_EINVAL, "sieve_cutover_log2 must be in [0, 32]");
   if (t.serve_short_max > (1u << 20)) return set_error(ISPRIME_EINVAL, "serve_short_max must be in [0, 2^20]");
-  if (t.td_fold > 2) return set_error(ISPRIME_EINVAL, "td_fold must be in [0, 2]");
+  if (t.td_fold > 3) return set_error(ISPRIME_EINVAL, "td_fold must be in [0, 3]");
   if (t.base2_split > 1) return set_error(ISPRIME_EINVAL, "base2_split must be 0 or 1");
   if (t.base2_ilp != 1 && t.base2_ilp != 2) return set_error(ISPRIME_EINVAL, "base2_ilp must be 1 or 2");
   if (t.rest_window != 3 && t.rest_window != 4) return set_error(ISPRIME_EINVAL, "rest_window must be 3 or 4");
@@ -131,6 +132,8 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.base2_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "base2_blocks_per_sm must be in [0, 32]");
   if (t.pdl > 1) return set_error(ISPRIME_EINVAL, "pdl must be 0 or 1");
   if (t.dual_stream > 1) return set_error(ISPRIME_EINVAL, "dual_stream must be 0 or 1");
+  if (t.host_chunk_log2 < 16 || t.host_chunk_log2 > 24)
+    return set_error(ISPRIME_EINVAL, "host_chunk_log2 must be in [16, 24]");
   if (t.td2_groups != 0 && t.td2_groups != 8 && t.td2_groups != 12 && t.td2_groups != 16 &&
       t.td2_groups != 24)
     return set_error(ISPRIME_EINVAL, "td2_groups must be 0, 8, 12, 16 or 24");
@@ -184,7 +187,8 @@ static size_t scratch_bytes(const isprime_ctx* ctx) {
   return ctx->sieve_limit / 16 +
          (ctx->q.capacity + ctx->q2.capacity + ctx->host_q[0].capacity +
           ctx->host_q[1].capacity) * 24 +
-         ctx->stage_elems * 9 + 2 * sizeof(unsigned long long) + ctx->window_cap;
+         ctx->stage_elems * 9 * isprime_ctx::kStageSlots + 2 * sizeof(unsigned long long) +
+         ctx->window_cap;
 }
 
 struct DeviceGuard {
@@ -619,12 +623,16 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
   DeviceGuard g(ctx->device);
   if (n <= (size_t)kInlineMax) return inline_run(ctx, h_in, h_out, n, s);
   std::lock_guard<std::mutex> host_lock(ctx->host_mu);
-  // Pipeline: chunk k is copied in on copy_in, classified on the compute
-  // stream of staging slot k % 2 with that slot's own queues, and copied out
-  // on copy_out, so the copy-in of chunk k+1 and the copy-out of chunk k-1
-  // overlap the kernels of chunk k, and the kernels of consecutive chunks
-  // overlap each other's tails.
-  const size_t step_max = std::min((size_t)1 << ctx->tune.chunk_log2, (size_t)1 << 22);
+  // Pipeline: chunk k is copied in on copy_in into staging slot k % 4,
+  // classified on compute stream k % 2 with that stream's own queues, and
+  // copied out on copy_out.  With four staging slots the copy engine runs up
+  // to two chunks ahead of the kernels (a slot is refilled once the chunk
+  // four back has been computed and copied out), so after the first chunk
+  // the kernels rarely wait for a copy; the kernels of consecutive chunks, on
+  // the two streams, overlap each other's tails.
+  constexpr int kSlots = isprime_ctx::kStageSlots;
+  const size_t step_max =
+      std::min((size_t)1 << ctx->tune.chunk_log2, (size_t)1 << ctx->tune.host_chunk_log2);
   const size_t stage = std::min(step_max, n);
   {
     std::lock_guard<std::mutex> lock(ctx->mu);
@@ -648,15 +656,15 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
       ctx->d_stage_in = nullptr;
       ctx->d_stage_out = nullptr;
       ctx->stage_elems = 0;
-      IP_CUDA(cudaMalloc(&ctx->d_stage_in, 2 * stage * sizeof(uint64_t)));
-      IP_CUDA(cudaMalloc(&ctx->d_stage_out, 2 * stage));
+      IP_CUDA(cudaMalloc(&ctx->d_stage_in, kSlots * stage * sizeof(uint64_t)));
+      IP_CUDA(cudaMalloc(&ctx->d_stage_out, kSlots * stage));
       ctx->stage_elems = stage;
     }
   }
   const size_t step = std::min(ctx->stage_elems, step_max);
-  cudaEvent_t* in_ready = &ctx->stage_ev[0];   // [2] copy-in of a slot finished
-  cudaEvent_t* comp_done = &ctx->stage_ev[2];  // [2] kernels reading/writing a slot finished
-  cudaEvent_t* out_done = &ctx->stage_ev[4];   // [2] copy-out of a slot finished
+  cudaEvent_t* in_ready = &ctx->stage_ev[0];            // copy-in of a slot finished
+  cudaEvent_t* comp_done = &ctx->stage_ev[kSlots];      // kernels on a slot finished
+  cudaEvent_t* out_done = &ctx->stage_ev[2 * kSlots];   // copy-out of a slot finished
   // The slots may still be in use by a previous call's last chunks.
   IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->host_last, 0));
   // Arrays of at least four full chunks start with a quarter and a half of a
@@ -672,20 +680,21 @@ int isprime_u64_host(isprime_ctx* ctx, const uint64_t* h_in, uint8_t* h_out, siz
   for (size_t off = 0, k = 0, len = 0; off < n; off += len, ++k) {
     const size_t want = ramp_up && k == 0 ? step / 4 : ramp_up && k == 1 ? step / 2 : even;
     len = std::min(want, n - off);
-    const int slot = (int)(k & 1);
+    const int slot = (int)(k % kSlots);
+    const int lane = (int)(k & 1);  // compute stream and queue set
     uint64_t* din = ctx->d_stage_in + slot * step;
     uint8_t* dout = ctx->d_stage_out + slot * step;
-    if (k >= 2) IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, comp_done[slot], 0));
+    if (k >= (size_t)kSlots) IP_CUDA(cudaStreamWaitEvent(ctx->copy_in, comp_done[slot], 0));
     IP_CUDA(cudaMemcpyAsync(din, h_in + off, len * 8, cudaMemcpyHostToDevice, ctx->copy_in));
     IP_CUDA(cudaEventRecord(in_ready[slot], ctx->copy_in));
-    const cudaStream_t cs = ctx->host_s[slot];
+    const cudaStream_t cs = ctx->host_s[lane];
     IP_CUDA(cudaStreamWaitEvent(cs, in_ready[slot], 0));
-    if (k >= 2) IP_CUDA(cudaStreamWaitEvent(cs, out_done[slot], 0));
+    if (k >= (size_t)kSlots) IP_CUDA(cudaStreamWaitEvent(cs, out_done[slot], 0));
     {
       std::lock_guard<std::mutex> lock(ctx->mu);
       st = len <= ctx->tune.small_max
                ? launch_small_u64(ctx, din, dout, len, cs)
-               : run_chunk<false>(ctx, ctx->host_q[slot], din, dout, len, nullptr, cs);
+               : run_chunk<false>(ctx, ctx->host_q[lane], din, dout, len, nullptr, cs);
     }
     if (st) return st;
     IP_CUDA(cudaEventRecord(comp_done[slot], cs));

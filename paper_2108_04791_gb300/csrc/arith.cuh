@@ -767,29 +767,48 @@ IP_HD bool sprp2_64(const Mont64& M, uint64_t d, int s) {
   return false;
 }
 
-// Second trial-division stage: true when a prime of the first kGroups groups
-// of T divides n (n > 457, so such a divisor makes n composite).  Per group
-// of product m (odd, < 2^32), with n = n1 2^32 + n0:
-//   q = n0 (-m^-1) mod 2^32,  u = q m + n0 < 2^64 (its low word is 0),
+// A 32-bit residue of n = n1 2^32 + n0 modulo an odd m < 2^32 (mneg =
+// -m^-1 mod 2^32), by one Montgomery reduction step:
+//   q = n0 mneg mod 2^32,  u = q m + n0 < 2^64 (its low word is 0),
 //   t = n1 + u / 2^32 = (n + q m) / 2^32,
 // so t = n 2^-32 (mod m) and t <= 2^32 - 1 + m (u / 2^32 <= m); subtracting m
 // once when t >= m leaves r < 2^32 with the same residue.  2^-32 is a unit
 // modulo every odd p | m, so p | n exactly when p | r, and p | r is the
 // 32-bit test r p^-1 mod 2^32 <= floor((2^32 - 1) / p).
+IP_HD uint32_t mont_residue32(uint32_t n0, uint32_t n1, uint32_t m, uint32_t mneg) {
+  const uint32_t q = n0 * mneg;
+  const uint64_t u = (uint64_t)q * m + n0;
+  const uint64_t t = (uint64_t)n1 + (u >> 32);
+  return (uint32_t)(t >= m ? t - m : t);
+}
+
+// Second trial-division stage: true when a prime of the first kGroups groups
+// of T divides n (n > 457, so such a divisor makes n composite): one residue
+// per group of three primes, each prime tested on it.
 template <int kGroups>
 IP_HD bool td2_divisible(uint64_t n, const Td2Table& T) {
   const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
   bool div = false;
   IP_UNROLL
   for (int g = 0; g < kGroups; ++g) {
-    const uint32_t m = T.m[g];
-    const uint32_t q = n0 * T.mneg[g];
-    const uint64_t u = (uint64_t)q * m + n0;
-    const uint64_t t = (uint64_t)n1 + (u >> 32);
-    const uint32_t r = (uint32_t)(t >= m ? t - m : t);
+    const uint32_t r = mont_residue32(n0, n1, T.m[g], T.mneg[g]);
     IP_UNROLL
     for (int k = 3 * g; k < 3 * g + 3; ++k) div |= (uint32_t)(r * T.inv[k]) <= T.lim[k];
   }
+  return div;
+}
+
+// Trial division of a 64-bit n by the odd primes 3..53 on two residues (the
+// groups A and B of tables.cuh): true when one of them divides n.  inv and lim
+// are the primes' 32-bit inverses and limits in the order of kTdPrimeList.
+IP_HD bool td_pair_divisible(uint64_t n, const uint32_t* inv, const uint32_t* lim) {
+  const uint32_t n0 = (uint32_t)n, n1 = (uint32_t)(n >> 32);
+  const uint32_t ra = mont_residue32(n0, n1, kTdPairA, kTdPairNegA);
+  const uint32_t rb = mont_residue32(n0, n1, kTdPairB, kTdPairNegB);
+  bool div = false;
+  IP_UNROLL
+  for (int i = 0; i < kFoldPrimes; ++i)
+    div |= (uint32_t)((td_pair_in_a(i) ? ra : rb) * inv[i]) <= lim[i];
   return div;
 }
 

@@ -44,7 +44,7 @@ std::vector<Param> params() {
       {"mont_impl_base2", &isprime_tuning::mont_impl_base2, {6, 0, 5}, P},
       {"base2_window", &isprime_tuning::base2_window, {0, 1, 4}, P},
       {"compact_min", &isprime_tuning::compact_min, {33, 28, 24, 16}, P},
-      {"td_fold", &isprime_tuning::td_fold, {0, 1, 2}, P},
+      {"td_fold", &isprime_tuning::td_fold, {0, 1, 2, 3}, P},
       {"base2_split", &isprime_tuning::base2_split, {0, 1}, P},
       {"base2_ilp", &isprime_tuning::base2_ilp, {1, 2}, P},
       {"rest_window", &isprime_tuning::rest_window, {4, 3}, P},
@@ -77,7 +77,7 @@ const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_prim
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
                          "compact_min", "sieve_cutover_log2", "serve_short_max", "td_fold",
                          "base2_split", "base2_ilp", "rest_window", "window_ratio16",
-                         "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream"};
+                         "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream", "host_chunk_log2"};
 FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
@@ -88,8 +88,8 @@ FieldPtr kFieldPtr[] = {
     &isprime_tuning::serve_short_max, &isprime_tuning::td_fold, &isprime_tuning::base2_split,
     &isprime_tuning::base2_ilp, &isprime_tuning::rest_window, &isprime_tuning::window_ratio16,
     &isprime_tuning::base2_blocks_per_sm, &isprime_tuning::pdl, &isprime_tuning::td2_groups,
-    &isprime_tuning::dual_stream};
-constexpr int kNumFields = 25;
+    &isprime_tuning::dual_stream, &isprime_tuning::host_chunk_log2};
+constexpr int kNumFields = 26;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

@@ -60,13 +60,15 @@ __device__ void classify_single(const ClassifyArgs& a, uint64_t i) {
   if (!ok && a.invalid_ctx) atomicAdd(a.invalid_ctx, 1ull);
   if (IP_CHECK(i < a.n, kChkOut)) a.out[i] = (uint8_t)(d == kPrime);
   if (d == kMR64) {
-    const uint32_t pos = atomicAdd(&a.counters[0], 1u);
+    // the front size is the low half of the 64-bit word counters[0..1]
+    const uint32_t pos =
+        (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(a.counters), 1ull);
     if (IP_CHECK(pos < a.q64_cap, kChkQ64Front)) {
       a.q64_n[pos] = v;
       a.q64_idx[pos] = (uint32_t)i;
     }
   } else if (d == kMR32) {
-    const uint32_t pos = atomicAdd(&a.counters[1], 1u);
+    const uint32_t pos = atomicAdd(&a.counters[4], 1u);
     if (IP_CHECK(pos < a.q64_cap, kChkQ32)) {
       a.q32_n[pos] = (uint32_t)v;
       a.q32_idx[pos] = (uint32_t)i;
@@ -166,9 +168,14 @@ __global__ void __maxnreg__(40) classify_kernel(ClassifyArgs a) {
     uint32_t bf = 0, bb = 0, b32 = 0;
     if (lane == 0) {
       const uint32_t tf = wtot & 0x3FFu, tb = (wtot >> 10) & 0x3FFu, t32 = wtot >> 20;
-      if (tf) bf = atomicAdd(&a.counters[0], tf);
-      if (tb) bb = atomicAdd(&a.counters[4], tb);
-      if (t32) b32 = atomicAdd(&a.counters[1], t32);
+      // front and back sizes in one 64-bit word: one atomic for both regions
+      if (tf | tb) {
+        const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(a.counters),
+                                                 (unsigned long long)tf | ((unsigned long long)tb << 32));
+        bf = (uint32_t)old;
+        bb = (uint32_t)(old >> 32);
+      }
+      if (t32) b32 = atomicAdd(&a.counters[4], t32);
     }
     if (a.invalid || a.invalid_ctx) {
       const unsigned bad = __reduce_add_sync(0xFFFFFFFFu, nbad);
@@ -232,7 +239,9 @@ static void launch_classify_kernel(const ClassifyArgs& a, unsigned grid, unsigne
       case 2: classify_kernel<T, 15, 1, false><<<grid, block, 0, s>>>(a); return;
       case 3: classify_kernel<T, 15, 1, true><<<grid, block, 0, s>>>(a); return;
       case 4: classify_kernel<T, 15, 2, false><<<grid, block, 0, s>>>(a); return;
-      default: classify_kernel<T, 15, 2, true><<<grid, block, 0, s>>>(a); return;
+      case 5: classify_kernel<T, 15, 2, true><<<grid, block, 0, s>>>(a); return;
+      case 6: classify_kernel<T, 15, 3, false><<<grid, block, 0, s>>>(a); return;
+      default: classify_kernel<T, 15, 3, true><<<grid, block, 0, s>>>(a); return;
     }
   }
   switch (a.ntd) {

@@ -123,6 +123,8 @@ __device__ __forceinline__ int classify_value(uint64_t n, const P& a) {
         hit |= v * c_td.inv32[i] <= c_td.lim32[i];
         equal |= v == c_td.p[i];
       }
+    } else if constexpr (kFold == 3 && kNtd == kFoldPrimes) {
+      hit = td_pair_divisible(n, c_td.inv32, c_td.lim32);
     } else if constexpr (kFold > 0 && kNtd > 0) {
       const uint32_t lo = (uint32_t)n, hi = (uint32_t)(n >> 32);
       const uint32_t v32 = fold_sum32(lo, hi), v24 = fold_sum24(lo, hi);

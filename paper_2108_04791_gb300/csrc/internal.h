@@ -43,8 +43,11 @@ struct Queues {
   uint32_t* q64b = nullptr;     // positions in q64 that passed the base-2 test
   uint32_t* q32_n = nullptr;    // values in [S, 2^32) that survived trial division
   uint32_t* q32_idx = nullptr;
-  // [0] q64 front size, [1] q32 size, [2] q64b size, [3] base-2 task counter,
-  // [4] q64 back size (entries at capacity - 1, capacity - 2, ...), [5..7] unused
+  // [0] q64 front size, [1] q64 back size (entries at capacity - 1,
+  // capacity - 2, ...), [2] q64b size, [3] base-2 task counter, [4] q32 size,
+  // [5..7] unused.  [0] and [1] form one 64-bit word (front + 2^32 back) that
+  // classify advances with a single 64-bit atomic per warp for both regions
+  // (two 32-bit atomics on one sector cost classify a third of its time).
   uint32_t* counters = nullptr;
   size_t capacity = 0;
 };
@@ -119,7 +122,8 @@ struct isprime_ctx {
   size_t stage_elems = 0;
   cudaStream_t copy_in = nullptr;    // host -> device copies of the host path
   cudaStream_t copy_out = nullptr;   // device -> host copies of the host path
-  cudaEvent_t stage_ev[6] = {};      // per staging slot: copied in, computed, copied out
+  static constexpr int kStageSlots = 4;  // host path: staging buffers in flight
+  cudaEvent_t stage_ev[3 * kStageSlots] = {};  // per staging slot: copied in, computed, copied out
   cudaEvent_t host_last = nullptr;   // end of the previous host-path call
   ip::BatchState batch;              // batched path of the context's own calls
   ip::Queues host_q[2];              // host path: one queue set per staging slot

@@ -73,7 +73,7 @@ static void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, si
 // exponentiations per thread, base2_passes_shift_x2).
 //
 // The queue q64 has two regions (see classify.cu): [0, counters[0]) from the
-// front and [cap - counters[4], cap) from the back.  When classify splits by
+// front and [cap - counters[1], cap) from the back.  When classify splits by
 // s (n - 1 = 2^s d), the front holds s = 1 and the back s >= 2, so the
 // strong-test tail, which a warp runs for its largest s, is empty for the
 // front's warps.  Tasks of 32 * kIlp positions walk the front region (its
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   constexpr uint32_t kTask = 32u * kIlp;
   wait_for_producer();
   const uint32_t count_f = *(volatile uint32_t*)&counters[0];
-  const uint32_t count_b = *(volatile uint32_t*)&counters[4];
+  const uint32_t count_b = *(volatile uint32_t*)&counters[1];
   const uint32_t front_pad = (count_f + kTask - 1) / kTask * kTask;
   const uint32_t vcount = front_pad + count_b;  // virtual positions: front (padded), back
   const uint32_t back0 = cap - count_b;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256) mr32_kernel(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ counters,
                                                    uint8_t* __restrict__ out, uint32_t cap) {
   wait_for_producer();
-  const uint32_t count = *(volatile const uint32_t*)&counters[1];
+  const uint32_t count = *(volatile const uint32_t*)&counters[4];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
     if (IP_CHECK(i < cap && qidx[i] < cap, kChkMr32) && mr32_is_prime(qn[i])) out[qidx[i]] = 1;
 }

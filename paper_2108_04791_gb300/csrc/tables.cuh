@@ -107,6 +107,31 @@ constexpr bool fold_widths_divide() {
 }
 static_assert(fold_widths_divide(), "a folded prime does not divide 2^k - 1");
 
+// Trial division by two residues (td_fold 3).  The product of the odd primes
+// 3..53 is below 2^64 and splits into two groups with products below 2^32:
+//   A = 29 * 31 * 41 * 43 * 47 * 53 = 3,948,078,067
+//   B = 3 * 5 * 7 * 11 * 13 * 17 * 19 * 23 * 37 = 4,127,218,095
+// A 64-bit n is reduced to one 32-bit residue per group (mont_residue32 in
+// arith.cuh) and every prime is tested on its group's residue with the 32-bit
+// multiply-by-inverse test: two reductions and fifteen 32-bit tests instead of
+// chunk sums and 64-bit tests.  td_pair_in_a(i) is plain arithmetic on the
+// prime's index i (no table: device code calls it).
+constexpr bool td_pair_in_a(int i) { return i == 8 || i == 9 || (i >= 11 && i < kFoldPrimes); }
+constexpr uint64_t td_pair_product(bool group_a) {
+  uint64_t m = 1;
+  for (int i = 0; i < kFoldPrimes; ++i)
+    if (td_pair_in_a(i) == group_a) m *= kTdPrimeList[i];
+  return m;
+}
+static_assert(td_pair_product(true) < ((uint64_t)1 << 32) && td_pair_product(false) < ((uint64_t)1 << 32),
+              "two-residue trial division: a group's product does not fit 32 bits");
+static_assert(td_pair_product(true) == 3948078067ull && td_pair_product(false) == 4127218095ull,
+              "two-residue trial division: the groups");
+constexpr uint32_t kTdPairA = (uint32_t)td_pair_product(true);
+constexpr uint32_t kTdPairB = (uint32_t)td_pair_product(false);
+constexpr uint32_t kTdPairNegA = 0u - (uint32_t)ce_inv64(kTdPairA);  // -A^-1 mod 2^32
+constexpr uint32_t kTdPairNegB = 0u - (uint32_t)ce_inv64(kTdPairB);
+
 // Second trial-division stage (tuning td2_groups): the odd primes after 53,
 // tested only on the survivors of the first stage (the base-2 kernel's
 // queue), where a removed value saves a whole base-2 exponentiation.  They

@@ -52,6 +52,10 @@ int h_td2(uint64_t n, int groups) {
   }
 }
 uint32_t h_td2_prime(int i) { return ip::kTd2Host.p[i]; }
+int h_td_pair(uint64_t n) { return ip::td_pair_divisible(n, ip::kTdHost.inv32, ip::kTdHost.lim32); }
+uint32_t h_mont_residue32(uint64_t n, uint32_t m) {
+  return ip::mont_residue32((uint32_t)n, (uint32_t)(n >> 32), m, 0u - ip::inv32(m));
+}
 uint32_t h_td2_modulus(int g) { return ip::kTd2Host.m[g]; }
 }
 

@@ -34,7 +34,8 @@ def H(tmp_path_factory):
                             ("h_sprp32", [u32, u32], i32), ("h_td64", [u64, i32], i32),
                             ("h_td32", [u32, i32], i32), ("h_td_prime", [i32], u32),
                             ("h_td2", [u64, i32], i32), ("h_td2_prime", [i32], u32),
-                            ("h_td2_modulus", [i32], u32),
+                            ("h_td2_modulus", [i32], u32), ("h_td_pair", [u64], i32),
+                            ("h_mont_residue32", [u64, u32], u32),
                             ("h_mont_mul_w", [u64, u64, u64], u64), ("h_mont_sqr_w", [u64, u64], u64),
                             ("h_mont_sqr_h", [u64, u64], u64),
                             ("h_mont_mul_f", [u64, u64, u64], u64), ("h_mont_sqr_f", [u64, u64], u64),
@@ -180,6 +181,31 @@ def test_second_trial_stage(H):
         for v in vals:
             assert H.h_td2(v, groups) == int(any(v % p == 0 for p in ps)), (v, groups)
     assert H.h_td2(2**40, 5) == -1
+
+
+def test_two_residue_trial_division(H):
+    """td_pair_divisible (classify's td_fold 3): n is divisible by one of the
+    odd primes 3..53 exactly when one of its two Montgomery residues (modulo
+    29*31*41*43*47*53 and 3*5*7*11*13*17*19*23*37, both just below 2^32) is
+    divisible by that prime; and mont_residue32 returns a value below 2^32
+    congruent to n * 2^-32 modulo m, for moduli up to 2^32 - 1."""
+    primes = [3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53]
+    a, b = 29 * 31 * 41 * 43 * 47 * 53, 3 * 5 * 7 * 11 * 13 * 17 * 19 * 23 * 37
+    assert a == 3948078067 and b == 4127218095 and a * b == math.prod(primes)
+    rng = random.Random(28)
+    vals = [rng.randrange(2**32, R) for _ in range(4000)]
+    vals += [(rng.randrange(1, 2**32) << 32) for _ in range(200)]
+    vals += [(0xFFFFFFFF << 32) | rng.randrange(2**32) for _ in range(300)] + [R - 1 - k for k in range(300)]
+    for m in (a, b) + tuple(primes):
+        vals += [m * (R // m - j) + r for j in range(3) for r in (0, 1, m - 1) if m * (R // m - j) + r < R]
+        vals += [m * rng.randrange(2**32 // m + 1, R // m) for _ in range(20)]
+    for v in vals:
+        assert H.h_td_pair(v) == int(any(v % p == 0 for p in primes)), v
+    for m in (a, b, 3, 4294967291, 2**32 - 1, 65537):
+        ri = pow(2**32, -1, m)
+        for v in vals[:500] + [m, m * m % R, R - 1]:
+            r = H.h_mont_residue32(v, m)
+            assert r < 2**32 and r % m == v * ri % m, (v, m, r)
 
 
 def test_jacobi_and_squares(H):

@@ -327,6 +327,26 @@ def test_host_path_matches_device_path():
     _assert_same(v, got, oracle.isprime_u64(v))
 
 
+@pytest.mark.parametrize("n,host_log2", [((1 << 20) + 4097, 16), ((1 << 21) + 3, 18),
+                                         (5 * (1 << 18) + 77, 17), ((1 << 16) + 1, 16)])
+def test_host_path_many_chunks_reuse_every_staging_slot(n, host_log2):
+    """isprime_u64_host with chunks of at most 2^host_chunk_log2 values: the
+    ramp-up chunks, then equal chunks, the four staging slots each reused
+    several times (a slot's refill waits for the chunk four back to be
+    computed and copied out) and the two compute streams alternating; two
+    calls in a row with different inputs."""
+    v1 = plain_mixed(n, seed=43)
+    v2 = plain_large(n, seed=44)
+    with ipg.Context(0, sieve_limit=1 << 24) as c:
+        c.set_tuning(host_chunk_log2=host_log2, small_max=0)
+        _assert_same(v1, c.isprime_host(v1), oracle.isprime_u64(v1))
+        _assert_same(v2, c.isprime_host(v2), oracle.isprime_u64(v2))
+        with pytest.raises(ipg.IsPrimeError):
+            c.set_tuning(host_chunk_log2=15)
+        with pytest.raises(ipg.IsPrimeError):
+            c.set_tuning(host_chunk_log2=25)
+
+
 def test_two_streams_share_one_context():
     v1 = plain_large(1 << 18, seed=41)
     v2 = plain_mixed(1 << 18, seed=42)

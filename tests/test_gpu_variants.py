@@ -89,7 +89,7 @@ def _same(v, got, want, what):
                            f"gpu={int(got[bad[0]])} oracle={int(want[bad[0]])}")
 
 
-COMBOS = list(itertools.product([0, 1, 2], [0, 1], [1, 2], [3, 4]))
+COMBOS = list(itertools.product([0, 1, 2, 3], [0, 1], [1, 2], [3, 4]))
 
 
 @pytest.mark.parametrize("fold,split,ilp,win", COMBOS)
@@ -288,9 +288,10 @@ def test_second_trial_stage_on_short_queues(td2_data, ctx):
         ctx.set_tuning(td2_groups=0)
 
 
-def test_second_trial_stage_host_and_double_paths(td2_data, ctx):
+@pytest.mark.parametrize("fold", [2, 3])
+def test_second_trial_stage_host_and_double_paths(fold, td2_data, ctx):
     v, want = td2_data
-    ctx.set_tuning(td2_groups=24, small_max=0, chunk_log2=16)
+    ctx.set_tuning(td2_groups=24, small_max=0, chunk_log2=16, td_fold=fold)
     try:
         _same(v, ctx.isprime_host(v), want, "td2 host path")
         d = (v[:200_000] >> np.uint64(11)).astype(np.float64)  # integers below 2^53
@@ -298,13 +299,13 @@ def test_second_trial_stage_host_and_double_paths(td2_data, ctx):
         got = ctx.isprime(torch.from_numpy(d).to("cuda:0"))
         torch.cuda.synchronize()
         assert bad == 0
-        _same(d, got.cpu().numpy(), wd, "td2 double path")
+        _same(d, got.cpu().numpy(), wd, f"td2 double path fold={fold}")
     finally:
-        ctx.set_tuning(td2_groups=0, chunk_log2=24)
+        ctx.set_tuning(td2_groups=0, chunk_log2=24, td_fold=2)
 
 
 def test_tuning_rejects_out_of_range_variant_fields(ctx):
-    for kw in (dict(td_fold=3), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
+    for kw in (dict(td_fold=4), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
                dict(mont_impl=10), dict(mont_impl_base2=10), dict(pdl=2), dict(dual_stream=2),
                dict(td2_groups=4), dict(td2_groups=25),
                dict(rest_window=5), dict(rest_window=2)):
