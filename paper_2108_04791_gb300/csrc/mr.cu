@@ -84,8 +84,9 @@ static void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, si
 // stages the values that survive it in its slice of shared memory (a stack of
 // at most 63 positions and values); whenever 32 are staged, the warp runs the
 // base-2 test on the top 32, so the exponentiations run on full warps while
-// about a quarter of the queue never reaches them.  A warp with no task left
-// runs what it still holds.
+// about a quarter of the queue never reaches them.  When no task is left, the
+// warps of a block pool what their stacks still hold and run it as full
+// batches.
 template <int kImpl, int kMode, int kRest, int kIlp = 1, int kTd2 = 0>
 __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restrict__ qn,
                                                          const uint32_t* __restrict__ qidx,
@@ -129,9 +130,16 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
   };
   if constexpr (kTd2 > 0) {
     static_assert(kMode == 1 && kRest == 0 && kIlp == 1, "second trial stage: shift windows only");
-    // this warp's stack: 64 values, then 64 positions
-    uint64_t* st_n = s_tab + (threadIdx.x >> 5) * 96;
+    // this warp's stack: 64 values, then 64 positions; after the block's
+    // stacks, the block's leftovers (31 per warp at most): values, positions
+    const int nwarps = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5);
+    uint64_t* st_n = s_tab + warp * 96;
     uint32_t* st_pos = reinterpret_cast<uint32_t*>(st_n + 64);
+    uint64_t* left_n = s_tab + nwarps * 96;
+    uint32_t* left_pos = reinterpret_cast<uint32_t*>(left_n + 32 * nwarps);
+    __shared__ uint32_t s_left;
+    if (threadIdx.x == 0) s_left = 0;
+    __syncthreads();
     int held = 0;  // staged values, the same in every lane
     for (;;) {
       const bool have = next < vcount;
@@ -163,22 +171,39 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
         next = __shfl_sync(0xFFFFFFFFu, next, 0);
         __syncwarp();
       }
-      // full batches from the top of the stack; with no task left, the rest
-      while (held >= 32 || (!have && held > 0)) {
-        const int b0 = held >= 32 ? held - 32 : 0;
-        const bool valid = lane < held - b0;
-        const uint64_t n = valid ? st_n[b0 + lane] : 0xFFFFFFFFFFFFFFC5ull;
-        const uint32_t pos = valid ? st_pos[b0 + lane] : 0u;
+      // full batches from the top of the stack
+      while (held >= 32) {
+        const uint64_t n = st_n[held - 32 + lane];
+        const uint32_t pos = st_pos[held - 32 + lane];
         __syncwarp();  // read before the next task's values overwrite the slots
-        held = b0;
-        bool pass = false;
-        if (valid) {
-          const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
-          pass = base2_passes_shift<kImpl>(n, nib);
-        }
-        append_passing(pass, pos);
+        held -= 32;
+        const int nib = __reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(n));
+        append_passing(base2_passes_shift<kImpl>(n, nib), pos);
       }
       if (!have) break;
+    }
+    // No task left: the warps of the block pool what their stacks still hold
+    // (fewer than 32 each) and run it as full batches, about half as many
+    // warp-batches as each warp running its own partial one.
+    uint32_t at = 0;
+    if (lane == 0 && held > 0) at = atomicAdd(&s_left, (uint32_t)held);
+    at = __shfl_sync(0xFFFFFFFFu, at, 0);
+    if (lane < held && IP_CHECK(at + lane < 32u * nwarps, kChkSmemQueue)) {
+      left_n[at + lane] = st_n[lane];
+      left_pos[at + lane] = st_pos[lane];
+    }
+    __syncthreads();
+    const uint32_t left = s_left;
+    for (uint32_t b = 32u * warp; b < left; b += 32u * nwarps) {
+      const bool valid = b + lane < left;
+      const uint64_t n = valid ? left_n[b + lane] : 0xFFFFFFFFFFFFFFC5ull;
+      const uint32_t pos = valid ? left_pos[b + lane] : 0u;
+      bool pass = false;
+      if (valid) {
+        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
+        pass = base2_passes_shift<kImpl>(n, nib);
+      }
+      append_passing(pass, pos);
     }
     return;
   }
@@ -353,8 +378,9 @@ static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsig
                              uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s,
                              int per_sm_cap, bool pdl) {
   // the table of mode 4 and the finishing of kRest 1: 16 words per thread;
-  // the second trial stage: 96 words per warp (64 values, 64 positions)
-  const size_t smem = kTd2 > 0 ? (size_t)96 * (block / 32) * sizeof(uint64_t)
+  // the second trial stage: 96 words per warp (64 values, 64 positions) and
+  // 48 for the block's leftovers (32 values and 32 positions)
+  const size_t smem = kTd2 > 0 ? (size_t)(96 + 48) * (block / 32) * sizeof(uint64_t)
                       : (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t)
                                                    : 0;
   auto kern = mr64_base2_kernel<kImpl, kMode, kRest, kIlp, kTd2>;
