@@ -26,10 +26,11 @@
 
 namespace ip {
 
-// Arithmetic: Montgomery formulation 6 (32-bit words in PTX) in both stages,
-// 3-bit windows for the six bases (as the plain path's default), and folded
-// trial division when the count is the default 15 primes.
-constexpr int kImplB2 = 6, kImplRest = 6;
+// Arithmetic: Montgomery formulation 9 (32-bit words in PTX, the final
+// correction on the multiply pipe) in both stages, 3-bit windows for the six
+// bases (as the plain path's defaults), and trial division on two residues
+// when the count is the default 15 primes.
+constexpr int kImplB2 = 9, kImplRest = 9;
 constexpr int kBatchWin = 3;
 
 struct BatchParams {
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchParams p) {
       uint64_t v = 0;
       if (e < e1) {
         v = d.in[e];
-        dec = classify_value<kNtd, BatchParams, false, (kNtd == 15 ? 2 : 0)>(v, p);
+        dec = classify_value<kNtd, BatchParams, false, (kNtd == 15 ? 3 : 0)>(v, p);
         if (IP_CHECK(e < d.n, kChkBatchOut)) d.out[e] = (uint8_t)(dec == kPrime);
       }
       smem_push(dec == kMR64 || dec == kMR32, v, (uint64_t)(d.out + e), q1v, q1a, &s_n1, q1cap);
