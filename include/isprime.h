@@ -93,7 +93,9 @@ typedef struct {
                               compact_min survivors finishes them in place (the rest_test
                               stage run by the same warp) instead of appending them to the
                               survivor queue; 0..33, 33 = always compact.  In-place finishing
-                              needs base2_window 1 or 4 (with 0 the survivors are always compacted) */
+                              needs base2_window 1 or 4 (with 0 the survivors are always compacted);
+                              with 0 or 1 every survivor is finished in place and the six-base
+                              kernel is not launched */
   uint32_t sieve_cutover_log2; /* sieve / Miller-Rabin cutover of the array paths: the resident
                               sieve answers n < min(S, 2^k); values from there up to 2^32 take
                               trial division and the 32-bit Miller-Rabin test (0..32) */
@@ -142,6 +144,10 @@ typedef struct {
                               keeps the caller's stream order); 0: one stream */
   uint32_t host_chunk_log2;  /* isprime_u64_host: chunks of at most 2^host_chunk_log2 values
                               (and at most 2^chunk_log2), 16..24, default 22 */
+  uint32_t inplace_max_log2; /* chunks of at most 2^inplace_max_log2 values run as if
+                              compact_min were 1 (base2_window 1 or 4): the base-2 kernel's
+                              warps finish their own passers and the six-base kernel is not
+                              launched; 0..24, 0 = never */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

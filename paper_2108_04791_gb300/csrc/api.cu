@@ -101,6 +101,7 @@ static isprime_tuning default_tuning() {
   t.pdl = 1;  // programmatic dependent launch of the Miller-Rabin kernels: 0.6% on plain_large
   t.td2_groups = 16;  // second trial stage, primes 59 .. 311: base 2 -12%, step -4.8% on plain_large
   t.dual_stream = 0;
+  t.inplace_max_log2 = 0;
   t.host_chunk_log2 = 22;  // host path: 1.089 ms per 2^24 values against 1.26 (23) and 1.15 (21)
   return t;
 }
@@ -132,6 +133,7 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.base2_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "base2_blocks_per_sm must be in [0, 32]");
   if (t.pdl > 1) return set_error(ISPRIME_EINVAL, "pdl must be 0 or 1");
   if (t.dual_stream > 1) return set_error(ISPRIME_EINVAL, "dual_stream must be 0 or 1");
+  if (t.inplace_max_log2 > 24) return set_error(ISPRIME_EINVAL, "inplace_max_log2 must be <= 24");
   if (t.host_chunk_log2 < 16 || t.host_chunk_log2 > 24)
     return set_error(ISPRIME_EINVAL, "host_chunk_log2 must be in [16, 24]");
   if (t.td2_groups != 0 && t.td2_groups != 8 && t.td2_groups != 12 && t.td2_groups != 16 &&

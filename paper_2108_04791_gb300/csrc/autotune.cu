@@ -40,8 +40,8 @@ std::vector<Param> params() {
       {"classify_block", &isprime_tuning::classify_block, {128, 256, 512}, P},
       {"mr_block", &isprime_tuning::mr_block, {64, 128, 256}, P},
       {"blocks_per_sm", &isprime_tuning::blocks_per_sm, {4, 8, 16}, P},
-      {"mont_impl", &isprime_tuning::mont_impl, {6, 0, 5}, P},
-      {"mont_impl_base2", &isprime_tuning::mont_impl_base2, {6, 0, 5}, P},
+      {"mont_impl", &isprime_tuning::mont_impl, {9, 6, 0, 5}, P},
+      {"mont_impl_base2", &isprime_tuning::mont_impl_base2, {9, 6, 0, 5}, P},
       {"base2_window", &isprime_tuning::base2_window, {0, 1, 4}, P},
       {"compact_min", &isprime_tuning::compact_min, {33, 28, 24, 16}, P},
       {"td_fold", &isprime_tuning::td_fold, {0, 1, 2, 3}, P},
@@ -52,6 +52,7 @@ std::vector<Param> params() {
       {"pdl", &isprime_tuning::pdl, {0, 1}, P},
       {"td2_groups", &isprime_tuning::td2_groups, {0, 8, 12, 16, 24}, P},
       {"dual_stream", &isprime_tuning::dual_stream, {0, 1}, P},
+      {"inplace_max_log2", &isprime_tuning::inplace_max_log2, {0, 17, 20, 24}, P},
       {"sieve_cutover_log2", &isprime_tuning::sieve_cutover_log2, {32, 28, 24, 20}, P | B},
       {"batch_block", &isprime_tuning::batch_block, {64, 128, 256}, B},
       {"batch_tile_log2", &isprime_tuning::batch_tile_log2, {8, 9, 10, 11, 12}, B},
@@ -77,7 +78,7 @@ const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_prim
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
                          "compact_min", "sieve_cutover_log2", "serve_short_max", "td_fold",
                          "base2_split", "base2_ilp", "rest_window", "window_ratio16",
-                         "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream", "host_chunk_log2"};
+                         "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream", "host_chunk_log2", "inplace_max_log2"};
 FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
@@ -88,8 +89,9 @@ FieldPtr kFieldPtr[] = {
     &isprime_tuning::serve_short_max, &isprime_tuning::td_fold, &isprime_tuning::base2_split,
     &isprime_tuning::base2_ilp, &isprime_tuning::rest_window, &isprime_tuning::window_ratio16,
     &isprime_tuning::base2_blocks_per_sm, &isprime_tuning::pdl, &isprime_tuning::td2_groups,
-    &isprime_tuning::dual_stream, &isprime_tuning::host_chunk_log2};
-constexpr int kNumFields = 26;
+    &isprime_tuning::dual_stream, &isprime_tuning::host_chunk_log2,
+    &isprime_tuning::inplace_max_log2};
+constexpr int kNumFields = 27;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

@@ -501,6 +501,9 @@ static int launch_mr64(const Queues& q, uint8_t* out, unsigned grid, unsigned bl
     default: launch_base2<0>(q, out, grid, block, o, mark, sm_count, s); break;
   }
   if (ctx && (st = launch_end(ctx, s, &tl, "mr64_base2_kernel"))) return st;
+  // compact_min <= 1 with a windowed base-2 schedule: every warp finishes its
+  // own passers, nothing is compacted, and the six-base kernel has no work
+  if (o.compact_min <= 1 && o.window != 0) return st;
   if (ctx && (st = launch_begin(ctx, ISPRIME_K_MR64_REST, s, &tl))) return st;
   switch (o.impl) {
     case 1: launch_rest<1>(q, out, grid, block, o, spread_grid, sm_count, s); break;
@@ -552,6 +555,12 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
   o.b2_per_sm = (int)ctx->tune.base2_blocks_per_sm;
   o.pdl = ctx->tune.pdl != 0 && !ctx->timing;  // timing events between launches would serialise them
   o.td2 = (int)ctx->tune.td2_groups;
+  // Short chunks: every warp of the base-2 kernel finishes its own passers
+  // and the six-base kernel is not launched (one launch less per call, where
+  // launches, not arithmetic, set the time).
+  if (ctx->tune.inplace_max_log2 != 0 && len <= ((uint64_t)1 << ctx->tune.inplace_max_log2) &&
+      o.window != 0)
+    o.compact_min = 1;
   if (ctx->count_ops) {  // isprime_count_ops: formulation 6 with its operations counted
     o.impl_b2 = 16;
     o.impl = 17;

@@ -280,10 +280,15 @@ def test_tuning_does_not_change_results():
                    dict(pdl=1), dict(pdl=1, sieve_cutover_log2=20), dict(pdl=1, base2_window=0),
                    dict(pdl=1, rest_test=1), dict(pdl=1, chunk_log2=16), dict(pdl=0),
                    dict(compact_min=0), dict(compact_min=1), dict(compact_min=16),
+                   dict(compact_min=1, base2_window=4), dict(compact_min=0, rest_test=1),
+                   dict(compact_min=1, base2_window=0), dict(compact_min=1, chunk_log2=16),
+                   dict(compact_min=0, base2_window=1, chunk_log2=24),
                    dict(compact_min=4, rest_test=1), dict(compact_min=8, mont_impl_base2=5),
                    dict(compact_min=2, base2_window=0), dict(compact_min=33),
                    dict(sieve_cutover_log2=0), dict(sieve_cutover_log2=20),
-                   dict(sieve_cutover_log2=23, td_primes=0), dict(sieve_cutover_log2=32)]:
+                   dict(sieve_cutover_log2=23, td_primes=0), dict(sieve_cutover_log2=32),
+                   dict(inplace_max_log2=20, chunk_log2=24), dict(inplace_max_log2=16, chunk_log2=16),
+                   dict(inplace_max_log2=20, rest_test=1), dict(inplace_max_log2=20, base2_window=0)]:
             c.set_tuning(**kw)
             _assert_same(v, _gpu(v, c), want)
 
