@@ -80,9 +80,12 @@ typedef struct {
   uint32_t batch_blocks_per_sm; /* cap on resident batched blocks per SM (0 = occupancy limit) */
   uint32_t base2_window;   /* base-2 exponentiation: 0 binary with a doubling per set bit;
                               1 4-bit windows, x 2^w mod n as x 2^w - q n with q estimated
-                              from a single-precision reciprocal of n (default); 4 4-bit
-                              windows, x 2^w R mod n by a Montgomery product with a table of
-                              2^w R in shared memory */
+                              from a single-precision reciprocal of n (default); 2 the same
+                              windows with q estimated in integers (one high multiply by a 32-bit
+                              reciprocal of n); 4 4-bit windows, x 2^w R mod n by a Montgomery
+                              product with a table of 2^w R in shared memory.  Modes 1 and 2
+                              take the second trial stage, finishing in place and (mode 1) two
+                              survivors per thread */
   uint32_t rest_test;      /* after base 2: 0 the six remaining bases of Eq. 4 (default), 1 the
                               strong Lucas test with Selfridge's parameters (Baillie-PSW).
                               Both are exact below 2^64; 1 rests on the published search

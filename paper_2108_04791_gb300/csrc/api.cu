@@ -118,8 +118,8 @@ static int check_tuning(const isprime_tuning& t) {
   if (bad_block(t.batch_block, 256)) return set_error(ISPRIME_EINVAL, "batch_block must be a multiple of 32 in [32, 256]");
   if (t.batch_tile_log2 < 8 || t.batch_tile_log2 > 14) return set_error(ISPRIME_EINVAL, "batch_tile_log2 must be in [8, 14]");
   if (t.batch_blocks_per_sm > 32) return set_error(ISPRIME_EINVAL, "batch_blocks_per_sm must be in [0, 32]");
-  if (t.base2_window != 0 && t.base2_window != 1 && t.base2_window != 4)
-    return set_error(ISPRIME_EINVAL, "base2_window must be 0, 1 or 4");
+  if (t.base2_window != 0 && t.base2_window != 1 && t.base2_window != 2 && t.base2_window != 4)
+    return set_error(ISPRIME_EINVAL, "base2_window must be 0, 1, 2 or 4");
   if (t.rest_test > 1) return set_error(ISPRIME_EINVAL, "rest_test must be 0 or 1");
   if (t.small_max > (1u << 20)) return set_error(ISPRIME_EINVAL, "small_max must be in [0, 2^20]");
   if (t.compact_min > 33) return set_error(ISPRIME_EINVAL, "compact_min must be in [0, 33]");

@@ -277,8 +277,9 @@ __device__ __forceinline__ bool base2_passes_win(uint64_t n, uint64_t* tab, int 
 // n finishes it.  Multiplication by a plain power of two commutes with the
 // Montgomery map, so x may be a Montgomery residue.
 struct Pow2Red {
-  uint32_t sh;  // clz(n) (at most 31)
-  float inv;    // 1 / float(top word of n << sh)
+  uint32_t sh;   // clz(n) (at most 31)
+  float inv;     // 1 / float(top word of n << sh)
+  uint32_t rcp;  // min(floor(inv 2^63), 2^32 - 1): 2^63 / nt within a relative 2^-22
 };
 
 __device__ __forceinline__ Pow2Red pow2red_setup(uint64_t n) {
@@ -286,16 +287,14 @@ __device__ __forceinline__ Pow2Red pow2red_setup(uint64_t n) {
   P.sh = (uint32_t)__clzll((long long)n);
   const uint32_t nt = __funnelshift_l((uint32_t)n, (uint32_t)(n >> 32), P.sh);
   P.inv = __frcp_rn(__uint2float_rn(nt));
+  P.rcp = __float2uint_rz(__fmul_rn(P.inv, 9223372036854775808.0f));  // saturates at 2^32 - 1
   return P;
 }
 
-__device__ __forceinline__ uint64_t mul_pow2_mod(uint64_t x, uint32_t w, uint64_t n,
-                                                 const Pow2Red& P) {
+// x 2^w - q n for a given estimate q of floor(x 2^w / n) that is exact or one
+// less: the remainder is in [0, 2n), and one conditional subtraction ends it.
+__device__ __forceinline__ uint64_t pow2_remainder(uint64_t x, uint32_t w, uint64_t n, uint32_t q) {
   const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
-  const uint32_t xt = __funnelshift_l(x0, x1, P.sh);
-  const float p2w = __uint_as_float((127u + w) << 23);  // 2^w, exact
-  const float v = fmaxf(__fmaf_rn(__fmul_rn(__uint2float_rn(xt), P.inv), p2w, -0.03125f), 0.0f);
-  const uint32_t q = __float2uint_rz(v);
   const uint32_t y0 = x0 << w, y1 = __funnelshift_l(x0, x1, w), y2 = __funnelshift_l(x1, 0u, w);
   uint32_t r0, r1, d0, d1, d2;
   asm("{\n\t.reg .u32 pl, ph, sl, sh, r2;\n\t.reg .u64 p, s;\n\t"
@@ -317,10 +316,33 @@ __device__ __forceinline__ uint64_t mul_pow2_mod(uint64_t x, uint32_t w, uint64_
   return (int32_t)d2 < 0 ? (((uint64_t)r1 << 32) | r0) : (((uint64_t)d1 << 32) | d0);
 }
 
+// x 2^w mod n (x < n, w <= 15, odd n >= 2^32) with the quotient estimated in
+// integers (base2_window 2): e = floor(xt rcp / 2^32) is (x / n) 2^31 within
+// 2^9 + 3 (rcp's relative error 2^-22 gives 2^9, the truncation of x and n to
+// their top words 2, the floor 1), so with the bias 2^10 subtracted (clamped
+// at 0), q = e' >> (31 - w) is floor(x 2^w / n) or one less: before the
+// floor, e' 2^(w - 31) lies at most (2^10 + 2^9 + 3) 2^(w - 31) < 1/32 below
+// x 2^w / n and never above it (w <= 15).
+__device__ __forceinline__ uint64_t mul_pow2_mod_int(uint64_t x, uint32_t w, uint64_t n,
+                                                     const Pow2Red& P) {
+  const uint32_t xt = __funnelshift_l((uint32_t)x, (uint32_t)(x >> 32), P.sh);
+  const uint32_t e = __umulhi(xt, P.rcp);
+  const uint32_t q = (e > 1024u ? e - 1024u : 0u) >> (31u - w);
+  return pow2_remainder(x, w, n, q);
+}
+
+__device__ __forceinline__ uint64_t mul_pow2_mod(uint64_t x, uint32_t w, uint64_t n,
+                                                 const Pow2Red& P) {
+  const uint32_t xt = __funnelshift_l((uint32_t)x, (uint32_t)(x >> 32), P.sh);
+  const float p2w = __uint_as_float((127u + w) << 23);  // 2^w, exact
+  const float v = fmaxf(__fmaf_rn(__fmul_rn(__uint2float_rn(xt), P.inv), p2w, -0.03125f), 0.0f);
+  return pow2_remainder(x, w, n, __float2uint_rz(v));
+}
+
 // Base 2 with 4-bit windows and no table: per nibble w of d four squarings
 // and x 2^w mod n by mul_pow2_mod.  Same warp-uniform schedule as
 // base2_passes_win (leading zero nibbles square the Montgomery 1).  n >= 2^32.
-template <int kImpl>
+template <int kImpl, bool kIntEst = false>
 __device__ __forceinline__ bool base2_passes_shift(uint64_t n, int nib_warp) {
   using Ops = MontOps<kImpl>;
   const Mont64 M = mont64_setup(n);
@@ -329,13 +351,16 @@ __device__ __forceinline__ bool base2_passes_shift(uint64_t n, int nib_warp) {
   const int s = ctz64(d);
   d >>= s;
   uint64_t e = nib_warp >= 16 ? d : d << (64 - 4 * nib_warp);  // left-aligned exponent
-  uint64_t x = mul_pow2_mod(M.one, (uint32_t)(e >> 60), n, P);
+  auto step = [&](uint64_t v, uint32_t w) {
+    return kIntEst ? mul_pow2_mod_int(v, w, n, P) : mul_pow2_mod(v, w, n, P);
+  };
+  uint64_t x = step(M.one, (uint32_t)(e >> 60));
   op_note<kImpl>(2);
   for (int k = 1; k < nib_warp; ++k) {
     e <<= 4;
 #pragma unroll
     for (int r = 0; r < 4; ++r) x = Ops::sqr(x, M);
-    x = mul_pow2_mod(x, (uint32_t)(e >> 60), n, P);
+    x = step(x, (uint32_t)(e >> 60));
     op_note<kImpl>(2);
   }
   return sprp_tail64<kImpl>(M, x, s);

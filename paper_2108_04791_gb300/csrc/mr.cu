@@ -65,7 +65,8 @@ static void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, si
 
 // kMode: the base-2 schedule (the tuning field base2_window): 0 binary with
 // a modular doubling per set bit, 1 4-bit windows with x 2^w mod n by a
-// quotient estimate, 4 4-bit windows with the table 2^w R in shared memory.
+// quotient estimated in single precision, 2 the same with the quotient
+// estimated in integers, 4 4-bit windows with the table 2^w R in shared memory.
 // kRest (modes 1 and 4): 0 compact every survivor into q64b; 1 or 2 a warp
 // with at least compact_min survivors finishes them itself, with the six
 // remaining bases (1) or the strong Lucas test (2), and compacts nothing.
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
     }
   };
   if constexpr (kTd2 > 0) {
-    static_assert(kMode == 1 && kRest == 0 && kIlp == 1, "second trial stage: shift windows only");
+    static_assert((kMode == 1 || kMode == 2) && kRest == 0 && kIlp == 1,
+                  "second trial stage: shift windows only");
     // this warp's stack: 64 values, then 64 positions; after the block's
     // stacks, the block's leftovers (31 per warp at most): values, positions
     const int nwarps = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5);
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
         __syncwarp();  // read before the next task's values overwrite the slots
         held -= 32;
         const int nib = __reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(n));
-        append_passing(base2_passes_shift<kImpl>(n, nib), pos);
+        append_passing(base2_passes_shift<kImpl, kMode == 2>(n, nib), pos);
       }
       if (!have) break;
     }
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
       bool pass = false;
       if (valid) {
         const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
-        pass = base2_passes_shift<kImpl>(n, nib);
+        pass = base2_passes_shift<kImpl, kMode == 2>(n, nib);
       }
       append_passing(pass, pos);
     }
@@ -243,9 +245,9 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
       if (kMode == 4) {
         const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n[0]));
         pass[0] = base2_passes_win<kImpl>(n[0], s_tab + threadIdx.x, (int)blockDim.x, nib);
-      } else if (kMode == 1) {
+      } else if (kMode == 1 || kMode == 2) {
         const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n[0]));
-        pass[0] = base2_passes_shift<kImpl>(n[0], nib);
+        pass[0] = base2_passes_shift<kImpl, kMode == 2>(n[0], nib);
       } else {
         pass[0] = base2_passes<kImpl>(n[0]);
       }
@@ -395,24 +397,24 @@ template <int kImpl, int kMode>
 static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
                               const MrOpts& o, uint32_t mark, int sm_count, cudaStream_t s) {
   if (o.compact_min > 32) {
-    constexpr bool kFast = (kImpl == 6 || kImpl == 9 || kImpl == 16) && kMode == 1;
+    constexpr bool kFast = (kImpl == 6 || kImpl == 9 || kImpl == 16) && (kMode == 1 || kMode == 2);
     if constexpr (kFast) {
       // the second trial stage (formulations 6 and 9 and the counting build,
       // estimated-quotient windows, one survivor per thread)
       if (o.ilp == 1 && o.td2 > 0) {
         switch (o.td2) {
-          case 8: launch_base2_win<kImpl, 1, 0, 1, 8>(q, out, grid, block, o.compact_min, mark,
+          case 8: launch_base2_win<kImpl, kMode, 0, 1, 8>(q, out, grid, block, o.compact_min, mark,
                                                       sm_count, s, o.b2_per_sm, o.pdl); return;
-          case 12: launch_base2_win<kImpl, 1, 0, 1, 12>(q, out, grid, block, o.compact_min, mark,
+          case 12: launch_base2_win<kImpl, kMode, 0, 1, 12>(q, out, grid, block, o.compact_min, mark,
                                                         sm_count, s, o.b2_per_sm, o.pdl); return;
-          case 16: launch_base2_win<kImpl, 1, 0, 1, 16>(q, out, grid, block, o.compact_min, mark,
+          case 16: launch_base2_win<kImpl, kMode, 0, 1, 16>(q, out, grid, block, o.compact_min, mark,
                                                         sm_count, s, o.b2_per_sm, o.pdl); return;
-          default: launch_base2_win<kImpl, 1, 0, 1, 24>(q, out, grid, block, o.compact_min, mark,
+          default: launch_base2_win<kImpl, kMode, 0, 1, 24>(q, out, grid, block, o.compact_min, mark,
                                                         sm_count, s, o.b2_per_sm, o.pdl); return;
         }
       }
-      // two survivors per thread
-      if (o.ilp == 2) {
+      // two survivors per thread (float quotient estimate only)
+      if (o.ilp == 2 && kMode == 1) {
         launch_base2_win<kImpl, 1, 0, 2>(q, out, grid, block, o.compact_min, mark, sm_count, s,
                                          o.b2_per_sm, o.pdl);
         return;
@@ -436,6 +438,8 @@ static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned 
     launch_base2_mode<kImpl, 4>(q, out, grid, block, o, mark, sm_count, s);
   } else if (o.window == 1) {
     launch_base2_mode<kImpl, 1>(q, out, grid, block, o, mark, sm_count, s);
+  } else if (o.window == 2) {
+    launch_base2_mode<kImpl, 2>(q, out, grid, block, o, mark, sm_count, s);
   } else {
     launch_k(mr64_base2_kernel<kImpl, 0, 0>, grid, block, 0, s, o.pdl, q.q64_n, q.q64_idx,
              q.counters, q.q64b, out, 33u, mark, (uint32_t)q.capacity);

@@ -288,7 +288,11 @@ def test_tuning_does_not_change_results():
                    dict(sieve_cutover_log2=0), dict(sieve_cutover_log2=20),
                    dict(sieve_cutover_log2=23, td_primes=0), dict(sieve_cutover_log2=32),
                    dict(inplace_max_log2=20, chunk_log2=24), dict(inplace_max_log2=16, chunk_log2=16),
-                   dict(inplace_max_log2=20, rest_test=1), dict(inplace_max_log2=20, base2_window=0)]:
+                   dict(inplace_max_log2=20, rest_test=1), dict(inplace_max_log2=20, base2_window=0),
+                   dict(inplace_max_log2=0, base2_window=2, rest_test=0),
+                   dict(base2_window=2, compact_min=8), dict(base2_window=2, compact_min=33,
+                                                             base2_ilp=2),
+                   dict(base2_window=2, mont_impl_base2=6), dict(base2_window=2, td2_groups=0)]:
             c.set_tuning(**kw)
             _assert_same(v, _gpu(v, c), want)
 

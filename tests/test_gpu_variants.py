@@ -258,19 +258,24 @@ def td2_data(data):
     return w, oracle.isprime_u64(w)
 
 
-@pytest.mark.parametrize("td2,split,chunk_log2", [(8, 1, 24), (12, 0, 24), (16, 1, 24),
-                                                  (24, 1, 24), (16, 0, 16), (24, 1, 16)])
-def test_second_trial_stage_matches_oracle(td2, split, chunk_log2, td2_data, ctx):
+@pytest.mark.parametrize("td2,split,chunk_log2,window", [(8, 1, 24, 1), (12, 0, 24, 1),
+                                                         (16, 1, 24, 1), (24, 1, 24, 1),
+                                                         (16, 0, 16, 1), (24, 1, 16, 1),
+                                                         (16, 1, 24, 2), (0, 1, 24, 2),
+                                                         (16, 0, 16, 2)])
+def test_second_trial_stage_matches_oracle(td2, split, chunk_log2, window, td2_data, ctx):
     """td2_groups > 0: the base-2 kernel tests its queue against the primes
     59 .. 457 first and stages the survivors per warp; with the s-split on and
-    off, one chunk and many (every chunk's stacks drain at its end)."""
+    off, one chunk and many (every chunk's stacks drain at its end), and with
+    the base-2 window step's quotient estimated in single precision (1) or in
+    integers (2)."""
     v, want = td2_data
     ctx.set_tuning(td2_groups=td2, base2_split=split, chunk_log2=chunk_log2, small_max=0,
-                   td_fold=2, base2_ilp=1, rest_window=3)
+                   td_fold=2, base2_ilp=1, rest_window=3, base2_window=window)
     try:
-        _same(v, _run(ctx, v), want, f"td2={td2} split={split} chunk_log2={chunk_log2}")
+        _same(v, _run(ctx, v), want, f"td2={td2} split={split} chunk_log2={chunk_log2} w={window}")
     finally:
-        ctx.set_tuning(td2_groups=0, base2_split=1, chunk_log2=24)
+        ctx.set_tuning(td2_groups=0, base2_split=1, chunk_log2=24, base2_window=1)
 
 
 def test_second_trial_stage_on_short_queues(td2_data, ctx):
@@ -308,6 +313,7 @@ def test_tuning_rejects_out_of_range_variant_fields(ctx):
     for kw in (dict(td_fold=4), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
                dict(mont_impl=10), dict(mont_impl_base2=10), dict(pdl=2), dict(dual_stream=2),
                dict(td2_groups=4), dict(td2_groups=25), dict(inplace_max_log2=25),
+               dict(base2_window=3),
                dict(rest_window=5), dict(rest_window=2)):
         with pytest.raises(ipg.IsPrimeError):
             ctx.set_tuning(**kw)

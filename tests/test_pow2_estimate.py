@@ -7,7 +7,10 @@ multiply-add that also subtracts 1/32.  Its correctness rests on the estimate
 being floor(x 2^w / n) or one less (the remainder is then in [0, 2n) and one
 conditional subtraction finishes it).  This test emulates each IEEE single
 operation with exact rational arithmetic and correct rounding, and checks that
-claim on adversarial and random inputs.  CPU only; it imports no library code.
+claim on adversarial and random inputs.  The integer form of the estimate
+(base2_window 2: a 32-bit reciprocal rcp = min(floor(inv 2^63), 2^32 - 1) from
+the same single-precision inv, e = floor(xt rcp / 2^32), q = max(e - 2^10, 0)
+>> (31 - w)) is checked the same way.  CPU only; it imports no library code.
 """
 from fractions import Fraction
 import random
@@ -76,3 +79,54 @@ def test_estimate_is_q_or_q_minus_one(w):
             assert est in (q, q - 1), (x, w, n, q, est)
             r = (x << w) - est * n
             assert 0 <= r < 2 * n
+
+
+def _estimate_int(x: int, w: int, n: int) -> int:
+    sh = 64 - n.bit_length()
+    nt = ((n << sh) >> 32) & 0xFFFFFFFF
+    xt = ((x << sh) >> 32) & 0xFFFFFFFF
+    inv = _round_f32(1 / _round_f32(Fraction(nt)))
+    scaled = _round_f32(inv * 2**63)  # exact: a power-of-two scaling
+    rcp = min(scaled.numerator // scaled.denominator, 2**32 - 1)
+    e = (xt * rcp) >> 32
+    return max(e - 1024, 0) >> (31 - w)
+
+
+@pytest.mark.parametrize("w", range(16))
+def test_integer_estimate_is_q_or_q_minus_one(w):
+    rng = random.Random(2000 + w)
+    moduli = _moduli(rng) + [(1 << 63) | 1, (1 << 63) + 2**32 + 1, 2**32 + 2**31 + 1,
+                             (2**32 - 1) << 32 | 1]  # top words at 2^31 (rcp saturates) and 2^32 - 1
+    for n in moduli:
+        xs = {0, 1, n - 1, n - 2, n // 2, (n + 1) // 2}
+        xs.update(rng.randrange(n) for _ in range(4))
+        for _ in range(6):  # x 2^w / n just above and just below an integer k
+            k = rng.randrange(1, 2**w + 1)
+            lo = (k * n) >> w
+            xs.update(v for v in (lo - 1, lo, lo + 1) if 0 <= v < n)
+        for x in xs:
+            q = (x << w) // n
+            est = _estimate_int(x, w, n)
+            assert est in (q, q - 1), (x, w, n, q, est)
+
+
+def test_integer_estimate_needs_its_bias():
+    """Without the bias of 2^10 the integer estimate overshoots floor(x 2^w / n)
+    for some inputs (x 2^w / n just below an integer), so the bias is needed."""
+    rng = random.Random(99)
+    over = 0
+    for n in _moduli(rng):
+        sh = 64 - n.bit_length()
+        nt = ((n << sh) >> 32) & 0xFFFFFFFF
+        inv = _round_f32(1 / _round_f32(Fraction(nt)))
+        scaled = _round_f32(inv * 2**63)
+        rcp = min(scaled.numerator // scaled.denominator, 2**32 - 1)
+        for w in (0, 7, 15):
+            for k in range(1, 40):
+                x = ((k * n) >> w)  # x 2^w / n just below k
+                if x >= n:
+                    continue
+                xt = ((x << sh) >> 32) & 0xFFFFFFFF
+                if ((xt * rcp) >> 32) >> (31 - w) > (x << w) // n:
+                    over += 1
+    assert over > 0
