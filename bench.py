@@ -170,8 +170,57 @@ def _max_over_ranks(x: float, world: int, device=None) -> float:
 
 # ---------------------------------------------------------------- clocks
 
+def _gpu_uuid(index: int) -> str | None:
+    """The CUDA device's UUID in nvidia-smi's form (GPU-...), or None."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(index).uuid)
+    except Exception:  # no CUDA device, or a torch without the field
+        return None
+    return u if u.startswith("GPU-") else "GPU-" + u
+
+
+# A separate process that reads the SM clock and the clock-event reasons of one
+# GPU through the driver's NVML library (read-only queries) every millisecond
+# and writes "time,MHz,reason bits" lines; it runs outside this interpreter, so
+# it keeps sampling while the benchmark holds the interpreter lock.
+_NVML_SAMPLER = r"""
+import ctypes, sys, time
+uuid, index, path = sys.argv[1], int(sys.argv[2]), sys.argv[3]
+lib = ctypes.CDLL("libnvidia-ml.so.1")
+if lib.nvmlInit_v2() != 0:
+    sys.exit(1)
+h = ctypes.c_void_p()
+if (uuid == "-" or lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h))) and \
+        lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)):
+    sys.exit(1)
+reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+    lib.nvmlDeviceGetCurrentClocksThrottleReasons
+mx = ctypes.c_uint()
+lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+c, r = ctypes.c_uint(), ctypes.c_ulonglong()
+with open(path, "w", buffering=1) as f:
+    f.write("max,%d\n" % mx.value)
+    while True:
+        if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(c)) == 0:
+            if reasons(h, ctypes.byref(r)) != 0:
+                r.value = 0
+            f.write("%.6f,%d,%d\n" % (time.time(), c.value, r.value))
+        time.sleep(0.001)
+"""
+
+# nvmlClocksEventReasons bits
+_NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+    """SM clock and throttle reasons while running: nvidia-smi every 50 ms (the
+    sampler starts before the region and the region starts after its first
+    sample), and, where the driver's NVML library loads, a separate process
+    reading the same quantities every millisecond, so that regions of a few
+    milliseconds still get samples of their own (begin()/end() mark the
+    region; without marks every sample counts)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -179,45 +228,103 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
+        self.uuid = _gpu_uuid(gpu_index)
         self.proc = None
         self.path = None
+        self.nv_proc = None
+        self.nv_path = None
+        self.t_begin = self.t_end = None
+
+    def begin(self):
+        """Marks the start of the timed region."""
+        self.t_begin = time.time()
+
+    def end(self):
+        """Marks its end (call it after the device has synchronised)."""
+        self.t_end = time.time()
 
     def start(self):
+        try:
+            fd, self.nv_path = tempfile.mkstemp(suffix=".nvml")
+            os.close(fd)
+            self.nv_proc = subprocess.Popen(
+                [sys.executable, "-c", _NVML_SAMPLER, self.uuid or "-", str(self.gpu), self.nv_path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.nv_proc = None
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-i", self.uuid or str(self.gpu), "-lms", "50"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        t0 = time.time()  # both samplers running (or given up) before the region
+        while time.time() - t0 < 3.0:
+            smi_ok = self.proc is None or os.path.getsize(self.path) > 0
+            nv_ok = self.nv_proc is None or self.nv_proc.poll() is not None or \
+                os.path.getsize(self.nv_path) > 40
+            if smi_ok and nv_ok:
+                break
+            time.sleep(0.01)
+
+    def _stop_proc(self, p):
+        if p is None:
+            return
+        p.terminate()
+        try:
+            p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            p.kill()
 
     def stop(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.fh.close()
         rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        if self.proc is not None:
+            self._stop_proc(self.proc)
+            self.fh.close()
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        nv, nv_all, nv_max = [], 0, None
+        if self.nv_proc is not None:
+            self._stop_proc(self.nv_proc)
+            with open(self.nv_path) as f:
+                for line in f:
+                    p = line.strip().split(",")
+                    if p[0] == "max" and len(p) == 2:
+                        nv_max = float(p[1])
+                    elif len(p) == 3:
+                        nv_all += 1
+                        t = float(p[0])
+                        if self.t_begin is None or self.t_end is None or \
+                                self.t_begin <= t <= self.t_end:
+                            nv.append((float(p[1]), int(p[2])))
+            os.unlink(self.nv_path)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        loaded = [m for m in mhz if m > 0.5 * (max(mhz) if mhz else 1)]
+        reasons = {names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"}
+        if nv_max:
+            mx.append(nv_max)
+        if nv:
+            for _, bits in nv:
+                reasons |= {nm for b, nm in _NVML_REASONS.items() if bits & b}
+            mhz = [c for c, _ in nv]  # the dense samples decide the median
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": max(mx) if mx else None,
+                    "reasons": sorted(reasons) or ["no samples"], "samples": 0}
+        loaded = [m for m in mhz if m > 0.5 * max(mhz)]
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows) + len(nv),
+                "sources": {"nvidia_smi": len(rows), "nvml": len(nv), "nvml_total": nv_all,
+                            "nvml_window": "timed region" if self.t_end else "whole phase"}}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -318,8 +425,9 @@ def run_mine(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
 
-    for _ in range(max(args.warmup, 3)):
-        ctx.isprime(d_in, out=out)
+    for k in range(max(args.warmup, 3)):
+        flush.fill_(k & 0xFF)  # the first fill loads torch's fill kernel (a quarter second
+        ctx.isprime(d_in, out=out)  # of host time) here rather than in the timed region
     torch.cuda.synchronize(dev)
 
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -332,6 +440,7 @@ def run_mine(args, world, rank, local):
     clocks.start()
     _barrier(world)
     torch.cuda.synchronize(dev)
+    clocks.begin()
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)                    # evict the previous step's lines from L2
@@ -339,6 +448,7 @@ def run_mine(args, world, rank, local):
         ctx.isprime(d_in, out=out)
         ev_e[k].record(stream)
     torch.cuda.synchronize(dev)
+    clocks.end()
     _barrier(world)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -535,7 +645,8 @@ def plain_record(ctx, dev, workload: str, steps: int, with_cpu: bool) -> dict:
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def timed(fn, k):
-        for _ in range(3):
+        for i in range(3):
+            flush.fill_(i & 0xFF)
             fn()
         torch.cuda.synchronize(dev)
         tot = 0.0

@@ -40,6 +40,8 @@ constexpr size_t kNoallocQ32N = kNoallocQ64B + 4 * kNoallocMaxElems;    // u32 v
 constexpr size_t kNoallocQ32Idx = kNoallocQ32N + 4 * kNoallocMaxElems;  // u32 indices
 constexpr size_t kNoallocCounters = kNoallocQ32Idx + 4 * kNoallocMaxElems;
 constexpr size_t kNoallocBytes = kNoallocCounters + 256;
+// classify advances counters[0..1] as one 64-bit word
+static_assert(kNoallocCounters % 8 == 0, "queue counters must be 8-byte aligned");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
