@@ -75,7 +75,7 @@ static isprime_tuning default_tuning() {
   isprime_tuning t{};
   t.classify_block = 256;
   t.mr_block = 256;
-  t.blocks_per_sm = 16;
+  t.blocks_per_sm = 32;  // classify 0.088 -> 0.086 ms on plain_large against 16
   t.td_primes = 15;  // 3..53
   t.chunk_log2 = 24;
   t.mont_impl = 9;       // formulation 6 with its correction on the multiply pipe:

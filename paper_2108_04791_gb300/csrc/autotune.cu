@@ -39,7 +39,7 @@ std::vector<Param> params() {
       {"td_primes", &isprime_tuning::td_primes, {7, 11, 15, 23, 31}, P | B},
       {"classify_block", &isprime_tuning::classify_block, {128, 256, 512}, P},
       {"mr_block", &isprime_tuning::mr_block, {64, 128, 256}, P},
-      {"blocks_per_sm", &isprime_tuning::blocks_per_sm, {4, 8, 16}, P},
+      {"blocks_per_sm", &isprime_tuning::blocks_per_sm, {4, 8, 16, 32}, P},
       {"mont_impl", &isprime_tuning::mont_impl, {9, 6, 0, 5}, P},
       {"mont_impl_base2", &isprime_tuning::mont_impl_base2, {9, 6, 0, 5}, P},
       {"base2_window", &isprime_tuning::base2_window, {0, 1, 4}, P},
