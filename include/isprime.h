@@ -151,6 +151,9 @@ typedef struct {
                               compact_min were 1 (base2_window 1 or 4): the base-2 kernel's
                               warps finish their own passers and the six-base kernel is not
                               launched; 0..24, 0 = never */
+  uint32_t serve_long_log2;  /* a server created on the context closes a batch of long requests
+                              once it holds 2^serve_long_log2 values (its first request may be
+                              larger); 16..28, default 24 */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -102,6 +102,7 @@ static isprime_tuning default_tuning() {
   t.td2_groups = 16;  // second trial stage, primes 59 .. 311: base 2 -12%, step -4.8% on plain_large
   t.dual_stream = 0;
   t.inplace_max_log2 = 0;
+  t.serve_long_log2 = 24;
   t.host_chunk_log2 = 22;  // host path: 1.089 ms per 2^24 values against 1.26 (23) and 1.15 (21)
   return t;
 }
@@ -134,6 +135,8 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.pdl > 1) return set_error(ISPRIME_EINVAL, "pdl must be 0 or 1");
   if (t.dual_stream > 1) return set_error(ISPRIME_EINVAL, "dual_stream must be 0 or 1");
   if (t.inplace_max_log2 > 24) return set_error(ISPRIME_EINVAL, "inplace_max_log2 must be <= 24");
+  if (t.serve_long_log2 < 16 || t.serve_long_log2 > 28)
+    return set_error(ISPRIME_EINVAL, "serve_long_log2 must be in [16, 28]");
   if (t.host_chunk_log2 < 16 || t.host_chunk_log2 > 24)
     return set_error(ISPRIME_EINVAL, "host_chunk_log2 must be in [16, 24]");
   if (t.td2_groups != 0 && t.td2_groups != 8 && t.td2_groups != 12 && t.td2_groups != 16 &&

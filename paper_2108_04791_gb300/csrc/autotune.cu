@@ -78,7 +78,8 @@ const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_prim
                          "batch_blocks_per_sm", "base2_window", "rest_test", "small_max",
                          "compact_min", "sieve_cutover_log2", "serve_short_max", "td_fold",
                          "base2_split", "base2_ilp", "rest_window", "window_ratio16",
-                         "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream", "host_chunk_log2", "inplace_max_log2"};
+                         "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream", "host_chunk_log2", "inplace_max_log2",
+                         "serve_long_log2"};
 FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
@@ -90,8 +91,8 @@ FieldPtr kFieldPtr[] = {
     &isprime_tuning::base2_ilp, &isprime_tuning::rest_window, &isprime_tuning::window_ratio16,
     &isprime_tuning::base2_blocks_per_sm, &isprime_tuning::pdl, &isprime_tuning::td2_groups,
     &isprime_tuning::dual_stream, &isprime_tuning::host_chunk_log2,
-    &isprime_tuning::inplace_max_log2};
-constexpr int kNumFields = 27;
+    &isprime_tuning::inplace_max_log2, &isprime_tuning::serve_long_log2};
+constexpr int kNumFields = 28;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

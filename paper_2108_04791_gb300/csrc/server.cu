@@ -119,6 +119,7 @@ struct isprime_server {
   uint64_t next_ticket = 1;
   std::thread dispatcher, completer;
   size_t small_cut = 0;  // requests of at most this many elements form short batches
+  size_t long_cut = (size_t)1 << 24;  // a long batch grows to at most this many elements
   int fatal = ISPRIME_OK;
   std::string fatal_msg;
   // statistics
@@ -133,9 +134,9 @@ namespace ip {
 namespace {
 
 constexpr size_t kMaxBatchRequests = 4096;
-// A long batch stops growing at this many elements (after its first request),
-// so that batches in flight stay short enough to overlap and rotate.
-constexpr size_t kMaxLongBatchElems = (size_t)1 << 24;
+// A long batch stops growing at 2^serve_long_log2 elements (after its first
+// request; the context's tuning), so that batches in flight stay short enough
+// to overlap and rotate.
 
 size_t request_bytes(size_t n) { return ((8 * n + 255) & ~(size_t)255) + ((n + 255) & ~(size_t)255); }
 
@@ -214,7 +215,7 @@ void dispatcher_loop(isprime_server* S) {
     for (RequestP& r : S->pending) {
       const bool take = !full && (is_short(S, *r) ? 1 : 0) == cls;
       if (take && cls == 1 && elems + r->n > S->small_cut) full = true;
-      if (take && cls == 0 && !batch.empty() && elems + r->n > kMaxLongBatchElems) full = true;
+      if (take && cls == 0 && !batch.empty() && elems + r->n > S->long_cut) full = true;
       size_t off = 0;
       if (take && !full && batch.size() < kMaxBatchRequests &&
           (r->direct || S->arena->alloc(r->bytes, &off))) {
@@ -354,6 +355,7 @@ int isprime_server_create(isprime_ctx* ctx, size_t mem_budget_bytes, int n_slots
   {
     std::lock_guard<std::mutex> lock(ctx->mu);
     S->small_cut = ctx->tune.serve_short_max;
+    S->long_cut = (size_t)1 << ctx->tune.serve_long_log2;
   }
   int prev = 0;
   IP_CUDA(cudaGetDevice(&prev));

@@ -26,10 +26,14 @@ def _requests(n_req, max_size, seed):
     return [np.ascontiguousarray(vals[offs[i]:offs[i + 1]]) for i in range(n_req)]
 
 
-@pytest.mark.parametrize("n_slots,small_max", [(3, None), (1, None), (2, 1 << 12), (3, 0)])
-def test_mixed_concurrent_requests_equal_results_alone(n_slots, small_max):
+@pytest.mark.parametrize("n_slots,small_max,long_log2", [(3, None, 24), (1, None, 24),
+                                                        (2, 1 << 12, 24), (3, 0, 24),
+                                                        (2, 1 << 10, 16), (3, 0, 16)])
+def test_mixed_concurrent_requests_equal_results_alone(n_slots, small_max, long_log2):
     """Short and long requests from four client threads; short ones (at most
-    serve_short_max elements) are batched apart and keep the last slot."""
+    serve_short_max elements) are batched apart and keep the last slot; with
+    serve_long_log2 16 a long batch closes at 2^16 values, so many small long
+    batches rotate through the slots."""
     reqs = _requests(240, 1 << 15, seed=91) + [np.zeros(0, np.uint64),
                                                np.array([2**64 - 59, 1, 2], np.uint64)]
     ctx = ipg.Context.default(0)
@@ -39,7 +43,7 @@ def test_mixed_concurrent_requests_equal_results_alone(n_slots, small_max):
         alone.append(ctx.isprime(t).cpu().numpy() if r.size else np.zeros(0, np.uint8))
     sctx = ipg.Context(0) if small_max is not None else ctx
     if small_max is not None:
-        sctx.set_tuning(serve_short_max=small_max)
+        sctx.set_tuning(serve_short_max=small_max, serve_long_log2=long_log2)
     with ipg.Server(sctx, mem_budget_bytes=64 << 20, n_slots=n_slots) as srv:
         results = [None] * len(reqs)
 

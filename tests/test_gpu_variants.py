@@ -313,7 +313,7 @@ def test_tuning_rejects_out_of_range_variant_fields(ctx):
     for kw in (dict(td_fold=4), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
                dict(mont_impl=10), dict(mont_impl_base2=10), dict(pdl=2), dict(dual_stream=2),
                dict(td2_groups=4), dict(td2_groups=25), dict(inplace_max_log2=25),
-               dict(base2_window=3),
+               dict(base2_window=3), dict(serve_long_log2=15), dict(serve_long_log2=29),
                dict(rest_window=5), dict(rest_window=2)):
         with pytest.raises(ipg.IsPrimeError):
             ctx.set_tuning(**kw)
