@@ -185,6 +185,8 @@ int isprime_ctx_destroy(isprime_ctx *ctx);
 int isprime_default_ctx(int device, isprime_ctx **out);
 
 int isprime_ctx_get_tuning(const isprime_ctx *ctx, isprime_tuning *out);
+/* The parameters a new context starts with (no device is touched). */
+int isprime_tuning_defaults(isprime_tuning *out);
 /* Validates and installs new parameters (ISPRIME_EINVAL if out of range). */
 int isprime_ctx_set_tuning(isprime_ctx *ctx, const isprime_tuning *t);
 int isprime_ctx_stats(const isprime_ctx *ctx, isprime_stats *out);

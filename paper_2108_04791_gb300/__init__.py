@@ -117,6 +117,7 @@ def lib():
                 "isprime_ctx_destroy": ([vp], i32),
                 "isprime_default_ctx": ([i32, ctypes.POINTER(vp)], i32),
                 "isprime_ctx_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
+                "isprime_tuning_defaults": ([ctypes.POINTER(Tuning)], i32),
                 "isprime_ctx_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
                 "isprime_ctx_stats": ([vp, ctypes.POINTER(_Stats)], i32),
                 "isprime_u64": ([vp, vp, sz, vp], i32),
@@ -465,6 +466,13 @@ def isprime(t, out=None, stream=None, invalid=None):
 
 def isprime_host(values, device: int = 0) -> np.ndarray:
     return _default_ctx(device).isprime_host(values)
+
+
+def default_tuning() -> dict:
+    """The tuning a new context starts with (needs no GPU)."""
+    t = Tuning()
+    _check(lib().isprime_tuning_defaults(ctypes.byref(t)))
+    return t.as_dict()
 
 
 def isprime_scalar(value: int, device: int = 0) -> bool:

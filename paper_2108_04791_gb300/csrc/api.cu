@@ -479,6 +479,12 @@ int isprime_default_ctx(int device, isprime_ctx** out) {
   return default_ctx(device, out);
 }
 
+int isprime_tuning_defaults(isprime_tuning* out) {
+  if (!out) return set_error(ISPRIME_EINVAL, "NULL argument");
+  *out = default_tuning();
+  return ISPRIME_OK;
+}
+
 int isprime_ctx_get_tuning(const isprime_ctx* ctx, isprime_tuning* out) {
   if (!ctx || !out) return set_error(ISPRIME_EINVAL, "NULL argument");
   *out = ctx->tune;

@@ -56,6 +56,17 @@ def test_plain_large_two_stage_trial_work():
     assert work == bench.WORK_PLAIN_LARGE and stage2 == 0
 
 
+def test_ncu_traffic_is_recorded_for_the_default_tuning():
+    """bench.py reports the ncu DRAM bytes only for the build and tuning the
+    capture was taken with; the recorded tuning must be the library's
+    defaults (the bench runs them), else every line would carry null.  (The
+    source hash is compared at run time: a kernel changed after the capture
+    gives null until the next capture.)"""
+    import paper_2108_04791_gb300 as ipg
+    assert bench.NCU_TRAFFIC["tuning"] == ipg.default_tuning()
+    assert len(bench.NCU_TRAFFIC["sources"]) == 16
+
+
 def test_batched_and_served_work_on_a_sample():
     """The stored full-workload figures (written by make_work_counts.py over
     every element) agree with a recount of 2^18 elements taken in 16 blocks
