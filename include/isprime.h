@@ -154,6 +154,9 @@ typedef struct {
   uint32_t serve_long_log2;  /* a server created on the context closes a batch of long requests
                               once it holds 2^serve_long_log2 values (its first request may be
                               larger); 16..28, default 24 */
+  uint32_t rest_ilp;       /* six-base kernel on long queues with rest_window 3: the bases one
+                              at a time (1) or in pairs, two exponentiations interleaved per
+                              thread (2, default) */
 } isprime_tuning;
 
 /* Per-context counters since creation (or the last reset). */

@@ -52,7 +52,8 @@ class Tuning(ctypes.Structure):
                 ("window_ratio16", ctypes.c_uint32), ("base2_blocks_per_sm", ctypes.c_uint32),
                 ("pdl", ctypes.c_uint32), ("td2_groups", ctypes.c_uint32),
                 ("dual_stream", ctypes.c_uint32), ("host_chunk_log2", ctypes.c_uint32),
-                ("inplace_max_log2", ctypes.c_uint32), ("serve_long_log2", ctypes.c_uint32)]
+                ("inplace_max_log2", ctypes.c_uint32), ("serve_long_log2", ctypes.c_uint32),
+                ("rest_ilp", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -103,6 +103,7 @@ static isprime_tuning default_tuning() {
   t.dual_stream = 0;
   t.inplace_max_log2 = 0;
   t.serve_long_log2 = 24;
+  t.rest_ilp = 2;  // six bases in pairs: six-base kernel -1.2% on plain_large
   t.host_chunk_log2 = 22;  // host path: 1.089 ms per 2^24 values against 1.26 (23) and 1.15 (21)
   return t;
 }
@@ -135,6 +136,7 @@ static int check_tuning(const isprime_tuning& t) {
   if (t.pdl > 1) return set_error(ISPRIME_EINVAL, "pdl must be 0 or 1");
   if (t.dual_stream > 1) return set_error(ISPRIME_EINVAL, "dual_stream must be 0 or 1");
   if (t.inplace_max_log2 > 24) return set_error(ISPRIME_EINVAL, "inplace_max_log2 must be <= 24");
+  if (t.rest_ilp < 1 || t.rest_ilp > 2) return set_error(ISPRIME_EINVAL, "rest_ilp must be 1 or 2");
   if (t.serve_long_log2 < 16 || t.serve_long_log2 > 28)
     return set_error(ISPRIME_EINVAL, "serve_long_log2 must be in [16, 28]");
   if (t.host_chunk_log2 < 16 || t.host_chunk_log2 > 24)

@@ -48,6 +48,7 @@ std::vector<Param> params() {
       {"base2_split", &isprime_tuning::base2_split, {0, 1}, P},
       {"base2_ilp", &isprime_tuning::base2_ilp, {1, 2}, P},
       {"rest_window", &isprime_tuning::rest_window, {4, 3}, P},
+      {"rest_ilp", &isprime_tuning::rest_ilp, {1, 2}, P},
       {"base2_blocks_per_sm", &isprime_tuning::base2_blocks_per_sm, {4, 0, 6, 5}, P},
       {"pdl", &isprime_tuning::pdl, {0, 1}, P},
       {"td2_groups", &isprime_tuning::td2_groups, {0, 8, 12, 16, 24}, P},
@@ -79,7 +80,7 @@ const char* kFields[] = {"classify_block", "mr_block", "blocks_per_sm", "td_prim
                          "compact_min", "sieve_cutover_log2", "serve_short_max", "td_fold",
                          "base2_split", "base2_ilp", "rest_window", "window_ratio16",
                          "base2_blocks_per_sm", "pdl", "td2_groups", "dual_stream", "host_chunk_log2", "inplace_max_log2",
-                         "serve_long_log2"};
+                         "serve_long_log2", "rest_ilp"};
 FieldPtr kFieldPtr[] = {
     &isprime_tuning::classify_block, &isprime_tuning::mr_block, &isprime_tuning::blocks_per_sm,
     &isprime_tuning::td_primes, &isprime_tuning::chunk_log2, &isprime_tuning::mont_impl,
@@ -91,8 +92,9 @@ FieldPtr kFieldPtr[] = {
     &isprime_tuning::base2_ilp, &isprime_tuning::rest_window, &isprime_tuning::window_ratio16,
     &isprime_tuning::base2_blocks_per_sm, &isprime_tuning::pdl, &isprime_tuning::td2_groups,
     &isprime_tuning::dual_stream, &isprime_tuning::host_chunk_log2,
-    &isprime_tuning::inplace_max_log2, &isprime_tuning::serve_long_log2};
-constexpr int kNumFields = 28;
+    &isprime_tuning::inplace_max_log2, &isprime_tuning::serve_long_log2,
+    &isprime_tuning::rest_ilp};
+constexpr int kNumFields = 29;
 
 std::string format_tuning(const isprime_tuning& t) {
   std::string s;

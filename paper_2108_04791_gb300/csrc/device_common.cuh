@@ -181,6 +181,47 @@ __device__ __forceinline__ uint64_t mont_pow_win(const Mont64& M, uint64_t aR, u
   return x;
 }
 
+// a^d and b^d mod n at once (two bases, one exponent): the schedule of
+// mont_pow_win run on both in one loop, the second table at tb, so that the
+// products of one chain overlap the carry chains of the other.  nib_warp is
+// the warp's largest digit count (>= this lane's).
+template <int kImpl, int kW>
+__device__ __forceinline__ void mont_pow_win2(const Mont64& M, uint64_t aR, uint64_t bR, uint64_t d,
+                                              uint64_t* ta, uint64_t* tb, int ld, int nib_warp,
+                                              uint64_t* xa, uint64_t* xb) {
+  using Ops = MontOps<kImpl>;
+  constexpr int kT = 1 << kW;
+  ta[0] = M.one;
+  tb[0] = M.one;
+  ta[ld] = aR;
+  tb[ld] = bR;
+  uint64_t s = Ops::sqr(aR, M), t = Ops::sqr(bR, M);
+  ta[2 * ld] = s;
+  tb[2 * ld] = t;
+#pragma unroll
+  for (int j = 3; j < kT; ++j) {
+    s = Ops::mul(s, aR, M);
+    t = Ops::mul(t, bR, M);
+    ta[j * ld] = s;
+    tb[j * ld] = t;
+  }
+  const int nib = nib_warp;
+  const int top = (int)((d >> (kW * (nib - 1))) & (kT - 1));
+  uint64_t x = ta[top * ld], y = tb[top * ld];
+  for (int k = nib - 2; k >= 0; --k) {
+#pragma unroll
+    for (int r = 0; r < kW; ++r) {
+      x = Ops::sqr(x, M);
+      y = Ops::sqr(y, M);
+    }
+    const int dg = (int)((d >> (kW * k)) & (kT - 1));
+    x = Ops::mul(x, ta[dg * ld], M);
+    y = Ops::mul(y, tb[dg * ld], M);
+  }
+  *xa = x;
+  *xb = y;
+}
+
 // Digits of kW bits in d >= 1.
 template <int kW>
 __device__ __forceinline__ int win_digits(uint64_t d) {
@@ -210,6 +251,33 @@ __device__ __forceinline__ bool rest64_is_prime_warp(uint64_t n, bool valid, uin
   }
   return valid && prime;
 }
+
+// rest64_is_prime_warp with the six bases in pairs (mont_pow_win2; tab2 is
+// the second table, same stride).
+template <int kImpl, int kW>
+__device__ __forceinline__ bool rest64_is_prime_warp2(uint64_t n, bool valid, uint64_t* tab,
+                                                      uint64_t* tab2, int ld) {
+  const Mont64 M = mont64_setup(n);
+  const uint64_t r2 = mont64_r2<kImpl>(M);
+  uint64_t d = n - 1;
+  const int s = ctz64(d);
+  d >>= s;
+  const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)win_digits<kW>(d));
+  bool prime = true;
+#pragma unroll 1
+  for (int b = 1; b < kNumBases64; b += 2) {
+    const uint64_t aR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b], r2, M);
+    const uint64_t bR = MontOps<kImpl>::mul((uint64_t)c_bases.b64[b + 1], r2, M);
+    uint64_t x, y;
+    mont_pow_win2<kImpl, kW>(M, aR, bR, d, tab, tab2, ld, nib, &x, &y);
+    prime = prime && sprp_tail64<kImpl>(M, x, s);
+    __syncwarp();
+    prime = prime && sprp_tail64<kImpl>(M, y, s);
+    __syncwarp();
+  }
+  return valid && prime;
+}
+static_assert((kNumBases64 - 1) % 2 == 0, "the six bases after base 2 pair up");
 
 // The bases of Eq. 4 with indices first .. first + cnt - 1 (first >= 1) for
 // an odd n >= 2^32 that passed base 2: true when all pass.  Warp-synchronous

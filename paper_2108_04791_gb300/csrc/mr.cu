@@ -274,7 +274,10 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
 // kLucas: the strong Lucas test (Baillie-PSW with the base-2 stage) instead
 // of the six remaining Miller-Rabin bases.  kW: window bits of the six
 // exponentiations (3 or 4; the shared table holds 2^kW values per thread).
-template <int kImpl, bool kLucas, bool kSpread, int kW = kWin>
+// kPair (one survivor per thread, kSpread false): the bases in pairs, two
+// exponentiations interleaved per thread (rest64_is_prime_warp2), the second
+// table after the first (2^kW more words per thread).
+template <int kImpl, bool kLucas, bool kSpread, int kW = kWin, bool kPair = false>
 __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restrict__ qn,
                                                         const uint32_t* __restrict__ qidx,
                                                         const uint32_t* __restrict__ q64b,
@@ -326,8 +329,13 @@ __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restri
     uint32_t j = valid ? q64b[i] : 0u;
     if (!IP_CHECK(j < cap, kChkRestRead)) j = 0;
     const uint64_t n = valid ? qn[j] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 for idle lanes
-    const bool prime =
-        kLucas ? lucas_warp<kImpl>(n, valid) : rest64_is_prime_warp<kImpl, kW>(n, valid, tab, ld);
+    bool prime;
+    if constexpr (kLucas)
+      prime = lucas_warp<kImpl>(n, valid);
+    else if constexpr (kPair)
+      prime = rest64_is_prime_warp2<kImpl, kW>(n, valid, tab, tab + (ld << kW), ld);
+    else
+      prime = rest64_is_prime_warp<kImpl, kW>(n, valid, tab, ld);
     if (!IP_CHECK(!valid || qidx[j] < cap, kChkRestOut)) {
     } else if (kSpread) {
       if (valid && !prime) out[qidx[j]] = 0;
@@ -370,6 +378,7 @@ struct MrOpts {
   int b2_per_sm = 0;  // base2_blocks_per_sm (0: as many as fit)
   bool pdl = false;   // launch with programmatic stream serialization
   int td2 = 0;        // td2_groups: second trial stage in the base-2 kernel
+  int rest_ilp = 1;   // six-base kernel: bases one at a time (1) or in pairs (2)
 };
 
 // Modes 1 and 4 run one wave of resident blocks (the kernel balances the
@@ -450,7 +459,8 @@ static void launch_base2(const Queues& q, uint8_t* out, unsigned grid, unsigned 
 // over the threads whenever the queue is at most a sixth of its threads.
 template <int kImpl, int kW>
 static void launch_rest_w(const Queues& q, uint8_t* out, unsigned grid, unsigned block,
-                          unsigned spread_grid, int sm_count, cudaStream_t s, bool pdl) {
+                          unsigned spread_grid, int sm_count, cudaStream_t s, bool pdl,
+                          bool pair = false) {
   const size_t smem = ((size_t)1 << kW) * block * sizeof(uint64_t);
   if (spread_grid) {
     // at most the blocks that can be resident: more would only queue up (and
@@ -460,6 +470,9 @@ static void launch_rest_w(const Queues& q, uint8_t* out, unsigned grid, unsigned
     const unsigned g = resident_grid(fn, block, smem, sm_count, spread_grid);
     launch_k(mr64_rest_kernel<kImpl, false, true, kW>, g, block, smem, s, pdl, q.q64_n, q.q64_idx,
              q.q64b, q.counters, out, spread_threads, (uint32_t)q.capacity);
+  } else if (pair) {
+    launch_k(mr64_rest_kernel<kImpl, false, false, kW, true>, grid, block, 2 * smem, s, pdl,
+             q.q64_n, q.q64_idx, q.q64b, q.counters, out, 0u, (uint32_t)q.capacity);
   } else {
     launch_k(mr64_rest_kernel<kImpl, false, false, kW>, grid, block, smem, s, pdl, q.q64_n,
              q.q64_idx, q.q64b, q.counters, out, 0u, (uint32_t)q.capacity);
@@ -473,7 +486,7 @@ static void launch_rest(const Queues& q, uint8_t* out, unsigned grid, unsigned b
     launch_k(mr64_rest_kernel<kImpl, true, false>, grid, block, 0, s, o.pdl, q.q64_n, q.q64_idx,
              q.q64b, q.counters, out, 0u, (uint32_t)q.capacity);
   } else if ((kImpl == 6 || kImpl == 9 || kImpl == 17) && o.rest_win == 3) {
-    launch_rest_w<kImpl, 3>(q, out, grid, block, spread_grid, sm_count, s, o.pdl);
+    launch_rest_w<kImpl, 3>(q, out, grid, block, spread_grid, sm_count, s, o.pdl, o.rest_ilp == 2);
   } else {
     launch_rest_w<kImpl, kWin>(q, out, grid, block, spread_grid, sm_count, s, o.pdl);
   }
@@ -559,6 +572,7 @@ int launch_mr(isprime_ctx* ctx, const Queues& q, uint8_t* out, uint64_t len, cud
   o.b2_per_sm = (int)ctx->tune.base2_blocks_per_sm;
   o.pdl = ctx->tune.pdl != 0 && !ctx->timing;  // timing events between launches would serialise them
   o.td2 = (int)ctx->tune.td2_groups;
+  o.rest_ilp = (int)ctx->tune.rest_ilp;
   // Short chunks: every warp of the base-2 kernel finishes its own passers
   // and the six-base kernel is not launched (one launch less per call, where
   // launches, not arithmetic, set the time).

@@ -309,11 +309,31 @@ def test_second_trial_stage_host_and_double_paths(fold, td2_data, ctx):
         ctx.set_tuning(td2_groups=0, chunk_log2=24, td_fold=2)
 
 
+@pytest.mark.parametrize("split", [1, 0])
+def test_paired_bases_match_oracle(split, td2_data, ctx):
+    """rest_ilp = 2 (default): the six-base kernel (its long-queue form, chunks
+    above 2^22 values) runs the bases in pairs, two exponentiations per
+    thread, and rest_ilp = 1 one base at a time; the
+    inputs are the variant set plus plain_large values, 2^22 + 4097 in all,
+    so the queue is long and ragged."""
+    v0, _ = td2_data
+    n = (1 << 22) + 4097
+    v = np.concatenate([v0, plain_large(n - v0.size, seed=77)])
+    want = oracle.isprime_u64(v)
+    for ilp in (2, 1):
+        ctx.set_tuning(rest_ilp=ilp, rest_window=3, base2_split=split, small_max=0, chunk_log2=24)
+        try:
+            _same(v, _run(ctx, v), want, f"rest_ilp={ilp} split={split}")
+        finally:
+            ctx.set_tuning(rest_ilp=2, base2_split=1)
+
+
 def test_tuning_rejects_out_of_range_variant_fields(ctx):
     for kw in (dict(td_fold=4), dict(base2_split=2), dict(base2_ilp=3), dict(base2_ilp=0),
                dict(mont_impl=10), dict(mont_impl_base2=10), dict(pdl=2), dict(dual_stream=2),
                dict(td2_groups=4), dict(td2_groups=25), dict(inplace_max_log2=25),
                dict(base2_window=3), dict(serve_long_log2=15), dict(serve_long_log2=29),
+               dict(rest_ilp=0), dict(rest_ilp=3),
                dict(rest_window=5), dict(rest_window=2)):
         with pytest.raises(ipg.IsPrimeError):
             ctx.set_tuning(**kw)
