@@ -274,9 +274,10 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
 // kLucas: the strong Lucas test (Baillie-PSW with the base-2 stage) instead
 // of the six remaining Miller-Rabin bases.  kW: window bits of the six
 // exponentiations (3 or 4; the shared table holds 2^kW values per thread).
-// kPair (one survivor per thread, kSpread false): the bases in pairs, two
-// exponentiations interleaved per thread (rest64_is_prime_warp2), the second
-// table after the first (2^kW more words per thread).
+// kPair: one survivor per thread (kSpread: when the queue is too long to
+// spread) takes the bases in pairs, two exponentiations interleaved per
+// thread (rest64_is_prime_warp2), the second table after the first (2^kW
+// more words per thread).
 template <int kImpl, bool kLucas, bool kSpread, int kW = kWin, bool kPair = false>
 __global__ void __launch_bounds__(256) mr64_rest_kernel(const uint64_t* __restrict__ qn,
                                                         const uint32_t* __restrict__ qidx,
@@ -466,6 +467,14 @@ static void launch_rest_w(const Queues& q, uint8_t* out, unsigned grid, unsigned
     // at most the blocks that can be resident: more would only queue up (and
     // cost their launch when the queue is empty)
     const uint32_t spread_threads = spread_grid * block;
+    if (pair) {  // a queue too long to spread takes the bases in pairs
+      auto kern = mr64_rest_kernel<kImpl, false, true, kW, true>;
+      const unsigned g =
+          resident_grid(reinterpret_cast<const void*>(kern), block, 2 * smem, sm_count, spread_grid);
+      launch_k(kern, g, block, 2 * smem, s, pdl, q.q64_n, q.q64_idx, q.q64b, q.counters, out,
+               spread_threads, (uint32_t)q.capacity);
+      return;
+    }
     const void* fn = reinterpret_cast<const void*>(&mr64_rest_kernel<kImpl, false, true, kW>);
     const unsigned g = resident_grid(fn, block, smem, sm_count, spread_grid);
     launch_k(mr64_rest_kernel<kImpl, false, true, kW>, g, block, smem, s, pdl, q.q64_n, q.q64_idx,
