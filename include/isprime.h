@@ -85,7 +85,8 @@ typedef struct {
                               reciprocal of n); 4 4-bit windows, x 2^w R mod n by a Montgomery
                               product with a table of 2^w R in shared memory.  Modes 1 and 2
                               take the second trial stage, finishing in place and (mode 1) two
-                              survivors per thread */
+                              survivors per thread (with the second trial stage for td2_groups
+                              16 and 24) */
   uint32_t rest_test;      /* after base 2: 0 the six remaining bases of Eq. 4 (default), 1 the
                               strong Lucas test with Selfridge's parameters (Baillie-PSW).
                               Both are exact below 2^64; 1 rests on the published search

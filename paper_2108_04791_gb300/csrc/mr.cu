@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
                                                          uint32_t compact_min, uint32_t mark,
                                                          uint32_t cap) {
   extern __shared__ uint64_t s_tab[];  // mode 4 or kRest 1: 16 x blockDim
-  constexpr uint32_t kTask = 32u * kIlp;
+  constexpr uint32_t kTask = kTd2 > 0 ? 32u : 32u * kIlp;  // queue positions per task
   wait_for_producer();
   const uint32_t count_f = *(volatile uint32_t*)&counters[0];
   const uint32_t count_b = *(volatile uint32_t*)&counters[1];
@@ -130,18 +130,46 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
     }
   };
   if constexpr (kTd2 > 0) {
-    static_assert((kMode == 1 || kMode == 2) && kRest == 0 && kIlp == 1,
-                  "second trial stage: shift windows only");
-    // this warp's stack: 64 values, then 64 positions; after the block's
-    // stacks, the block's leftovers (31 per warp at most): values, positions
+    static_assert((kMode == 1 || kMode == 2) && kRest == 0 && (kIlp == 1 || kMode == 1),
+                  "second trial stage: shift windows only (two per thread: the float estimate)");
+    // A batch is kB = 32 kIlp values (kIlp per lane).  This warp's stack holds
+    // fewer than kB plus one task: kStack values, then kStack positions; after
+    // the block's stacks, the block's leftovers (fewer than kB per warp).
+    constexpr int kB = 32 * kIlp, kStack = kB + 32;
     const int nwarps = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5);
-    uint64_t* st_n = s_tab + warp * 96;
-    uint32_t* st_pos = reinterpret_cast<uint32_t*>(st_n + 64);
-    uint64_t* left_n = s_tab + nwarps * 96;
-    uint32_t* left_pos = reinterpret_cast<uint32_t*>(left_n + 32 * nwarps);
+    uint64_t* st_n = s_tab + warp * (kStack + kStack / 2);
+    uint32_t* st_pos = reinterpret_cast<uint32_t*>(st_n + kStack);
+    uint64_t* left_n = s_tab + nwarps * (kStack + kStack / 2);
+    uint32_t* left_pos = reinterpret_cast<uint32_t*>(left_n + kB * nwarps);
     __shared__ uint32_t s_left;
     if (threadIdx.x == 0) s_left = 0;
     __syncthreads();
+    // base 2 on kB values of stack slots s0 + lane + 32 u (u < kIlp); lanes
+    // past `cnt` values test a prime and report nothing
+    auto run_batch = [&](const uint64_t* sn, const uint32_t* sp, int s0, int cnt) {
+      uint64_t n[kIlp];
+      uint32_t pos[kIlp];
+      bool ok[kIlp];
+#pragma unroll
+      for (int u = 0; u < kIlp; ++u) {
+        const int k = s0 + lane + 32 * u;
+        ok[u] = lane + 32 * u < cnt;
+        n[u] = ok[u] ? sn[k] : 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59 (prime) when idle
+        pos[u] = ok[u] ? sp[k] : 0u;
+      }
+      __syncwarp();  // read before the next task's values overwrite the slots
+      bool pass[kIlp];
+      if constexpr (kIlp == 2) {
+        const int nib = (int)__reduce_max_sync(
+            0xFFFFFFFFu, (unsigned)max(base2_nibbles(n[0]), base2_nibbles(n[1])));
+        base2_passes_shift_x2<kImpl>(n[0], n[1], nib, &pass[0], &pass[1]);
+      } else {
+        const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(n[0]));
+        pass[0] = base2_passes_shift<kImpl, kMode == 2>(n[0], nib);
+      }
+#pragma unroll
+      for (int u = 0; u < kIlp; ++u) append_passing(ok[u] && pass[u], pos[u]);
+    };
     int held = 0;  // staged values, the same in every lane
     for (;;) {
       const bool have = next < vcount;
@@ -164,7 +192,7 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
         const unsigned km = __ballot_sync(0xFFFFFFFFu, keep);
         if (keep) {
           const int k = held + __popc(km & ((1u << lane) - 1u));
-          if (IP_CHECK(k < 64, kChkSmemQueue)) {
+          if (IP_CHECK(k < kStack, kChkSmemQueue)) {
             st_n[k] = n;
             st_pos[k] = pos;
           }
@@ -174,39 +202,30 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
         __syncwarp();
       }
       // full batches from the top of the stack
-      while (held >= 32) {
-        const uint64_t n = st_n[held - 32 + lane];
-        const uint32_t pos = st_pos[held - 32 + lane];
-        __syncwarp();  // read before the next task's values overwrite the slots
-        held -= 32;
-        const int nib = __reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(n));
-        append_passing(base2_passes_shift<kImpl, kMode == 2>(n, nib), pos);
+      while (held >= kB) {
+        held -= kB;
+        run_batch(st_n, st_pos, held, kB);
       }
       if (!have) break;
     }
     // No task left: the warps of the block pool what their stacks still hold
-    // (fewer than 32 each) and run it as full batches, about half as many
+    // (fewer than kB each) and run it as full batches, about half as many
     // warp-batches as each warp running its own partial one.
     uint32_t at = 0;
     if (lane == 0 && held > 0) at = atomicAdd(&s_left, (uint32_t)held);
     at = __shfl_sync(0xFFFFFFFFu, at, 0);
-    if (lane < held && IP_CHECK(at + lane < 32u * nwarps, kChkSmemQueue)) {
-      left_n[at + lane] = st_n[lane];
-      left_pos[at + lane] = st_pos[lane];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const int k = lane + 32 * u;
+      if (k < held && IP_CHECK(at + k < (uint32_t)(kB * nwarps), kChkSmemQueue)) {
+        left_n[at + k] = st_n[k];
+        left_pos[at + k] = st_pos[k];
+      }
     }
     __syncthreads();
     const uint32_t left = s_left;
-    for (uint32_t b = 32u * warp; b < left; b += 32u * nwarps) {
-      const bool valid = b + lane < left;
-      const uint64_t n = valid ? left_n[b + lane] : 0xFFFFFFFFFFFFFFC5ull;
-      const uint32_t pos = valid ? left_pos[b + lane] : 0u;
-      bool pass = false;
-      if (valid) {
-        const int nib = __reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n));
-        pass = base2_passes_shift<kImpl, kMode == 2>(n, nib);
-      }
-      append_passing(pass, pos);
-    }
+    for (uint32_t b = (uint32_t)(kB * warp); b < left; b += (uint32_t)(kB * nwarps))
+      run_batch(left_n, left_pos, (int)b, (int)min(left - b, (uint32_t)kB));
     return;
   }
   while (next < vcount) {
@@ -390,9 +409,9 @@ static void launch_base2_win(const Queues& q, uint8_t* out, unsigned grid, unsig
                              uint32_t compact_min, uint32_t mark, int sm_count, cudaStream_t s,
                              int per_sm_cap, bool pdl) {
   // the table of mode 4 and the finishing of kRest 1: 16 words per thread;
-  // the second trial stage: 96 words per warp (64 values, 64 positions) and
-  // 48 for the block's leftovers (32 values and 32 positions)
-  const size_t smem = kTd2 > 0 ? (size_t)(96 + 48) * (block / 32) * sizeof(uint64_t)
+  // the second trial stage, per warp: a stack of 32 (kIlp + 1) values and
+  // positions and 32 kIlp leftover slots, 1.5 words each
+  const size_t smem = kTd2 > 0 ? (size_t)(48 * (kIlp + 1) + 48 * kIlp) * (block / 32) * sizeof(uint64_t)
                       : (kMode == 4 || kRest == 1) ? (size_t)16 * block * sizeof(uint64_t)
                                                    : 0;
   auto kern = mr64_base2_kernel<kImpl, kMode, kRest, kIlp, kTd2>;
@@ -411,7 +430,19 @@ static void launch_base2_mode(const Queues& q, uint8_t* out, unsigned grid, unsi
     if constexpr (kFast) {
       // the second trial stage (formulations 6 and 9 and the counting build,
       // estimated-quotient windows, one survivor per thread)
-      if (o.ilp == 1 && o.td2 > 0) {
+      if constexpr (kMode == 1) {  // two staged values per lane (td2_groups 16 or 24)
+        if (o.ilp == 2 && o.td2 == 16) {
+          launch_base2_win<kImpl, 1, 0, 2, 16>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                               o.b2_per_sm, o.pdl);
+          return;
+        }
+        if (o.ilp == 2 && o.td2 == 24) {
+          launch_base2_win<kImpl, 1, 0, 2, 24>(q, out, grid, block, o.compact_min, mark, sm_count, s,
+                                               o.b2_per_sm, o.pdl);
+          return;
+        }
+      }
+      if (o.td2 > 0) {
         switch (o.td2) {
           case 8: launch_base2_win<kImpl, kMode, 0, 1, 8>(q, out, grid, block, o.compact_min, mark,
                                                       sm_count, s, o.b2_per_sm, o.pdl); return;

@@ -258,24 +258,26 @@ def td2_data(data):
     return w, oracle.isprime_u64(w)
 
 
-@pytest.mark.parametrize("td2,split,chunk_log2,window", [(8, 1, 24, 1), (12, 0, 24, 1),
-                                                         (16, 1, 24, 1), (24, 1, 24, 1),
-                                                         (16, 0, 16, 1), (24, 1, 16, 1),
-                                                         (16, 1, 24, 2), (0, 1, 24, 2),
-                                                         (16, 0, 16, 2)])
-def test_second_trial_stage_matches_oracle(td2, split, chunk_log2, window, td2_data, ctx):
+@pytest.mark.parametrize("td2,split,chunk_log2,window,ilp", [
+    (8, 1, 24, 1, 1), (12, 0, 24, 1, 1), (16, 1, 24, 1, 1), (24, 1, 24, 1, 1), (16, 0, 16, 1, 1),
+    (24, 1, 16, 1, 1), (16, 1, 24, 2, 1), (0, 1, 24, 2, 1), (16, 0, 16, 2, 1),
+    (16, 1, 24, 1, 2), (24, 0, 24, 1, 2), (16, 1, 16, 1, 2), (24, 1, 16, 1, 2), (16, 1, 24, 2, 2),
+    (8, 1, 24, 1, 2)])
+def test_second_trial_stage_matches_oracle(td2, split, chunk_log2, window, ilp, td2_data, ctx):
     """td2_groups > 0: the base-2 kernel tests its queue against the primes
     59 .. 457 first and stages the survivors per warp; with the s-split on and
     off, one chunk and many (every chunk's stacks drain at its end), and with
     the base-2 window step's quotient estimated in single precision (1) or in
-    integers (2)."""
+    integers (2); with one staged value per lane or two (base2_ilp 2: batches
+    of 64, two interleaved exponentiations per lane)."""
     v, want = td2_data
     ctx.set_tuning(td2_groups=td2, base2_split=split, chunk_log2=chunk_log2, small_max=0,
-                   td_fold=2, base2_ilp=1, rest_window=3, base2_window=window)
+                   td_fold=2, base2_ilp=ilp, rest_window=3, base2_window=window)
     try:
-        _same(v, _run(ctx, v), want, f"td2={td2} split={split} chunk_log2={chunk_log2} w={window}")
+        _same(v, _run(ctx, v), want,
+              f"td2={td2} split={split} chunk_log2={chunk_log2} w={window} ilp={ilp}")
     finally:
-        ctx.set_tuning(td2_groups=0, base2_split=1, chunk_log2=24, base2_window=1)
+        ctx.set_tuning(td2_groups=0, base2_split=1, chunk_log2=24, base2_window=1, base2_ilp=1)
 
 
 def test_second_trial_stage_on_short_queues(td2_data, ctx):
@@ -283,14 +285,15 @@ def test_second_trial_stage_on_short_queues(td2_data, ctx):
     kernel's marks) and partial stacks: every length from 1 to 70 and a few
     longer ones, each slice of the inputs on its own."""
     v, want = td2_data
-    ctx.set_tuning(td2_groups=16, small_max=0)
-    try:
-        rng = np.random.default_rng(33)
-        for n in list(range(1, 71)) + [127, 1000, 4097, 30001]:
-            o = int(rng.integers(0, v.size - n))
-            _same(v[o:o + n], _run(ctx, v[o:o + n]), want[o:o + n], f"td2 short n={n}")
-    finally:
-        ctx.set_tuning(td2_groups=0)
+    for ilp in (1, 2):
+        ctx.set_tuning(td2_groups=16, small_max=0, base2_ilp=ilp)
+        try:
+            rng = np.random.default_rng(33)
+            for n in list(range(1, 71)) + [127, 1000, 4097, 30001]:
+                o = int(rng.integers(0, v.size - n))
+                _same(v[o:o + n], _run(ctx, v[o:o + n]), want[o:o + n], f"td2 short n={n} ilp={ilp}")
+        finally:
+            ctx.set_tuning(td2_groups=0, base2_ilp=1)
 
 
 @pytest.mark.parametrize("fold", [2, 3])
