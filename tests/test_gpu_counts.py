@@ -74,3 +74,27 @@ def test_counts_bound_the_canonical_count_on_the_bench_array(ctx):
     r_issue, r_lanes = c["rest_squarings"]
     assert r_lanes >= w["rest_squarings"] - 6 * 3 * w["base2_passes"]
     assert 32 * r_issue <= 1.25 * (w["rest_squarings"] + 6 * 4 * w["base2_passes"])
+
+
+def test_counts_follow_the_two_stage_schedule():
+    """With the second trial stage (td2_groups 16: the primes 59..311 in the
+    base-2 kernel) the base-2 squarings carried by active lanes follow the
+    oracle's count at trial bound 311 (the windows do up to 3 fewer per value
+    than the binary schedule), not the count at 53; the six-base
+    kernel's work is that of the one-stage schedule, as no prime is removed."""
+    ctx_tuning = dict(base2_window=1, base2_ilp=1, rest_window=3, compact_min=33, td2_groups=16)
+    v = plain_large(1 << 22, seed=1)
+    t = torch.from_numpy(v.view(np.int64)).to("cuda:0")
+    with ipg.Context(0) as c:
+        c.set_tuning(**ctx_tuning)
+        got = c.count_ops(t)
+    w311 = oracle.work_counts(v, td_bound=311)
+    w53 = oracle.work_counts(v, td_bound=53)
+    lanes = got["base2_squarings"][1]
+    # (lanes also square the Montgomery 1 for leading zero digits below the
+    # warp's largest digit count: a fraction of a percent here)
+    assert w311["base2_squarings"] - 3 * w311["mr64_elements"] <= lanes <= 1.01 * w311["base2_squarings"]
+    assert lanes < 0.8 * w53["base2_squarings"]
+    assert w311["base2_passes"] == w53["base2_passes"]
+    r_lanes = got["rest_squarings"][1]
+    assert r_lanes >= w53["rest_squarings"] - 6 * 3 * w53["base2_passes"]
