@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
     if (threadIdx.x == 0) s_left = 0;
     __syncthreads();
     // base 2 on kB values of stack slots s0 + lane + 32 u (u < kIlp); lanes
-    // past `cnt` values test a prime and report nothing
+    // past `cnt` values sit out (one value per lane) or test a prime and
+    // report nothing (two per lane)
     auto run_batch = [&](const uint64_t* sn, const uint32_t* sp, int s0, int cnt) {
       uint64_t n[kIlp];
       uint32_t pos[kIlp];
@@ -163,9 +164,12 @@ __global__ void __launch_bounds__(256) mr64_base2_kernel(const uint64_t* __restr
         const int nib = (int)__reduce_max_sync(
             0xFFFFFFFFu, (unsigned)max(base2_nibbles(n[0]), base2_nibbles(n[1])));
         base2_passes_shift_x2<kImpl>(n[0], n[1], nib, &pass[0], &pass[1]);
-      } else {
-        const int nib = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)base2_nibbles(n[0]));
-        pass[0] = base2_passes_shift<kImpl, kMode == 2>(n[0], nib);
+      } else {  // lanes without a value sit out (a full batch has none)
+        pass[0] = false;
+        if (ok[0]) {
+          const int nib = (int)__reduce_max_sync(__activemask(), (unsigned)base2_nibbles(n[0]));
+          pass[0] = base2_passes_shift<kImpl, kMode == 2>(n[0], nib);
+        }
       }
 #pragma unroll
       for (int u = 0; u < kIlp; ++u) append_passing(ok[u] && pass[u], pos[u]);
