@@ -69,7 +69,7 @@ SM_MAX_MHZ = 2070.0
 # recorded here; they hold for that build only and are reported as null for
 # any other.
 NCU_TRAFFIC = {
-    "sources": "99213ed06a255dd3",
+    "sources": "c81e2467fcb1e9a0",
     "tuning": {"classify_block": 256, "mr_block": 256, "blocks_per_sm": 32, "td_primes": 15, "chunk_log2": 24, "mont_impl": 9, "mont_impl_base2": 9, "batch_block": 128, "batch_tile_log2": 10, "batch_blocks_per_sm": 0, "base2_window": 1, "rest_test": 0, "small_max": 8192, "compact_min": 33, "sieve_cutover_log2": 32, "serve_short_max": 32768, "td_fold": 3, "base2_split": 1, "base2_ilp": 1, "rest_window": 3, "window_ratio16": 0, "base2_blocks_per_sm": 4, "pdl": 1, "td2_groups": 16, "dual_stream": 0, "host_chunk_log2": 22, "inplace_max_log2": 0, "serve_long_log2": 24, "rest_ilp": 2},
     "mr64_base2": 27.45e6, "mr64_rest": 46.06e6, "classify_u64": 145.76e6}
 

@@ -7,20 +7,23 @@
 //
 // Kernels (each a grid-stride loop over a queue whose length is read on the
 // device, so no host synchronisation separates the stages):
-//   mr64_base2_kernel  base 2 for every 64-bit survivor of trial division, by
+//   mr64_base2_kernel  a second trial stage (td2_groups: the primes after 53,
+//                      on the queue's values, survivors staged per warp so
+//                      the exponentiations run on full warps), then base 2 by
 //                      4-bit windows where "multiply by 2^w" is x 2^w - q n
-//                      with an estimated quotient (base2_window 1), or a
-//                      Montgomery product with the table 2^w R (4), or
-//                      binary with a modular doubling per set bit (0).  Passing elements (the primes and rare
-//                      strong pseudoprimes) are compacted with warp ballots
-//                      into a second queue, so the next kernel runs on dense
-//                      warps of likely primes instead of idling behind
-//                      early-exiting composites.  With the compaction threshold
-//                      compact_min <= 32, a warp left with at least that many
-//                      survivors finishes them itself.
-//   mr64_rest_kernel   the six remaining bases, 4-bit fixed-window
-//                      exponentiation with the per-thread window table in
-//                      shared memory.  On chunks of at most 2^22 elements a
+//                      with an estimated quotient (base2_window 1 or 2), or a
+//                      Montgomery product with the table 2^w R (4), or binary
+//                      with a modular doubling per set bit (0).  Passing
+//                      elements (the primes and rare strong pseudoprimes) are
+//                      compacted with warp ballots into a second queue, so the
+//                      next kernel runs on dense warps of likely primes instead
+//                      of idling behind early-exiting composites.  With the
+//                      compaction threshold compact_min <= 32, a warp left with
+//                      at least that many survivors finishes them itself.
+//   mr64_rest_kernel   the six remaining bases, fixed-window exponentiation
+//                      (3- or 4-bit, rest_window) with the per-thread window
+//                      tables in shared memory, the bases one at a time or in
+//                      pairs (rest_ilp).  On chunks of at most 2^22 elements a
 //                      queue shorter than the grid is spread over 6, 3 or 2
 //                      threads per survivor (the base-2 kernel then marks its
 //                      survivors prime and a failing base clears the byte);
