@@ -97,3 +97,20 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert sizes == [ctypes.sizeof(ipg.Tuning), ctypes.sizeof(ipg._Stats), ctypes.sizeof(ipg._KTime),
                      ctypes.sizeof(ipg._IntRates), ctypes.sizeof(ipg.ArrayDesc),
                      ctypes.sizeof(ipg._ServerStats), ctypes.sizeof(ipg._OpCounts)]
+
+
+def test_tuning_struct_matches_the_binding(L):
+    """The Python binding's Tuning mirrors isprime_tuning field by field (names
+    and order, all uint32_t), and the defaults read back through
+    isprime_tuning_defaults land in the right fields."""
+    src = open(HEADER).read()
+    body = src[src.index("typedef struct"):src.index("} isprime_tuning;")]
+    body = body[body.rindex("typedef struct"):]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(uint32_t|uint64_t|int)\s+([a-z0-9_]+)\s*;", body)
+    assert fields and all(t == "uint32_t" for t, _ in fields)
+    assert [n for _, n in fields] == [n for n, _ in ipg.Tuning._fields_]
+    d = ipg.default_tuning()
+    assert d["chunk_log2"] == 24 and d["td_primes"] == 15 and d["td2_groups"] == 16
+    assert d["rest_ilp"] == 2 and d["td_fold"] == 3 and d["mont_impl"] == 9
+    assert d["serve_long_log2"] == 24 and d["host_chunk_log2"] == 22 and d["inplace_max_log2"] == 0
